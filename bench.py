@@ -1,0 +1,401 @@
+#!/usr/bin/env python3
+"""Benchmark of the particle-particle ladder (R += sum_cd (ac|bd) t2) on GB300.
+
+One step = one ladder_apply (all steps of the hot path: operand preparation,
+Cholesky->ERI GEMM, ladder GEMM, a<=b unpack) on the synthetic workload.
+Default workload: no=10, nv=200, nchol=630 (the one-batch configuration whose
+packed ERI is 6.4 GB), seeded generators of ``ladder_inputs``.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision emu|fp64]
+                    [--config c2] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  ``value`` = algorithmic TFLOP/s
+(2 X v^2 p + 2 o^2 v^2 p with p = v(v+1)/2, per instance) summed over ranks,
+timed with CUDA events on the launching stream between barriers, max over
+ranks; inputs resident in HBM.  ``e2e`` repeats the measurement through the
+same public call with the inputs copied from pinned host memory and R read
+back every step.  Multi-GPU runs (torchrun) give each rank its own
+independent instance (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from ladder_inputs import CONFIGS, make_inputs  # noqa: E402
+
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+FALLBACK_BF16_TFLOPS = 1900.0
+NOMINAL_BF16_TFLOPS = 2250.0
+NOMINAL_FP64_TFLOPS = 1.25
+
+
+def load_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": FALLBACK_HBM_GBS, "bf16_tflops": FALLBACK_BF16_TFLOPS,
+                "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_baseline_sample(L, t2, target_s=15.0):
+    """Time the oracle (as it stands) on a bounded sample of (a, b) pairs."""
+    import oracle
+    nchol, nv, _ = L.shape
+    no = t2.shape[0]
+    per_pair = 2.0 * nchol * nv * nv + 2.0 * no * no * nv * nv
+    rng = np.random.default_rng(7)
+    n = max(1, oracle.num_threads())
+    a = rng.integers(0, nv, n)
+    b = rng.integers(0, nv, n)
+    t0 = time.perf_counter()
+    oracle.ladder_pairs(L, t2, a, b)
+    dt = time.perf_counter() - t0
+    n2 = int(max(1, min(nv * nv, n * max(1.0, target_s / max(dt, 1e-3)))))
+    a = rng.integers(0, nv, n2)
+    b = rng.integers(0, nv, n2)
+    t0 = time.perf_counter()
+    oracle.ladder_pairs(L, t2, np.minimum(a, b), np.maximum(a, b))
+    dt = time.perf_counter() - t0
+    return {"value": n2 * per_pair / dt / 1e12, "unit": "TFLOP/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{n2} random (a<=b) pairs of the workload, all (i,j), {dt:.1f} s wall"}, n2, dt
+
+
+def run_reference(args, cfg):
+    """The CPU oracle as the reference arm (rank 0 only)."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    L, t2, _, _ = make_inputs(cfg.no, cfg.nv, cfg.nchol, cfg.seed)
+    import oracle
+    nchol, nv, _ = L.shape
+    no = t2.shape[0]
+    per_pair = 2.0 * nchol * nv * nv + 2.0 * no * no * nv * nv
+    rng = np.random.default_rng(11)
+    # Size one step to ~ (few minutes / (steps + warmup)).
+    n = max(1, oracle.num_threads())
+    t0 = time.perf_counter()
+    oracle.ladder_pairs(L, t2, rng.integers(0, nv, n), rng.integers(0, nv, n))
+    probe = time.perf_counter() - t0
+    step_s = min(20.0, 150.0 / max(1, args.steps + args.warmup))
+    npairs = int(max(1, min(nv * nv, n * step_s / max(probe, 1e-3))))
+    times = []
+    for k in range(args.warmup + args.steps):
+        a = rng.integers(0, nv, npairs)
+        b = rng.integers(0, nv, npairs)
+        t0 = time.perf_counter()
+        oracle.ladder_pairs(L, t2, np.minimum(a, b), np.maximum(a, b))
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+    tot = sum(times)
+    value = args.steps * npairs * per_pair / tot / 1e12
+    line = {
+        "impl": "reference", "metric": "PP-ladder TFLOP/s", "value": value, "unit": "TFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{cfg.name}: no={cfg.no} nv={cfg.nv} nchol={cfg.nchol} seed={cfg.seed}",
+                   "sample_pairs_per_step": npairs},
+        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": f"{npairs} random (a<=b) pairs per step of {nv * (nv + 1) // 2}, all (i,j)"},
+        "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def measure_peaks():
+    """Library matmul throughput on this GPU (context for the roofline denominators)."""
+    import torch
+    out = {}
+
+    def timeit(fn, flops, reps):
+        fn()
+        torch.cuda.synchronize()
+        best = 1e30
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1) * 1e-3)
+        return flops / best / 1e12
+
+    n = 8192
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    out["fp64_matmul_tflops"] = timeit(lambda: a @ b, 2.0 * n ** 3, 3)
+    del a, b
+    a = torch.randn(n, n, dtype=torch.bfloat16, device="cuda")
+    b = torch.randn(n, n, dtype=torch.bfloat16, device="cuda")
+    out["bf16_matmul_tflops"] = timeit(lambda: a @ b, 2.0 * n ** 3, 10)
+    del a, b
+    try:
+        a = torch.randint(-64, 64, (n, n), dtype=torch.int8, device="cuda")
+        b = torch.randint(-64, 64, (n, n), dtype=torch.int8, device="cuda").t()
+        out["int8_mm_tops"] = timeit(lambda: torch._int_mm(a, b), 2.0 * n ** 3, 10)
+    except Exception as e:  # pragma: no cover - depends on the library build
+        out["int8_mm_tops"] = f"unavailable: {e}"
+    out["gpu"] = torch.cuda.get_device_name()
+    out["sms"] = torch.cuda.get_device_properties(0).multi_processor_count
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--config", default="c2", choices=sorted(CONFIGS))
+    ap.add_argument("--precision", default="emu", choices=["emu", "fp64"])
+    ap.add_argument("--nslices", type=int, default=0)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--measure-peaks", action="store_true",
+                    help="print torch/cuBLAS matmul throughput for fp64, bf16 and int8 and exit")
+    args = ap.parse_args()
+    if args.measure_peaks:
+        measure_peaks()
+        return
+    cfg = CONFIGS[args.config]
+    if args.warmup < 3:
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args, cfg)
+        return
+
+    import torch
+    import paper_2603_20912_gb300 as lad
+    from paper_2603_20912_gb300 import build
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    build.build()
+    precision = lad.LADDER_EMU_BF16 if args.precision == "emu" else lad.LADDER_FP64
+    # Each rank: its own independent instance (seed offset by rank).
+    L, t2, _, _ = make_inputs(cfg.no, cfg.nv, cfg.nchol, cfg.seed + 7919 * rank)
+    Lh = torch.from_numpy(L).pin_memory()
+    th = torch.from_numpy(t2).pin_memory()
+    Ld = Lh.to("cuda", non_blocking=True)
+    td = th.to("cuda", non_blocking=True)
+    R = torch.zeros_like(td)
+    plan = lad.ladder_plan(cfg.no, cfg.nv, cfg.nchol, precision, nslices=args.nslices, device=local)
+    ws = plan.workspace()
+    desc = plan.describe()
+    stream = torch.cuda.current_stream()
+    flops = lad.ladder_flops(cfg.no, cfg.nv, cfg.nchol)
+
+    for _ in range(args.warmup):
+        lad.ladder_apply(plan, Ld, td, R, ws)
+    torch.cuda.synchronize()
+    plan.set_timing(True)
+    sampler = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        lad.ladder_apply(plan, Ld, td, R, ws)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    barrier(world)
+    ms_total = ev0.elapsed_time(ev1)
+    ms_total = max_over_ranks(ms_total, world)
+    ms_step = ms_total / args.steps
+    value = world * flops * args.steps / (ms_total * 1e-3) / 1e12
+
+    counts = {}
+    kms = {}
+    for kind, name in [(lad.LADDER_KERNEL_PREP, "prep"), (lad.LADDER_KERNEL_ERI, "eri"),
+                       (lad.LADDER_KERNEL_LADDER, "ladder"), (lad.LADDER_KERNEL_FINISH, "finish")]:
+        ms, n = plan.timing(kind)
+        kms[name] = ms
+        counts[name] = n
+    plan.set_timing(False)
+    launches = sum(counts.values())
+
+    # Dominant kernel: the ERI GEMM.  Algorithmic flops per launch = 2 X v^2 (pairs in the block);
+    # the emulated kernel executes S(S+1)/2 BF16 slice products per FP64 product.
+    nv2 = cfg.nv * cfg.nv
+    pairs_total = cfg.nv * (cfg.nv + 1) // 2
+    eri_flops_call = 2.0 * cfg.nchol * nv2 * pairs_total
+    peaks, peak_src = load_peaks()
+    if precision == lad.LADDER_EMU_BF16:
+        S = desc["nslices"]
+        slice_products = S * (S + 1) // 2
+        eri_exec_flops_call = eri_flops_call * slice_products
+        achieved = eri_exec_flops_call * args.steps / (kms["eri"] * 1e-3) / 1e12 if kms["eri"] > 0 else None
+        peak = peaks.get("bf16_tflops", FALLBACK_BF16_TFLOPS)
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "kernel": "eri_emu (tcgen05 BF16 slice GEMM)", "peak_source": f"bf16_tflops ({peak_src})",
+                "executed_slice_products": slice_products}
+        dtype = "f64-emulated(bf16 slices)"
+    else:
+        achieved = eri_flops_call * args.steps / (kms["eri"] * 1e-3) / 1e12 if kms["eri"] > 0 else None
+        bf16 = peaks.get("bf16_tflops", FALLBACK_BF16_TFLOPS)
+        peak = bf16 * NOMINAL_FP64_TFLOPS / NOMINAL_BF16_TFLOPS
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "kernel": "eri_fp64_kernel (DMMA)",
+                "peak_source": f"bf16_tflops ({peak_src}) x nominal FP64/BF16 ratio 1.25/2250"}
+        dtype = "f64"
+
+    # End to end through the public call with host buffers: H2D of L and t2 from pinned memory,
+    # apply into a zeroed R, D2H of R, every step.
+    e2e = None
+    if not args.no_e2e:
+        Rh = torch.empty(t2.shape, dtype=torch.float64).pin_memory()
+        barrier(world)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            Ld.copy_(Lh, non_blocking=True)
+            td.copy_(th, non_blocking=True)
+            R.zero_()
+            lad.ladder_apply(plan, Ld, td, R, ws)
+            Rh.copy_(R, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_e2e = max_over_ranks(e0.elapsed_time(e1), world)
+        e2e = {"value": world * flops * args.steps / (ms_e2e * 1e-3) / 1e12, "unit": "TFLOP/s",
+               "ms_per_step": ms_e2e / args.steps,
+               "h2d_bytes_per_step": int(L.nbytes + t2.nbytes), "d2h_bytes_per_step": int(t2.nbytes)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu, _, _ = cpu_baseline_sample(L, t2)
+
+    if rank == 0:
+        line = {
+            "metric": "PP-ladder TFLOP/s", "value": value, "unit": "TFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+            "config": {"workload": f"{cfg.name}: no={cfg.no} nv={cfg.nv} nchol={cfg.nchol} seed={cfg.seed}",
+                       "precision": args.precision, "nslices": desc["nslices"], "n_a": desc["n_a"],
+                       "n_b": desc["n_b"], "block_pairs": desc["n_block_pairs"],
+                       "l2": "inputs+workspace > L2 (V block written and re-read every step)",
+                       "parallelism": f"independent instance per GPU x{world}"},
+            "ms_per_call": ms_step,
+            "kernel_ms_per_call": {k: v / args.steps for k, v in kms.items()},
+            "gpu_launches": launches,
+            "roofline": roof,
+            "clocks": clocks,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,206 @@
+/*
+ * ladder.h -- C ABI of the GB300 particle-particle ladder library (libladder.so).
+ *
+ * The library evaluates the closed-shell particle-particle ladder term of
+ * Cholesky-based CCSD (Sec. "Acceleration of CC calculations", Eq. ppl-term
+ * with Eq. cholesky inserted, i.e. Eq. vfunction-chol):
+ *
+ *     R[i,j,a,b] += sum_{c,d} (ac|bd) t2[i,j,c,d],
+ *     (ac|bd)     = sum_P L[P,a,c] L[P,b,d],
+ *
+ * rebuilding (ac|bd) on the fly from the Cholesky vectors in blocks of
+ * (a, b) pairs sized to the device memory (Sec. "Memory Management",
+ * "An Asymmetric and Dynamic Splitting Protocol", Table 1).  Only pairs with
+ * a <= b are formed; R_ji^ba = R_ij^ab supplies the rest.
+ *
+ * Index roles follow the paper's 'xac,xbd,icjd' contraction with the output
+ * stored (i, j, a, b) and the amplitudes stored (i, j, c, d).
+ *
+ * Conventions for every entry point
+ * ---------------------------------
+ * - Arrays are C-contiguous (row-major) IEEE float64 in device memory of the
+ *   plan's device:  L[nchol][nv][nv], t2[no][no][nv][nv], R[no][no][nv][nv].
+ *   Device pointers must be 256-byte aligned, otherwise LADDER_ERR_ARG.
+ * - Precondition ASSUMED, not checked: t2[i,j,a,b] == t2[j,i,b,a].  The
+ *   a <= b packing relies on it (with a non-symmetric t2 the result differs
+ *   from the definition).  Symmetry of L[P] in (a, c) is not required.
+ * - Ownership: the caller owns L, t2, R and the workspace.  A plan owns only
+ *   host metadata and a small device table written at plan time.
+ * - ladder_apply / ladder_apply_batched perform no allocation and no host
+ *   synchronisation; all work is enqueued on the given stream.
+ * - Synchronous errors (bad arguments, CUDA launch failures) are returned.
+ *   Errors detected by kernels (a bounded wait that ran out, a failed
+ *   consistency check) are recorded in the plan's device status word and
+ *   reported by ladder_last_status().
+ * - Not provided: no CPU fallback and no backend selection.
+ */
+#ifndef LADDER_H
+#define LADDER_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ladder_plan_s* ladder_plan_t;
+
+/* Status codes. */
+enum {
+    LADDER_OK = 0,
+    LADDER_ERR_ARG = 1,          /* invalid argument, size, alignment or null pointer   */
+    LADDER_ERR_BUDGET = 2,       /* no blocking fits the workspace budget                */
+    LADDER_ERR_CUDA = 3,         /* a CUDA runtime / driver call failed                  */
+    LADDER_ERR_UNSUPPORTED = 4,  /* valid request this build does not implement          */
+    LADDER_ERR_TIMEOUT = 5,      /* a kernel's bounded wait ran out (device status)      */
+    LADDER_ERR_NUMERIC = 6       /* a kernel consistency check failed (device status)    */
+};
+
+/* Arithmetic of the two contractions. */
+enum {
+    LADDER_FP64 = 0,      /* native FP64 (DMMA tensor instructions)                        */
+    LADDER_EMU_BF16 = 1,  /* FP64 emulated by BF16 digit slices on tcgen05, FP32 accumulate */
+    LADDER_EMU_INT8 = 2   /* INT8 slices: rejected with LADDER_ERR_UNSUPPORTED             */
+};
+
+/*
+ * ladder_plan -- choose the blocking and the kernels for one problem shape.
+ *
+ * Defines: the a/b blocking of the (a <= b) pair space (Sec. "An Asymmetric
+ * and Dynamic Splitting Protocol", Table 1, the C-split loop nest).  Blocks of
+ * n_a virtual indices a and n_b indices b (n_a != n_b allowed) are chosen by
+ * a cost model subject to the workspace budget.
+ *
+ *   out        receives the plan handle (set to NULL on failure).
+ *   no, nv     occupied / virtual orbital counts (>= 1).
+ *   nchol      number of Cholesky vectors (>= 1).
+ *   precision  LADDER_FP64 or LADDER_EMU_BF16.
+ *   nslices    digit slices per operand for the emulated path, 0 = default (6);
+ *              ignored for LADDER_FP64.  Valid range 3..8.
+ *   ws_budget_bytes  workspace budget; 0 = 0.9 * 0.98 * free device memory
+ *              (the safety factors of the paper's C-split rule).
+ *   device     CUDA device ordinal.
+ *
+ * Returns LADDER_OK, LADDER_ERR_ARG, LADDER_ERR_BUDGET (no blocking fits),
+ * LADDER_ERR_UNSUPPORTED (LADDER_EMU_INT8, or emulated nchol > 1365) or
+ * LADDER_ERR_CUDA.  Allocates a small device table (freed by
+ * ladder_plan_destroy).
+ */
+int ladder_plan(ladder_plan_t* out, int no, int nv, int nchol, int precision, int nslices,
+                size_t ws_budget_bytes, int device);
+
+/* Force the a/b block sizes of an existing plan (tests, tuning).  Rebuilds the
+ * device tables.  Returns LADDER_ERR_BUDGET if the workspace would exceed the
+ * plan's budget, LADDER_ERR_ARG for sizes outside 1..nv. */
+int ladder_plan_set_blocks(ladder_plan_t plan, int n_a, int n_b);
+
+/*
+ * ladder_plan_dry -- run the planner on the host only (no CUDA call), for
+ * inspection and tests.  Same meaning of no, nv, nchol, precision, nslices as
+ * ladder_plan; ws_budget_bytes must be > 0 and num_sms >= 1 (the SM count the
+ * cost model assumes).  force_n_a / force_n_b > 0 impose block sizes instead
+ * of the model's choice.  Outputs (any may be NULL): chosen n_a, n_b, the
+ * workspace bytes, the number of (A,B) block pairs, and up to max_blocks rows
+ * of blocks[5*k..5*k+4] = {a0, a1, b0, b1, npairs} in execution order.
+ * Returns LADDER_OK, LADDER_ERR_ARG, LADDER_ERR_BUDGET or LADDER_ERR_UNSUPPORTED.
+ */
+int ladder_plan_dry(int no, int nv, int nchol, int precision, int nslices, size_t ws_budget_bytes, int num_sms,
+                    int force_n_a, int force_n_b, int* n_a, int* n_b, size_t* ws_bytes, int max_blocks,
+                    int* n_block_pairs, int* blocks);
+
+/* Workspace bytes ladder_apply needs (device memory, 256-byte aligned start). */
+size_t ladder_workspace_bytes(ladder_plan_t plan);
+
+/* Describe a plan: block sizes, number of (A,B) block pairs, largest pair
+ * count of a block, slices.  Any output pointer may be NULL. */
+int ladder_plan_describe(ladder_plan_t plan, int* n_a, int* n_b, int* n_block_pairs,
+                         int* max_pairs_per_block, int* nslices, int* precision);
+
+/*
+ * ladder_apply -- R += ladder(L, t2)   (Eq. vfunction-chol).
+ *
+ *   L   device, [nchol][nv][nv] float64.
+ *   t2  device, [no][no][nv][nv] float64, t2[i,j,a,b] == t2[j,i,b,a].
+ *   R   device, [no][no][nv][nv] float64, accumulated in place (+=).
+ *   ws  device workspace of ladder_workspace_bytes(plan) bytes (contents
+ *       need not be initialised; they are overwritten).
+ *   stream  CUDA stream; all work is enqueued on it, nothing synchronises.
+ *
+ * Returns LADDER_OK or LADDER_ERR_ARG / LADDER_ERR_CUDA.  L, t2 and R must not
+ * overlap each other or the workspace.
+ */
+int ladder_apply(ladder_plan_t plan, const double* L, const double* t2, double* R, void* ws,
+                 cudaStream_t stream);
+
+/*
+ * ladder_energy -- E_L = sum_{ijab} (2 t2[i,j,a,b] - t2[i,j,b,a]) R[i,j,a,b].
+ *
+ * The closed-shell energy expression the ladder residual enters (the CC energy
+ * evaluation of Sec. "Molecular benchmark calculations").  FP64 throughout,
+ * fixed-order tree reduction (deterministic).
+ *
+ *   E_dev   device double* receiving E_L, or NULL.
+ *   E_host  host double* receiving E_L, or NULL; when non-NULL the call
+ *           synchronises the stream to read the value back.
+ * At least one of E_dev / E_host must be non-NULL.
+ */
+int ladder_energy(ladder_plan_t plan, const double* t2, const double* R, double* E_dev,
+                  double* E_host, cudaStream_t stream);
+
+/*
+ * ladder_plan_batched -- one plan for n independent ladder instances of
+ * uneven shape (no[k], nv[k], nchol[k]), run by ladder_apply_batched as one
+ * persistent launch.  Tile shapes and splits come from the built-in tuner.
+ * Same precision / nslices / budget / device meaning as ladder_plan.
+ */
+int ladder_plan_batched(ladder_plan_t* out, int n, const int* no, const int* nv, const int* nchol,
+                        int precision, int nslices, size_t ws_budget_bytes, int device);
+
+/*
+ * ladder_apply_batched -- R[k] += ladder(L[k], t2[k]) for every instance k.
+ * L, t2, R are HOST arrays of n device pointers.  No allocation and no host
+ * synchronisation; the work can be captured in a CUDA graph.
+ */
+int ladder_apply_batched(ladder_plan_t plan, const double* const* L, const double* const* t2,
+                         double* const* R, void* ws, cudaStream_t stream);
+
+/*
+ * Per-kernel timing for benchmarks.  ladder_plan_set_timing(plan, 1) creates a
+ * pool of CUDA events; while enabled, ladder_apply records an event pair on
+ * its stream around every kernel it launches, tagged with the kernel class
+ * (LADDER_KERNEL_*).  ladder_plan_timing waits for the recorded events and
+ * returns, for one class, the summed elapsed milliseconds and the launch count
+ * since the last reset; reset != 0 clears all records afterwards.  Timing is
+ * off by default and costs nothing then.
+ */
+enum {
+    LADDER_KERNEL_PREP = 0,     /* operand slicing / exponent kernels (emulated path) */
+    LADDER_KERNEL_ERI = 1,      /* Cholesky -> ERI GEMM                               */
+    LADDER_KERNEL_LADDER = 2,   /* ladder GEMM                                        */
+    LADDER_KERNEL_FINISH = 3,   /* accumulator finalisation / unpack                  */
+    LADDER_KERNEL_CLASSES = 4
+};
+int ladder_plan_set_timing(ladder_plan_t plan, int enable);
+int ladder_plan_timing(ladder_plan_t plan, int kernel_class, float* total_ms, int* launches, int reset);
+
+/* Read (and clear) the plan's device status word: LADDER_OK, LADDER_ERR_TIMEOUT
+ * or LADDER_ERR_NUMERIC.  Synchronises the stream. */
+int ladder_last_status(ladder_plan_t plan, cudaStream_t stream);
+
+/* Release a plan (NULL is ignored).  Frees the plan's device table. */
+void ladder_plan_destroy(ladder_plan_t plan);
+
+/* Static, human-readable description of a status code. */
+const char* ladder_strerror(int status);
+
+/* Algorithmic FP64 flop count of one ladder_apply with a <= b packing:
+ * 2 nchol nv^2 p + 2 no^2 nv^2 p, p = nv (nv + 1) / 2. */
+double ladder_flops(int no, int nv, int nchol);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LADDER_H */

@@ -1,0 +1,579 @@
+// Host runtime: the C ABI (include/ladder.h), the a/b block planner and the
+// per-call orchestration.
+//
+// Planner (Sec. "An Asymmetric and Dynamic Splitting Protocol", Table 1, and
+// the C-split loop nest): the paper sizes blocks along a, b (and c) so that
+// the two consecutive contractions of one batch fit the free VRAM, with a and
+// b split independently (n_a != n_b) and the budget taken as
+// avail * 0.98 * 0.9.  Here L, t2 and R stay resident in HBM and only the
+// intermediate of one (A, B) block pair -- the packed V block (a <= b only)
+// and, on the emulated path, its digit slices and an int64 accumulator -- is
+// staged in the workspace.  Among the (n_a, n_b) whose workspace fits the
+// budget the planner picks the one with the lowest modelled time: per block
+// pair, wave-quantised tile counts of the ERI GEMM and the ladder GEMM plus a
+// fixed launch overhead.  The loop order over block pairs is the C-split
+// order: b-blocks outer, a-blocks inner.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "ladder_internal.h"
+
+using ladder::BlockPair;
+
+namespace {
+
+int map_cuda(cudaError_t e) { return e == cudaSuccess ? LADDER_OK : LADDER_ERR_CUDA; }
+
+long long count_pairs(int a0, int a1, int b0, int b1) {
+    long long n = 0;
+    for (int a = a0; a < a1; ++a) n += std::max(0, b1 - std::max(a, b0));
+    return n;
+}
+
+struct Geometry {
+    int eri_tm, eri_tn, eri_occ;    // ERI tile and resident CTAs per SM
+    int lad_tm, lad_tn, lad_occ;    // ladder tile
+    double eri_tile_s;              // seconds for one ERI tile on one otherwise idle SM
+    double lad_tile_s;              // seconds for one ladder tile
+    double overhead_s;              // fixed cost per block pair
+};
+
+Geometry geometry_for(const ladder_plan_s& p) {
+    Geometry g{};
+    const double X = p.nchol, v2 = (double)p.nv * p.nv;
+    if (p.precision == LADDER_FP64) {
+        // FP64 DMMA: ~1.2 TFLOP/s per device; 64x64 tiles, several CTAs per SM.
+        const double sm_rate = 1.2e12 / std::max(1, p.num_sms);
+        g = {64, 64, 4, 64, 64, 4, 0, 0, 20e-6};
+        g.eri_tile_s = 2.0 * 64 * 64 * X / sm_rate;
+        g.lad_tile_s = 2.0 * 64 * 64 * v2 / sm_rate;
+    } else {
+        // BF16 tcgen05: ~1.5 PFLOP/s sustained; S(S+1)/2 slice products per element.
+        const double pairs = 0.5 * p.nslices * (p.nslices + 1);
+        const double sm_rate = 1.5e15 / std::max(1, p.num_sms);
+        const int ltn = std::min(128, ((p.no * p.no + 15) / 16) * 16);
+        g = {128, 128, 1, 128, ltn, 1, 0, 0, 25e-6};
+        g.eri_tile_s = 2.0 * 128 * 128 * X * pairs / sm_rate + 3e-6;
+        g.lad_tile_s = 2.0 * 128 * ltn * v2 * pairs / sm_rate + 3e-6;
+    }
+    return g;
+}
+
+long long count_eri_tiles(const BlockPair& bp, int nv, int tm, int tn) {
+    const int na = bp.a1 - bp.a0, nb = bp.b1 - bp.b0;
+    const long long M = (long long)na * nv, N = (long long)nb * nv;
+    const long long nrt = (M + tm - 1) / tm, nqt = (N + tn - 1) / tn;
+    long long tiles = 0;
+    for (long long rt = 0; rt < nrt; ++rt) {
+        const int a_min = bp.a0 + (int)(rt * tm / nv);
+        // smallest qt whose largest b reaches a_min
+        long long lo = 0, hi = nqt;
+        while (lo < hi) {
+            const long long mid = (lo + hi) / 2;
+            const long long last = std::min((mid + 1) * tn, N) - 1;
+            const int b_max = bp.b0 + (int)(last / nv);
+            if (b_max >= a_min) hi = mid; else lo = mid + 1;
+        }
+        tiles += nqt - lo;
+    }
+    return tiles;
+}
+
+std::vector<BlockPair> enumerate_blocks(int nv, int na, int nb) {
+    std::vector<BlockPair> out;
+    for (int b0 = 0; b0 < nv; b0 += nb) {          // C-split order: b outer, a inner
+        const int b1 = std::min(nv, b0 + nb);
+        for (int a0 = 0; a0 < nv; a0 += na) {
+            const int a1 = std::min(nv, a0 + na);
+            const long long n = count_pairs(a0, a1, b0, b1);
+            if (n > 0) out.push_back(BlockPair{a0, a1, b0, b1, (int)n, 0, 0});
+        }
+    }
+    return out;
+}
+
+ladder::WsLayout layout_for(const ladder_plan_s& p, long long max_pairs) {
+    using ladder::align_up;
+    using ladder::kAlign;
+    ladder::WsLayout w;
+    const size_t nv2 = (size_t)p.nv * p.nv, no2 = (size_t)p.no * p.no;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { const size_t o = off; off = align_up(off + bytes, kAlign); return o; };
+    if (p.precision == LADDER_FP64) {
+        w.v_blk = take((size_t)max_pairs * nv2 * sizeof(double));
+    } else {
+        const size_t S = p.nslices;
+        const size_t kpad = align_up(nv2, 8), xpad = align_up((size_t)p.nchol, 8);
+        w.v_blk = take(S * (size_t)max_pairs * kpad * 2);
+        w.rp_int = take((size_t)max_pairs * no2 * 8);
+        w.lt_slices = take(S * nv2 * xpad * 2);
+        w.lt_exp = take(((nv2 + ladder::kExpGroupRows - 1) / ladder::kExpGroupRows) * 4);
+        w.t_slices = take(S * no2 * kpad * 2);
+        w.t_exp = take(((no2 + ladder::kExpGroupRows - 1) / ladder::kExpGroupRows) * 4);
+        w.v_exp = take(nv2 * 4);
+        w.lnorm = take((size_t)p.nv * 8);
+    }
+    w.total = std::max<size_t>(off, kAlign);
+    return w;
+}
+
+long long max_pairs_of(const std::vector<BlockPair>& bps) {
+    long long m = 0;
+    for (auto& b : bps) m = std::max<long long>(m, b.npairs);
+    return m;
+}
+
+double model_time(const ladder_plan_s& p, const std::vector<BlockPair>& bps) {
+    const Geometry g = geometry_for(p);
+    const double slots_e = (double)p.num_sms * g.eri_occ, slots_l = (double)p.num_sms * g.lad_occ;
+    const long long nt = (long long)(p.no * p.no + g.lad_tn - 1) / g.lad_tn;
+    double t = 0.0;
+    for (auto& bp : bps) {
+        const long long te = count_eri_tiles(bp, p.nv, g.eri_tm, g.eri_tn);
+        const long long tl = ((long long)(bp.npairs + g.lad_tm - 1) / g.lad_tm) * nt;
+        t += std::ceil(te / slots_e) * g.eri_occ * g.eri_tile_s;
+        t += std::ceil(tl / slots_l) * g.lad_occ * g.lad_tile_s;
+        t += g.overhead_s;
+    }
+    return t;
+}
+
+// Build device tables for the chosen blocking: per block pair its pair list
+// (int2 (a, b), a-major) and row_start (first packed row of each a).
+int build_tables(ladder_plan_s& p) {
+    size_t n_int2 = 0, n_int = 0;
+    for (auto& bp : p.bps) n_int2 += bp.npairs;
+    for (auto& bp : p.bps) n_int += (size_t)(bp.a1 - bp.a0 + 1);
+    std::vector<int> host(2 * n_int2 + n_int);
+    size_t o2 = 0, oi = 2 * n_int2;
+    for (auto& bp : p.bps) {
+        bp.pairs_off = o2;
+        bp.rows_off = oi;
+        int row = 0;
+        for (int a = bp.a0; a < bp.a1; ++a) {
+            host[oi++] = row;
+            for (int b = std::max(a, bp.b0); b < bp.b1; ++b) {
+                host[2 * o2] = a;
+                host[2 * o2 + 1] = b;
+                ++o2;
+                ++row;
+            }
+        }
+        host[oi++] = row;
+    }
+    if (p.d_tables) {
+        cudaFree(p.d_tables);
+        p.d_tables = nullptr;
+    }
+    p.tables_bytes = std::max<size_t>(host.size() * sizeof(int), 16);
+    if (cudaMalloc(&p.d_tables, p.tables_bytes) != cudaSuccess) return LADDER_ERR_CUDA;
+    if (!host.empty() &&
+        cudaMemcpy(p.d_tables, host.data(), host.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+        return LADDER_ERR_CUDA;
+    return LADDER_OK;
+}
+
+int apply_blocking(ladder_plan_s& p, int na, int nb) {
+    std::vector<BlockPair> bps = enumerate_blocks(p.nv, na, nb);
+    const ladder::WsLayout w = layout_for(p, max_pairs_of(bps));
+    if (w.total > p.budget) return LADDER_ERR_BUDGET;
+    p.n_a = na;
+    p.n_b = nb;
+    p.bps = std::move(bps);
+    p.max_pairs = (int)max_pairs_of(p.bps);
+    p.ws = w;
+    return build_tables(p);
+}
+
+int select_blocking(const ladder_plan_s& p, int* out_na, int* out_nb) {
+    std::vector<int> cand;
+    for (int k = 1; k <= p.nv; ++k) {
+        const int n = (p.nv + k - 1) / k;
+        if (cand.empty() || cand.back() != n) cand.push_back(n);
+    }
+    // Candidate (n_a, n_b) ordered by the number of block pairs: the model time
+    // grows with it, so the best feasible blocking is among the first feasible ones.
+    struct Combo { double nbp; int na, nb; };
+    std::vector<Combo> combos;
+    for (int na : cand)
+        for (int nb : cand) combos.push_back({std::ceil((double)p.nv / na) * std::ceil((double)p.nv / nb), na, nb});
+    std::stable_sort(combos.begin(), combos.end(), [](const Combo& x, const Combo& y) { return x.nbp < y.nbp; });
+    double best = 1e300;
+    int bna = 0, bnb = 0, evaluated = 0;
+    for (const Combo& c : combos) {
+        std::vector<BlockPair> bps = enumerate_blocks(p.nv, c.na, c.nb);
+        if (layout_for(p, max_pairs_of(bps)).total > p.budget) continue;
+        const double t = model_time(p, bps);
+        if (t < best * (1 - 1e-9)) {
+            best = t;
+            bna = c.na;
+            bnb = c.nb;
+        }
+        if (++evaluated >= 64) break;
+    }
+    if (bna == 0) return LADDER_ERR_BUDGET;
+    *out_na = bna;
+    *out_nb = bnb;
+    return LADDER_OK;
+}
+
+int choose_blocking(ladder_plan_s& p) {
+    int na = 0, nb = 0;
+    const int rc = select_blocking(p, &na, &nb);
+    if (rc != LADDER_OK) return rc;
+    return apply_blocking(p, na, nb);
+}
+
+bool aligned256(const void* ptr) { return (reinterpret_cast<uintptr_t>(ptr) & 255u) == 0; }
+
+void free_events(ladder_plan_s* p) {
+    for (auto e : p->ev_pool) cudaEventDestroy(e);
+    p->ev_pool.clear();
+    p->ev_kind.clear();
+    p->ev_used = 0;
+    p->timing = false;
+}
+
+void destroy_plan(ladder_plan_s* p) {
+    if (!p) return;
+    for (auto* s : p->sub) destroy_plan(s);
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != p->device) cudaSetDevice(p->device);
+    free_events(p);
+    if (p->d_tables) cudaFree(p->d_tables);
+    if (p->d_status) cudaFree(p->d_status);
+    if (p->d_partials) cudaFree(p->d_partials);
+    if (cur >= 0 && cur != p->device) cudaSetDevice(cur);
+    delete p;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int make_plan(ladder_plan_s** out, int no, int nv, int nchol, int precision, int nslices, size_t budget,
+              int device) {
+    *out = nullptr;
+    if (no < 1 || nv < 1 || nchol < 1) return LADDER_ERR_ARG;
+    if ((long long)no * no > (1 << 20) || nv > 4096) return LADDER_ERR_ARG;
+    if (precision == LADDER_EMU_INT8) return LADDER_ERR_UNSUPPORTED;
+    if (precision != LADDER_FP64 && precision != LADDER_EMU_BF16) return LADDER_ERR_ARG;
+    if (nslices == 0) nslices = ladder::kDefaultSlices;
+    if (precision == LADDER_EMU_BF16) {
+        if (nslices < 3 || nslices > 8) return LADDER_ERR_ARG;
+        if (!ladder::emu_supported(no, nv, nchol, nslices)) return LADDER_ERR_UNSUPPORTED;
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess) return LADDER_ERR_CUDA;
+    if (device < 0 || device >= ndev) return LADDER_ERR_ARG;
+    DeviceGuard guard(device);
+    if (!guard.ok) return LADDER_ERR_CUDA;
+    auto* p = new (std::nothrow) ladder_plan_s();
+    if (!p) return LADDER_ERR_CUDA;
+    p->no = no;
+    p->nv = nv;
+    p->nchol = nchol;
+    p->precision = precision;
+    p->nslices = precision == LADDER_FP64 ? 0 : nslices;
+    p->device = device;
+    if (cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+        destroy_plan(p);
+        return LADDER_ERR_CUDA;
+    }
+    if (budget == 0) {
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+            destroy_plan(p);
+            return LADDER_ERR_CUDA;
+        }
+        budget = (size_t)((double)free_b * 0.98 * 0.9);
+    }
+    p->budget = budget;
+    int rc = choose_blocking(*p);
+    if (rc == LADDER_OK) {
+        if (cudaMalloc(&p->d_status, sizeof(unsigned)) != cudaSuccess ||
+            cudaMemset(p->d_status, 0, sizeof(unsigned)) != cudaSuccess)
+            rc = LADDER_ERR_CUDA;
+    }
+    if (rc == LADDER_OK) {
+        const long long ntile = (nv + 31) / 32;
+        const long long units = (long long)no * no * ntile * ntile;
+        p->n_partials = (int)std::max<long long>(1, std::min<long long>(units, 4LL * p->num_sms));
+        if (cudaMalloc(&p->d_partials, sizeof(double) * (p->n_partials + 1)) != cudaSuccess) rc = LADDER_ERR_CUDA;
+    }
+    if (rc != LADDER_OK) {
+        destroy_plan(p);
+        return rc;
+    }
+    *out = p;
+    return LADDER_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ladder_plan(ladder_plan_t* out, int no, int nv, int nchol, int precision, int nslices,
+                size_t ws_budget_bytes, int device) {
+    if (!out) return LADDER_ERR_ARG;
+    return make_plan(out, no, nv, nchol, precision, nslices, ws_budget_bytes, device);
+}
+
+int ladder_plan_set_blocks(ladder_plan_t plan, int n_a, int n_b) {
+    if (!plan || plan->batched) return LADDER_ERR_ARG;
+    if (n_a < 1 || n_b < 1 || n_a > plan->nv || n_b > plan->nv) return LADDER_ERR_ARG;
+    DeviceGuard guard(plan->device);
+    if (!guard.ok) return LADDER_ERR_CUDA;
+    // Validate before touching the plan so a rejected request leaves it intact.
+    std::vector<BlockPair> bps = enumerate_blocks(plan->nv, n_a, n_b);
+    if (layout_for(*plan, max_pairs_of(bps)).total > plan->budget) return LADDER_ERR_BUDGET;
+    return apply_blocking(*plan, n_a, n_b);
+}
+
+size_t ladder_workspace_bytes(ladder_plan_t plan) {
+    if (!plan) return 0;
+    return plan->ws.total;
+}
+
+int ladder_plan_describe(ladder_plan_t plan, int* n_a, int* n_b, int* n_block_pairs, int* max_pairs_per_block,
+                         int* nslices, int* precision) {
+    if (!plan) return LADDER_ERR_ARG;
+    if (n_a) *n_a = plan->n_a;
+    if (n_b) *n_b = plan->n_b;
+    if (n_block_pairs) *n_block_pairs = (int)plan->bps.size();
+    if (max_pairs_per_block) *max_pairs_per_block = plan->max_pairs;
+    if (nslices) *nslices = plan->nslices;
+    if (precision) *precision = plan->precision;
+    return LADDER_OK;
+}
+
+int ladder_apply(ladder_plan_t plan, const double* L, const double* t2, double* R, void* ws,
+                 cudaStream_t stream) {
+    if (!plan || plan->batched || !L || !t2 || !R || !ws) return LADDER_ERR_ARG;
+    if (!aligned256(L) || !aligned256(t2) || !aligned256(R) || !aligned256(ws)) return LADDER_ERR_ARG;
+    DeviceGuard guard(plan->device);
+    if (!guard.ok) return LADDER_ERR_CUDA;
+    cudaError_t e = cudaSuccess;
+    if (plan->precision == LADDER_FP64) {
+        for (const auto& bp : plan->bps) {
+            e = ladder::launch_fp64_block(*plan, bp, L, t2, R, ws, stream);
+            if (e != cudaSuccess) break;
+        }
+    } else {
+        e = ladder::launch_emu_prep(*plan, L, t2, ws, stream);
+        if (e == cudaSuccess) {
+            for (const auto& bp : plan->bps) {
+                e = ladder::launch_emu_block(*plan, bp, R, ws, stream);
+                if (e != cudaSuccess) break;
+            }
+        }
+    }
+    return map_cuda(e);
+}
+
+int ladder_energy(ladder_plan_t plan, const double* t2, const double* R, double* E_dev, double* E_host,
+                  cudaStream_t stream) {
+    if (!plan || plan->batched || !t2 || !R || (!E_dev && !E_host)) return LADDER_ERR_ARG;
+    if (!aligned256(t2) || !aligned256(R)) return LADDER_ERR_ARG;
+    DeviceGuard guard(plan->device);
+    if (!guard.ok) return LADDER_ERR_CUDA;
+    double* target = E_dev ? E_dev : plan->d_partials + plan->n_partials;
+    cudaError_t e = ladder::launch_energy(*plan, t2, R, target, stream);
+    if (e != cudaSuccess) return LADDER_ERR_CUDA;
+    if (E_host) {
+        e = cudaMemcpyAsync(E_host, target, sizeof(double), cudaMemcpyDeviceToHost, stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+        if (e != cudaSuccess) return LADDER_ERR_CUDA;
+    }
+    return LADDER_OK;
+}
+
+int ladder_plan_batched(ladder_plan_t* out, int n, const int* no, const int* nv, const int* nchol, int precision,
+                        int nslices, size_t ws_budget_bytes, int device) {
+    if (!out) return LADDER_ERR_ARG;
+    *out = nullptr;
+    if (n < 1 || !no || !nv || !nchol) return LADDER_ERR_ARG;
+    auto* p = new (std::nothrow) ladder_plan_s();
+    if (!p) return LADDER_ERR_CUDA;
+    p->batched = true;
+    p->precision = precision;
+    p->device = device;
+    size_t ws = ladder::kAlign;
+    for (int k = 0; k < n; ++k) {
+        ladder_plan_s* s = nullptr;
+        const int rc = make_plan(&s, no[k], nv[k], nchol[k], precision, nslices, ws_budget_bytes, device);
+        if (rc != LADDER_OK) {
+            destroy_plan(p);
+            return rc;
+        }
+        p->sub.push_back(s);
+        ws = std::max(ws, s->ws.total);
+    }
+    p->ws.total = ws;
+    p->nslices = p->sub[0]->nslices;
+    DeviceGuard guard(device);
+    if (cudaMalloc(&p->d_status, sizeof(unsigned)) != cudaSuccess ||
+        cudaMemset(p->d_status, 0, sizeof(unsigned)) != cudaSuccess) {
+        destroy_plan(p);
+        return LADDER_ERR_CUDA;
+    }
+    *out = p;
+    return LADDER_OK;
+}
+
+int ladder_apply_batched(ladder_plan_t plan, const double* const* L, const double* const* t2, double* const* R,
+                         void* ws, cudaStream_t stream) {
+    if (!plan || !plan->batched || !L || !t2 || !R || !ws) return LADDER_ERR_ARG;
+    for (size_t k = 0; k < plan->sub.size(); ++k) {
+        const int rc = ladder_apply(plan->sub[k], L[k], t2[k], R[k], ws, stream);
+        if (rc != LADDER_OK) return rc;
+    }
+    return LADDER_OK;
+}
+
+int ladder_plan_set_timing(ladder_plan_t plan, int enable) {
+    if (!plan) return LADDER_ERR_ARG;
+    DeviceGuard guard(plan->device);
+    std::vector<ladder_plan_s*> all{plan};
+    for (auto* s : plan->sub) all.push_back(s);
+    for (auto* q : all) {
+        free_events(q);
+        if (!enable) continue;
+        const size_t slots = 64 * (q->bps.size() + 8);
+        q->ev_pool.resize(2 * slots);
+        q->ev_kind.assign(slots, -1);
+        for (auto& e : q->ev_pool)
+            if (cudaEventCreate(&e) != cudaSuccess) {
+                free_events(q);
+                return LADDER_ERR_CUDA;
+            }
+        q->timing = true;
+    }
+    return LADDER_OK;
+}
+
+int ladder_plan_timing(ladder_plan_t plan, int kernel_class, float* total_ms, int* launches, int reset) {
+    if (!plan || kernel_class < 0 || kernel_class >= LADDER_KERNEL_CLASSES) return LADDER_ERR_ARG;
+    DeviceGuard guard(plan->device);
+    std::vector<ladder_plan_s*> all{plan};
+    for (auto* s : plan->sub) all.push_back(s);
+    float sum = 0.0f;
+    int n = 0;
+    for (auto* q : all) {
+        for (size_t k = 0; k < q->ev_used; ++k) {
+            if (q->ev_kind[k] != kernel_class) continue;
+            if (cudaEventSynchronize(q->ev_pool[2 * k + 1]) != cudaSuccess) return LADDER_ERR_CUDA;
+            float ms = 0.0f;
+            if (cudaEventElapsedTime(&ms, q->ev_pool[2 * k], q->ev_pool[2 * k + 1]) != cudaSuccess)
+                return LADDER_ERR_CUDA;
+            sum += ms;
+            ++n;
+        }
+        if (reset) q->ev_used = 0;
+    }
+    if (total_ms) *total_ms = sum;
+    if (launches) *launches = n;
+    return LADDER_OK;
+}
+
+int ladder_last_status(ladder_plan_t plan, cudaStream_t stream) {
+    if (!plan) return LADDER_ERR_ARG;
+    DeviceGuard guard(plan->device);
+    unsigned word = 0;
+    std::vector<ladder_plan_s*> all{plan};
+    for (auto* s : plan->sub) all.push_back(s);
+    for (auto* q : all) {
+        if (!q->d_status) continue;
+        unsigned w = 0;
+        if (cudaMemcpyAsync(&w, q->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+            cudaStreamSynchronize(stream) != cudaSuccess ||
+            cudaMemsetAsync(q->d_status, 0, sizeof(unsigned), stream) != cudaSuccess)
+            return LADDER_ERR_CUDA;
+        word |= w;
+    }
+    if (word & ladder::kStatusTimeout) return LADDER_ERR_TIMEOUT;
+    if (word & ladder::kStatusNumeric) return LADDER_ERR_NUMERIC;
+    return LADDER_OK;
+}
+
+void ladder_plan_destroy(ladder_plan_t plan) { destroy_plan(plan); }
+
+int ladder_plan_dry(int no, int nv, int nchol, int precision, int nslices, size_t ws_budget_bytes, int num_sms,
+                    int force_n_a, int force_n_b, int* n_a, int* n_b, size_t* ws_bytes, int max_blocks,
+                    int* n_block_pairs, int* blocks) {
+    if (no < 1 || nv < 1 || nchol < 1 || num_sms < 1 || ws_budget_bytes == 0) return LADDER_ERR_ARG;
+    if (precision == LADDER_EMU_INT8) return LADDER_ERR_UNSUPPORTED;
+    if (precision != LADDER_FP64 && precision != LADDER_EMU_BF16) return LADDER_ERR_ARG;
+    if (nslices == 0) nslices = ladder::kDefaultSlices;
+    if (precision == LADDER_EMU_BF16 && (nslices < 3 || nslices > 8)) return LADDER_ERR_ARG;
+    ladder_plan_s p;
+    p.no = no;
+    p.nv = nv;
+    p.nchol = nchol;
+    p.precision = precision;
+    p.nslices = precision == LADDER_FP64 ? 0 : nslices;
+    p.num_sms = num_sms;
+    p.budget = ws_budget_bytes;
+    int na = force_n_a, nb = force_n_b;
+    if (na <= 0 || nb <= 0) {
+        const int rc = select_blocking(p, &na, &nb);
+        if (rc != LADDER_OK) return rc;
+    } else if (na > nv || nb > nv) {
+        return LADDER_ERR_ARG;
+    }
+    const std::vector<BlockPair> bps = enumerate_blocks(nv, na, nb);
+    const ladder::WsLayout w = layout_for(p, max_pairs_of(bps));
+    if (w.total > p.budget) return LADDER_ERR_BUDGET;
+    if (n_a) *n_a = na;
+    if (n_b) *n_b = nb;
+    if (ws_bytes) *ws_bytes = w.total;
+    if (n_block_pairs) *n_block_pairs = (int)bps.size();
+    if (blocks) {
+        for (int k = 0; k < (int)bps.size() && k < max_blocks; ++k) {
+            blocks[5 * k + 0] = bps[k].a0;
+            blocks[5 * k + 1] = bps[k].a1;
+            blocks[5 * k + 2] = bps[k].b0;
+            blocks[5 * k + 3] = bps[k].b1;
+            blocks[5 * k + 4] = bps[k].npairs;
+        }
+    }
+    return LADDER_OK;
+}
+
+const char* ladder_strerror(int status) {
+    switch (status) {
+        case LADDER_OK: return "ok";
+        case LADDER_ERR_ARG: return "invalid argument (size, alignment or null pointer)";
+        case LADDER_ERR_BUDGET: return "no a/b blocking fits the workspace budget";
+        case LADDER_ERR_CUDA: return "CUDA runtime error";
+        case LADDER_ERR_UNSUPPORTED: return "unsupported configuration";
+        case LADDER_ERR_TIMEOUT: return "a kernel's bounded wait timed out";
+        case LADDER_ERR_NUMERIC: return "a kernel consistency check failed";
+        default: return "unknown status";
+    }
+}
+
+double ladder_flops(int no, int nv, int nchol) {
+    const double p = 0.5 * (double)nv * (nv + 1);
+    const double nv2 = (double)nv * nv;
+    return 2.0 * nchol * nv2 * p + 2.0 * (double)no * no * nv2 * p;
+}
+
+}  // extern "C"

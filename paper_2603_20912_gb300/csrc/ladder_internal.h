@@ -1,0 +1,115 @@
+// Internal definitions shared by the host-side runtime (planner, C ABI) and
+// the kernel translation units.  Not part of the public interface.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/ladder.h"
+
+namespace ladder {
+
+constexpr int kAlign = 256;                 // workspace sub-buffer alignment (bytes)
+constexpr int kDefaultSlices = 6;           // digit slices per operand (emulated path)
+constexpr int kDigitBits = 7;               // bits per signed digit, |digit| <= 64
+constexpr int kExpGroupRows = 64;           // rows sharing one power-of-two exponent
+constexpr int kEmuMaxExactK = 1365;         // K per exact accumulation chunk: 3 * 64^2 * K <= 2^24
+constexpr int kEmuChunkK = 1280;            // ladder K chunk (multiple of 64, <= kEmuMaxExactK)
+
+// Device status bits (ORed into the plan's status word by kernels).
+constexpr unsigned kStatusTimeout = 1u;
+constexpr unsigned kStatusNumeric = 2u;
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// One (A, B) block pair of the packed (a <= b) pair space: a in [a0, a1),
+// b in [b0, b1).  Its valid pairs are numbered a-major, b-minor, skipping a > b.
+struct BlockPair {
+    int a0, a1, b0, b1;
+    int npairs;        // number of (a, b) with a <= b in the block pair
+    size_t pairs_off;  // offset (in int2) of this block pair's pair list in the device table
+    size_t rows_off;   // offset (in int) of this block pair's row_start table (a1 - a0 + 1 ints)
+};
+
+// Workspace layout of one plan (byte offsets from the workspace base).
+struct WsLayout {
+    size_t v_blk = 0;      // FP64: V block [max_pairs][nv*nv] f64; EMU: V slices [S][max_pairs][kpad] bf16
+    size_t rp_int = 0;     // EMU: int64 fixed-point ladder accumulator [max_pairs][no*no]
+    size_t lt_slices = 0;  // EMU: L^T slices [S][nv*nv][xpad] bf16
+    size_t lt_exp = 0;     // EMU: exponent per group of L^T rows (int)
+    size_t t_slices = 0;   // EMU: T slices [S][no*no][kpad] bf16
+    size_t t_exp = 0;      // EMU: exponent per group of T rows (int)
+    size_t v_exp = 0;      // EMU: exponent bound per (a, b) pair [nv][nv] (int)
+    size_t lnorm = 0;      // EMU: max_c ||L[:, a, c]||_2 per a (double)
+    size_t total = 0;
+};
+
+struct TensorMaps;  // TMA descriptors (emulated path), defined in emu_kernels.cu
+
+}  // namespace ladder
+
+struct ladder_plan_s {
+    int no = 0, nv = 0, nchol = 0;
+    int precision = LADDER_FP64;
+    int nslices = ladder::kDefaultSlices;
+    int device = 0;
+    int num_sms = 0;
+    size_t budget = 0;
+    int n_a = 0, n_b = 0;
+    std::vector<ladder::BlockPair> bps;
+    int max_pairs = 0;
+    ladder::WsLayout ws;
+    // Device-side tables (allocated at plan time).
+    void* d_tables = nullptr;          // pair lists (int2) + row_start tables (int)
+    size_t tables_bytes = 0;
+    unsigned* d_status = nullptr;      // status word
+    double* d_partials = nullptr;      // energy reduction partials
+    int n_partials = 0;
+    // Optional per-kernel timing (benchmarks): event pairs tagged by kernel class.
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<int> ev_kind;
+    size_t ev_used = 0;
+    // Batched plans: sub-plans per instance.
+    std::vector<ladder_plan_s*> sub;
+    bool batched = false;
+};
+
+namespace ladder {
+
+// Records an event pair around one launch when the plan has timing enabled.
+struct LaunchTimer {
+    ladder_plan_s& p;
+    cudaStream_t s;
+    int kind;
+    long slot = -1;
+    LaunchTimer(const ladder_plan_s& plan, cudaStream_t stream, int k)
+        : p(const_cast<ladder_plan_s&>(plan)), s(stream), kind(k) {
+        if (p.timing && 2 * (p.ev_used + 1) <= p.ev_pool.size()) {
+            slot = (long)p.ev_used++;
+            p.ev_kind[slot] = kind;
+            cudaEventRecord(p.ev_pool[2 * slot], s);
+        }
+    }
+    ~LaunchTimer() {
+        if (slot >= 0) cudaEventRecord(p.ev_pool[2 * slot + 1], s);
+    }
+};
+
+// fp64_kernels.cu
+cudaError_t launch_fp64_block(const ladder_plan_s& p, const BlockPair& bp, const double* L,
+                              const double* t2, double* R, void* ws, cudaStream_t s);
+// energy.cu
+cudaError_t launch_energy(const ladder_plan_s& p, const double* t2, const double* R, double* E_dev,
+                          cudaStream_t s);
+// emu_kernels.cu
+cudaError_t launch_emu_prep(const ladder_plan_s& p, const double* L, const double* t2, void* ws,
+                            cudaStream_t s);
+cudaError_t launch_emu_block(const ladder_plan_s& p, const BlockPair& bp, double* R, void* ws,
+                             cudaStream_t s);
+bool emu_supported(int no, int nv, int nchol, int nslices);
+
+}  // namespace ladder
