@@ -33,7 +33,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from ladder_inputs import CONFIGS, make_inputs  # noqa: E402
+from ladder_inputs import CONFIGS, LadderShape, make_inputs  # noqa: E402
 
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
@@ -248,6 +248,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--config", default="c2", choices=sorted(CONFIGS))
+    ap.add_argument("--shape", default=None, help="no,nv,nchol overriding --config (profiling runs)")
     ap.add_argument("--precision", default="emu", choices=["emu", "fp64"])
     ap.add_argument("--nslices", type=int, default=0)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -260,6 +261,9 @@ def main():
         measure_peaks()
         return
     cfg = CONFIGS[args.config]
+    if args.shape:
+        no, nv, nchol = (int(x) for x in args.shape.split(","))
+        cfg = LadderShape(no=no, nv=nv, nchol=nchol, seed=4242, name="custom")
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
