@@ -1,0 +1,149 @@
+"""Exact-arithmetic CPU model of the emulated-FP64 ladder (test infrastructure).
+
+It restates, in numpy integer arithmetic, the digit-slice scheme that the
+CUDA kernels implement, so that tests can (1) check the scheme's error on
+small shapes against the FP64 oracle, and (2) pin properties the GPU must
+reproduce (integer grids are exact).  It is not the oracle: the oracle is
+the plain FP64 definition in ``oracle/``.
+
+Scheme (FP64 emulated by BF16 digit slices, Ozaki-style splitting):
+
+* Row groups of G consecutive rows share one exponent e with
+  max|x| < 2^(e-1), so u = x 2^-e lies in (-1/2, 1/2).
+* N = round_half_even(x 2^(7S - e)) (|N| <= 2^(7S-1)) is written in
+  balanced base 128: N = sum_s d_s 128^(S-s), |d_s| <= 64.  Slice plane s
+  holds d_s 2^(-7s) (exact in BF16: 7 significant bits).
+* A product sum over K of two sliced operands keeps the pairs s + t <= S + 1.
+  Levels l = s + t = 2, 3, 4 are exact integers while K * (l-1) * 64^2
+  <= 2^24 (K <= 1365): they accumulate in separate FP32 accumulators; the
+  levels >= 5 share a fourth FP32 accumulator (inexact, weight <= 2^-35).
+* ERI (K = nchol): the level sums form I = acc2 2^35 + acc3 2^28 + acc4 2^21
+  + round(A5 2^49), V = 2^(e_ac + e_bd - 49) I.  V is re-sliced per pair row
+  (a, b) with the exponent f_ab of the Cauchy-Schwarz bound
+  |(ac|bd)| <= max_c ||L_ac|| max_d ||L_bd||.
+* Ladder (K = nv^2, chunks of 1280): per chunk J = acc2 2^28 + acc3 2^21
+  + acc4 2^14 + round(A5 2^42), summed exactly over chunks in int64;
+  R_ij^ab = 2^(f_ab + g_ij - 42) sum J.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+DIGIT_BITS = 7
+GROUP = 64
+CHUNK = 1280
+
+
+def group_exponents(x2d: np.ndarray, group: int = GROUP) -> np.ndarray:
+    """e per group of `group` rows: smallest e with max|x| < 2^(e-1) (0 for an all-zero group)."""
+    rows = x2d.shape[0]
+    ng = (rows + group - 1) // group
+    e = np.zeros(ng, dtype=np.int64)
+    for g in range(ng):
+        m = float(np.max(np.abs(x2d[g * group:(g + 1) * group]))) if x2d.size else 0.0
+        if m > 0.0:
+            e[g] = math.frexp(m)[1] + 1
+    return e
+
+
+def to_digits(x2d: np.ndarray, S: int, group: int = GROUP):
+    """(digits [S, rows, K] int64, row exponent [rows] int64)."""
+    e = group_exponents(x2d, group)
+    erow = np.repeat(e, group)[: x2d.shape[0]]
+    scaled = np.ldexp(x2d, (DIGIT_BITS * S - erow)[:, None])
+    N = np.rint(scaled).astype(np.int64)
+    d = np.zeros((S,) + x2d.shape, dtype=np.int64)
+    for s in range(S - 1, 0, -1):
+        low = ((N + 64) & 127) - 64
+        d[s] = low
+        N = (N - low) >> 7
+    d[0] = N
+    return d, erow
+
+
+def from_digits(d: np.ndarray, erow: np.ndarray) -> np.ndarray:
+    S = d.shape[0]
+    v = np.zeros(d.shape[1:])
+    for s in range(S):
+        v += np.ldexp(d[s].astype(np.float64), (erow - DIGIT_BITS * (s + 1))[:, None])
+    return v
+
+
+def level_sums(dA: np.ndarray, dB: np.ndarray):
+    """Exact integer level sums acc2, acc3, acc4 and the weighted tail A5 (float64) of
+    sum_k A[m,k] B[n,k] over slice pairs s + t <= S + 1 (s, t 1-based)."""
+    S = dA.shape[0]
+    acc = {2: 0, 3: 0, 4: 0}
+    a5 = 0.0
+    for s in range(1, S + 1):
+        for t in range(1, S + 2 - s):
+            prod = dA[s - 1] @ dB[t - 1].T
+            lvl = s + t
+            if lvl <= 4:
+                acc[lvl] = acc[lvl] + prod
+            else:
+                a5 = a5 + np.ldexp(prod.astype(np.float64), -DIGIT_BITS * lvl)
+    z = np.zeros((dA.shape[1], dB.shape[1]), dtype=np.int64)
+    return (acc[2] if not np.isscalar(acc[2]) else z, acc[3] if not np.isscalar(acc[3]) else z,
+            acc[4] if not np.isscalar(acc[4]) else z, a5 if not np.isscalar(a5) else np.zeros(z.shape))
+
+
+def _round_shift(I: np.ndarray, sh: np.ndarray) -> np.ndarray:
+    """round(I / 2^sh), halves up; sh <= 0 shifts left."""
+    out = np.empty_like(I)
+    pos = sh > 0
+    shp = np.where(pos, sh, 1)
+    out[pos] = ((I + (np.int64(1) << (shp - 1))) >> shp)[pos]
+    out[~pos] = (I << np.where(pos, 0, -sh))[~pos]
+    return out
+
+
+def pair_exponent_bound(L: np.ndarray) -> np.ndarray:
+    """f[a, b] with max_c||L_ac|| max_d||L_bd|| (1 + 2^-20) < 2^(f-1)."""
+    nchol, nv, _ = L.shape
+    norms = np.sqrt(np.sum(L * L, axis=0))           # [a, c] = ||L[:, a, c]||
+    na = norms.max(axis=1)
+    f = np.zeros((nv, nv), dtype=np.int64)
+    for a in range(nv):
+        for b in range(nv):
+            B = na[a] * na[b] * (1.0 + 2.0 ** -20)
+            f[a, b] = math.frexp(B)[1] + 1 if B > 0 else 0
+    return f
+
+
+def emulated_ladder(L: np.ndarray, t2: np.ndarray, S: int = 6, group: int = GROUP, chunk: int = CHUNK):
+    """R = ladder(L, t2) through the emulation scheme (all pairs, no a <= b packing)."""
+    nchol, nv, _ = L.shape
+    no = t2.shape[0]
+    assert nchol <= 1365
+    Lt = np.ascontiguousarray(L.reshape(nchol, nv * nv).T)     # rows (a, c), K = P
+    dL, eL = to_digits(Lt, S, group)
+    a2, a3, a4, a5 = level_sums(dL, dL)                          # [(ac), (bd)]
+    I = (a2 << 35) + (a3 << 28) + (a4 << 21) + np.rint(np.ldexp(a5, 49)).astype(np.int64)
+    f = pair_exponent_bound(L)
+    # rows (a, c), cols (b, d) -> V[(a, b), (c, d)]
+    I4 = I.reshape(nv, nv, nv, nv).transpose(0, 2, 1, 3)          # [a, b, c, d]
+    e4 = eL.reshape(nv, nv)                                      # e_ac
+    sh = f[:, :, None, None] - e4[:, None, :, None] - e4[None, :, None, :] + 49 - DIGIT_BITS * S
+    Np = _round_shift(I4, sh).reshape(nv * nv, nv * nv)          # rows (a, b), K = (c, d)
+    assert np.all(np.abs(Np) <= (1 << (DIGIT_BITS * S - 1)))
+    dV = np.zeros((S,) + Np.shape, dtype=np.int64)
+    M = Np.copy()
+    for s in range(S - 1, 0, -1):
+        low = ((M + 64) & 127) - 64
+        dV[s] = low
+        M = (M - low) >> 7
+    dV[0] = M
+    T = t2.reshape(no * no, nv * nv)
+    dT, eT = to_digits(T, S, group)
+    K = nv * nv
+    J = np.zeros((nv * nv, no * no), dtype=np.int64)
+    for k0 in range(0, K, chunk):
+        sl = slice(k0, min(K, k0 + chunk))
+        b2, b3, b4, b5 = level_sums(dV[:, :, sl], dT[:, :, sl])
+        J += (b2 << 28) + (b3 << 21) + (b4 << 14) + np.rint(np.ldexp(b5, 42)).astype(np.int64)
+    fab = f.reshape(nv * nv)
+    Rp = np.ldexp(J.astype(np.float64), fab[:, None] + eT[None, :] - 42)   # [(a, b), (i, j)]
+    return Rp.T.reshape(no, no, nv, nv)
