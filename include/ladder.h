@@ -189,6 +189,37 @@ int ladder_plan_timing(ladder_plan_t plan, int kernel_class, float* total_ms, in
  * or LADDER_ERR_NUMERIC.  Synchronises the stream. */
 int ladder_last_status(ladder_plan_t plan, cudaStream_t stream);
 
+/*
+ * ladder_energy_noalloc -- E_L exactly as ladder_energy defines it, for
+ * callers that cannot allocate device memory.  The paper has no counterpart
+ * to this entry point.
+ *
+ * Who needs it: code that runs while a stream is being captured into a CUDA
+ * graph (allocation cannot be captured), frameworks that own all device
+ * memory through their own pool and forbid other allocators, and loops that
+ * must not take the allocator's locks.  It needs no plan and no workspace
+ * and calls no cudaMalloc, cudaFree or allocating library routine.
+ *
+ *   no, nv  orbital counts (>= 1); t2, R device [no][no][nv][nv] float64 on
+ *           the current device; E_dev device double receiving E_L.
+ *   stream  CUDA stream; the call enqueues two kernels and does not wait.
+ *
+ * Scratch: a 128 KiB file-scope device array (LADDER_NOALLOC_MAX_PARTIALS
+ * doubles) that every device loading the library holds until the process
+ * exits.  One partial sum per 64 tiles of 32 x 32 (a, b) elements, so the
+ * call rejects, with LADDER_ERR_ARG and before launching anything, shapes
+ * with ceil(no^2 ceil(nv/32)^2 / 64) > LADDER_NOALLOC_MAX_PARTIALS.
+ * The first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture.  All calls
+ * share the one array: calls whose kernels may overlap on the GPU (other
+ * streams, other threads) race and return wrong values -- order them.
+ * Every partial is rewritten by each call, so nothing is cleared in between.
+ * Returns LADDER_OK, LADDER_ERR_ARG or LADDER_ERR_CUDA.
+ */
+#define LADDER_NOALLOC_MAX_PARTIALS 16384
+int ladder_energy_noalloc(int no, int nv, const double* t2, const double* R, double* E_dev,
+                          cudaStream_t stream);
+
 /* Release a plan (NULL is ignored).  Frees the plan's device table. */
 void ladder_plan_destroy(ladder_plan_t plan);
 

@@ -86,6 +86,8 @@ def _load():
     lib.ladder_plan_set_timing.restype = ci
     lib.ladder_plan_timing.argtypes = [vp, ci, ctypes.POINTER(ctypes.c_float), pint, ci]
     lib.ladder_plan_timing.restype = ci
+    lib.ladder_energy_noalloc.argtypes = [ci, ci, vp, vp, vp, vp]
+    lib.ladder_energy_noalloc.restype = ci
     lib.ladder_flops.argtypes = [ci, ci, ci]
     lib.ladder_flops.restype = ctypes.c_double
     _lib = lib
@@ -255,6 +257,19 @@ def ladder_apply_batched(plan: Plan, Ls, t2s, Rs, ws=None, stream=None):
     return Rs
 
 
+def ladder_energy_noalloc(t2, R, E_dev, stream=None):
+    """E_L into the device scalar E_dev without a plan and without any allocation.
+
+    For callers that cannot allocate device memory (e.g. while a stream is being
+    captured into a CUDA graph).  The scratch is a fixed 128 KiB device array inside
+    the library, shared by every call: calls that may overlap on the GPU must be
+    ordered.  The first call on a device should come before any stream capture."""
+    no, _, nv, _ = t2.shape
+    _check(_load().ladder_energy_noalloc(int(no), int(nv), _dev_ptr(t2, "t2"), _dev_ptr(R, "R"),
+                                         _dev_ptr(E_dev, "E_dev"), _stream_handle(stream)), "ladder_energy_noalloc")
+    return E_dev
+
+
 def ladder_last_status(plan: Plan, stream=None) -> int:
     return plan.last_status(stream)
 
@@ -267,4 +282,5 @@ EXPORTED_SYMBOLS = [
     "ladder_plan", "ladder_plan_set_blocks", "ladder_workspace_bytes", "ladder_plan_describe", "ladder_apply",
     "ladder_energy", "ladder_plan_batched", "ladder_apply_batched", "ladder_last_status", "ladder_plan_destroy",
     "ladder_strerror", "ladder_flops", "ladder_plan_dry", "ladder_plan_set_timing", "ladder_plan_timing",
+    "ladder_energy_noalloc",
 ]
