@@ -78,7 +78,7 @@ enum {
  *   nchol      number of Cholesky vectors (>= 1).
  *   precision  LADDER_FP64 or LADDER_EMU_BF16.
  *   nslices    digit slices per operand for the emulated path, 0 = default (6);
- *              ignored for LADDER_FP64.  Valid range 3..8.
+ *              ignored for LADDER_FP64.  Valid range 4..8.
  *   ws_budget_bytes  workspace budget; 0 = 0.9 * 0.98 * free device memory
  *              (the safety factors of the paper's C-split rule).
  *   device     CUDA device ordinal.

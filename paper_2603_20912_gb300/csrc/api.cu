@@ -115,6 +115,7 @@ ladder::WsLayout layout_for(const ladder_plan_s& p, long long max_pairs) {
         w.lt_slices = take(S * nv2 * xpad * 2);
         w.lt_exp = take(((nv2 + ladder::kExpGroupRows - 1) / ladder::kExpGroupRows) * 4);
         w.t_slices = take(S * no2 * kpad * 2);
+        w.t_gmax = take(((no2 + ladder::kExpGroupRows - 1) / ladder::kExpGroupRows) * 8);
         w.t_exp = take(((no2 + ladder::kExpGroupRows - 1) / ladder::kExpGroupRows) * 4);
         w.v_exp = take(nv2 * 4);
         w.lnorm = take((size_t)p.nv * 8);
@@ -146,9 +147,36 @@ double model_time(const ladder_plan_s& p, const std::vector<BlockPair>& bps) {
 
 // Build device tables for the chosen blocking: per block pair its pair list
 // (int2 (a, b), a-major) and row_start (first packed row of each a).
+// ERI tiles (rt, qt) of one block pair that hold at least one a <= b, in an
+// L2-friendly order: bands of 8 row tiles, all column tiles of a band, then the next band.
+std::vector<int> eri_tiles(const BlockPair& bp, int nv, int tile) {
+    std::vector<int> out;
+    const long long M = (long long)(bp.a1 - bp.a0) * nv, N = (long long)(bp.b1 - bp.b0) * nv;
+    const int nrt = (int)((M + tile - 1) / tile), nqt = (int)((N + tile - 1) / tile);
+    const int band = 8;
+    for (int r0 = 0; r0 < nrt; r0 += band)
+        for (int qt = 0; qt < nqt; ++qt)
+            for (int rt = r0; rt < std::min(nrt, r0 + band); ++rt) {
+                const int a_min = bp.a0 + (int)((long long)rt * tile / nv);
+                const long long last = std::min((long long)(qt + 1) * tile, N) - 1;
+                const int b_max = bp.b0 + (int)(last / nv);
+                if (a_min <= b_max) {
+                    out.push_back(rt);
+                    out.push_back(qt);
+                }
+            }
+    return out;
+}
+
 int build_tables(ladder_plan_s& p) {
     size_t n_int2 = 0, n_int = 0;
+    std::vector<std::vector<int>> tiles;
     for (auto& bp : p.bps) n_int2 += bp.npairs;
+    if (p.precision != LADDER_FP64)
+        for (auto& bp : p.bps) {
+            tiles.push_back(eri_tiles(bp, p.nv, ladder::kEmuTile));
+            n_int2 += tiles.back().size() / 2;
+        }
     for (auto& bp : p.bps) n_int += (size_t)(bp.a1 - bp.a0 + 1);
     std::vector<int> host(2 * n_int2 + n_int);
     size_t o2 = 0, oi = 2 * n_int2;
@@ -166,6 +194,12 @@ int build_tables(ladder_plan_s& p) {
             }
         }
         host[oi++] = row;
+    }
+    for (size_t k = 0; k < tiles.size(); ++k) {
+        p.bps[k].tiles_off = o2;
+        p.bps[k].ntiles = (int)(tiles[k].size() / 2);
+        for (size_t t = 0; t < tiles[k].size(); ++t) host[2 * o2 + t] = tiles[k][t];
+        o2 += tiles[k].size() / 2;
     }
     if (p.d_tables) {
         cudaFree(p.d_tables);
@@ -277,7 +311,7 @@ int make_plan(ladder_plan_s** out, int no, int nv, int nchol, int precision, int
     if (precision != LADDER_FP64 && precision != LADDER_EMU_BF16) return LADDER_ERR_ARG;
     if (nslices == 0) nslices = ladder::kDefaultSlices;
     if (precision == LADDER_EMU_BF16) {
-        if (nslices < 3 || nslices > 8) return LADDER_ERR_ARG;
+        if (nslices < 4 || nslices > 8) return LADDER_ERR_ARG;
         if (!ladder::emu_supported(no, nv, nchol, nslices)) return LADDER_ERR_UNSUPPORTED;
     }
     int ndev = 0;
@@ -522,7 +556,7 @@ int ladder_plan_dry(int no, int nv, int nchol, int precision, int nslices, size_
     if (precision == LADDER_EMU_INT8) return LADDER_ERR_UNSUPPORTED;
     if (precision != LADDER_FP64 && precision != LADDER_EMU_BF16) return LADDER_ERR_ARG;
     if (nslices == 0) nslices = ladder::kDefaultSlices;
-    if (precision == LADDER_EMU_BF16 && (nslices < 3 || nslices > 8)) return LADDER_ERR_ARG;
+    if (precision == LADDER_EMU_BF16 && (nslices < 4 || nslices > 8)) return LADDER_ERR_ARG;
     ladder_plan_s p;
     p.no = no;
     p.nv = nv;

@@ -1,19 +1,730 @@
-// Emulated-FP64 path (BF16 digit slices on tcgen05).  Placeholder until the
-// kernels land: plans for this precision are rejected as unsupported.
+// Emulated-FP64 path: both contractions of the ladder run on the tcgen05
+// tensor cores as BF16 digit-slice products with FP32 accumulation in TMEM,
+// recombined exactly in integer arithmetic; FP64 is used only to scale the
+// final integer sums into R.
+//
+// Digit slices (FP64 emulation by splitting, the approach cited in the
+// introduction; this file fixes the variant): rows of an operand are grouped
+// (64 rows per group) and share one power-of-two exponent e with
+// max|x| < 2^(e-1).  N = rint(x 2^(7S-e)) is written in balanced base 128,
+// N = sum_s d_s 128^(S-s) with |d_s| <= 64, and slice plane s holds the BF16
+// value d_s 2^(-7s) (7 significant bits: exact).  A product sum over K keeps
+// the slice pairs with s + t <= S + 1.  Every product d_s d_t fits in 12 bits,
+// so the level sums l = s + t = 2, 3, 4 stay exact FP32 integers (times
+// 2^(-7l)) for K <= 1365; they get separate TMEM accumulators, and the levels
+// >= 5 share a fourth (weight <= 2^-35, rounded in FP32).
+//
+// ERI (C-split step 0, 'xac,xbd->acbd'): rows (a,c) and columns (b,d) of the
+// Gram matrix of L^T, K = nchol (one exact chunk).  The epilogue forms the
+// exact fixed-point value I = acc2 2^35 + acc3 2^28 + acc4 2^21 + rn(A5 2^49),
+// V = 2^(e_ac + e_bd - 49) I, and re-slices it for the ladder with one
+// exponent per (a,b) row taken from the Cauchy-Schwarz bound
+// |(ac|bd)| <= max_c ||L_ac|| max_d ||L_bd|| (the ERI is a Gram matrix), so no
+// pass over a whole V row is needed before slicing.
+//
+// Ladder (C-split step 1, 'acbd,ecfd->efab'): rows (a,b), columns (i,j),
+// K = (c,d) = nv^2 in exact chunks of 1280.  Per chunk J = acc2 2^28 +
+// acc3 2^21 + acc4 2^14 + rn(A5 2^42); chunk sums are added in int64 (exact,
+// so the order of the split-K atomics does not matter and the result is
+// deterministic).  R_ij^ab += 2^(f_ab + g_ij - 42) sum J and the mirror
+// R_ji^ba gets the same value.
+#include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <mutex>
 
 #include "ladder_internal.h"
+#include "tc_common.cuh"
 
 namespace ladder {
+namespace {
 
-bool emu_supported(int, int, int, int) { return false; }
+using namespace tc;
 
-cudaError_t launch_emu_prep(const ladder_plan_s&, const double*, const double*, void*, cudaStream_t) {
-    return cudaErrorNotSupported;
+constexpr int kG = kExpGroupRows;  // rows per exponent group
+constexpr int kEpiWarps = 8;       // epilogue warps (2 per TMEM lane quadrant)
+constexpr int kThreadsTC = 32 * (2 + kEpiWarps);
+constexpr int kTmemCols = 512;     // 4 accumulators x 128 columns
+constexpr int kAccStride = 128;    // TMEM columns between accumulators
+constexpr int kSmemBudget = 200 * 1024;
+
+__host__ __device__ constexpr int bk_for(int S) { return S <= 6 ? 32 : 16; }
+__host__ __device__ constexpr int stage_bytes(int S) { return 2 * S * kEmuTile * bk_for(S) * 2; }
+__host__ __device__ constexpr int stages_for(int S) {
+    return kSmemBudget / stage_bytes(S) < 4 ? kSmemBudget / stage_bytes(S) : 4;
+}
+__host__ __device__ constexpr int smem_bytes_for(int S) { return stages_for(S) * stage_bytes(S) + 1024; }
+
+// ------------------------------------------------------------------ digits
+// Balanced base-128 digits of N (|N| <= 2^(7S-1)) as BF16 plane values d_s 2^(-7s).
+__device__ __forceinline__ float small_int_to_float(int v) {
+    // exact for |v| < 2^22: 1.5 * 2^23 + v has an ulp of 1
+    return __int_as_float(0x4B400000 + v) - 12582912.0f;
 }
 
-cudaError_t launch_emu_block(const ladder_plan_s&, const BlockPair&, double*, void*, cudaStream_t) {
-    return cudaErrorNotSupported;
+__device__ __forceinline__ float pow2f(int k) { return __int_as_float((127 + k) << 23); }  // 2^k, |k| < 127
+
+template <int S>
+__device__ __forceinline__ void digits_of(long long N, __nv_bfloat16 (&out)[S]) {
+#pragma unroll
+    for (int s = S - 1; s >= 1; --s) {
+        const int low = (int)(((N + 64) & 127)) - 64;
+        N = (N - low) >> 7;
+        out[s] = __float2bfloat16_rn(small_int_to_float(low) * pow2f(-7 * (s + 1)));
+    }
+    out[0] = __float2bfloat16_rn(small_int_to_float((int)N) * pow2f(-7));
+}
+
+// round(I / 2^sh) with halves rounded up (sh <= 0 multiplies); values beyond
+// +-lim cannot occur for a valid exponent bound and are clamped and flagged.
+__device__ __forceinline__ long long rescale(long long I, int sh, long long lim, unsigned* status) {
+    long long N;
+    bool bad = false;
+    if (sh > 62) {
+        N = 0;
+    } else if (sh > 0) {
+        N = (I + (1LL << (sh - 1))) >> sh;
+    } else {
+        const int k = -sh;
+        const unsigned long long mag = I < 0 ? (unsigned long long)(-I) : (unsigned long long)I;
+        if (k >= 62 || (mag >> (62 - k)) != 0) {
+            bad = I != 0;
+            N = I < 0 ? -lim : (I > 0 ? lim : 0);
+        } else {
+            N = I << k;
+        }
+    }
+    if (N > lim || N < -lim) {
+        bad = true;
+        N = N > 0 ? lim : -lim;
+    }
+    if (bad) atomicOr(status, kStatusNumeric);
+    return N;
+}
+
+__device__ __forceinline__ int exponent_above(double m) {
+    // smallest e with m < 2^(e-1); 0 for m == 0
+    if (!(m > 0.0)) return 0;
+    int E;
+    frexp(m, &E);
+    return E + 1;
+}
+
+// ------------------------------------------------------------------ prep kernels
+// One block of 64 threads per group of 64 L^T rows r = (a,c): the group's exponent and,
+// per row, ||L[:, a, c]|| folded into max_c by an atomic max on the IEEE bits.
+__global__ void __launch_bounds__(64) lt_rowstats_kernel(const double* __restrict__ L, int nchol, int nv,
+                                                         int* __restrict__ lt_exp,
+                                                         unsigned long long* __restrict__ lnorm_bits) {
+    const long long nv2 = (long long)nv * nv;
+    const long long r = (long long)blockIdx.x * kG + threadIdx.x;
+    double m = 0.0, ss = 0.0;
+    if (r < nv2)
+        for (int P = 0; P < nchol; ++P) {
+            const double x = __ldg(L + (size_t)P * nv2 + r);
+            m = fmax(m, fabs(x));
+            ss = fma(x, x, ss);
+        }
+    __shared__ double red[2];
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) lt_exp[blockIdx.x] = exponent_above(fmax(red[0], red[1]));
+    if (r < nv2) atomicMax(lnorm_bits + r / nv, (unsigned long long)__double_as_longlong(sqrt(ss)));
+}
+
+// f[a][b]: smallest f with max_c||L_ac|| max_d||L_bd|| (1 + 2^-20) < 2^(f-1).
+__global__ void f_table_kernel(const unsigned long long* __restrict__ lnorm_bits, int nv, int* __restrict__ f) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= (long long)nv * nv) return;
+    const double na = __longlong_as_double((long long)lnorm_bits[k / nv]);
+    const double nb = __longlong_as_double((long long)lnorm_bits[k % nv]);
+    f[k] = exponent_above(na * nb * (1.0 + 0x1p-20));
+}
+
+// L^T slices: tile of 64 P x 64 rows through shared memory; writes planes[s][r][P].
+template <int S>
+__global__ void __launch_bounds__(256) lt_slice_kernel(const double* __restrict__ L, int nchol, int nv, int xpad,
+                                                       const int* __restrict__ lt_exp,
+                                                       __nv_bfloat16* __restrict__ planes) {
+    __shared__ double tile[64][65];
+    const long long nv2 = (long long)nv * nv;
+    const int P0 = blockIdx.x * 64;
+    const long long r0 = (long long)blockIdx.y * 64;
+    for (int i = threadIdx.x; i < 64 * 64; i += 256) {
+        const int p = i >> 6, rr = i & 63;
+        tile[p][rr] = (P0 + p < nchol && r0 + rr < nv2) ? __ldg(L + (size_t)(P0 + p) * nv2 + r0 + rr) : 0.0;
+    }
+    __syncthreads();
+    const int rr = threadIdx.x >> 2, pseg = (threadIdx.x & 3) * 16;
+    const long long r = r0 + rr;
+    if (r >= nv2) return;
+    const int e = lt_exp[r0 / kG];
+    const size_t plane = (size_t)nv2 * xpad;
+#pragma unroll 4
+    for (int k = 0; k < 16; ++k) {
+        const int P = P0 + pseg + k;
+        if (P >= nchol) break;
+        const long long N = __double2ll_rn(scalbn(tile[pseg + k][rr], 7 * S - e));
+        __nv_bfloat16 d[S];
+        digits_of<S>(N, d);
+#pragma unroll
+        for (int s = 0; s < S; ++s) planes[s * plane + (size_t)r * xpad + P] = d[s];
+    }
+}
+
+// max |T| per group of 64 T rows, via atomic max on the IEEE bits (T viewed [no^2][nv^2]).
+__global__ void __launch_bounds__(256) t_rowmax_kernel(const double* __restrict__ t2, long long K, int rows,
+                                                       unsigned long long* __restrict__ gmax) {
+    const int row = blockIdx.y;
+    const long long k0 = (long long)blockIdx.x * 8192;
+    double m = 0.0;
+    for (long long k = k0 + threadIdx.x; k < K && k < k0 + 8192; k += 256)
+        m = fmax(m, fabs(__ldg(t2 + (size_t)row * K + k)));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0.0) atomicMax(gmax + row / kG, (unsigned long long)__double_as_longlong(m));
+}
+
+__global__ void exp_from_max_kernel(const unsigned long long* __restrict__ gmax, int n, int* __restrict__ e) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < n) e[g] = exponent_above(__longlong_as_double((long long)gmax[g]));
+}
+
+// T slices: 8 consecutive k of one row per thread; planes[s][row][k] (row stride kpad).
+template <int S>
+__global__ void __launch_bounds__(256) t_slice_kernel(const double* __restrict__ t2, long long K, int rows, int kpad,
+                                                      const int* __restrict__ t_exp,
+                                                      __nv_bfloat16* __restrict__ planes) {
+    const long long per_row = (kpad + 7) / 8;
+    const long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= per_row * rows) return;
+    const int row = (int)(u / per_row);
+    const long long k0 = (u % per_row) * 8;
+    const int e = t_exp[row / kG];
+    const size_t plane = (size_t)rows * kpad;
+    __align__(16) __nv_bfloat16 out[S][8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const long long k = k0 + j;
+        const double x = k < K ? __ldg(t2 + (size_t)row * K + k) : 0.0;
+        __nv_bfloat16 d[S];
+        digits_of<S>(__double2ll_rn(scalbn(x, 7 * S - e)), d);
+#pragma unroll
+        for (int s = 0; s < S; ++s) out[s][j] = d[s];
+    }
+#pragma unroll
+    for (int s = 0; s < S; ++s)
+        *reinterpret_cast<uint4*>(planes + s * plane + (size_t)row * kpad + k0) = *reinterpret_cast<uint4*>(out[s]);
+}
+
+// ------------------------------------------------------------------ shared tcgen05 pieces
+struct Ring {
+    int stage = 0;
+    uint32_t phase = 0;
+    __device__ __forceinline__ void next(int stages) {
+        if (++stage == stages) {
+            stage = 0;
+            phase ^= 1u;
+        }
+    }
+};
+
+// Issue the S(S+1)/2 slice-pair MMAs of one stage (BK / 16 K-steps) into the 4 accumulators.
+template <int S>
+__device__ __forceinline__ void issue_pairs(uint32_t tmem, uint32_t sA, uint32_t sB, uint32_t a_plane_bytes,
+                                            uint32_t b_plane_bytes, uint32_t idesc, bool (&first)[4]) {
+    constexpr int BK = bk_for(S);
+#pragma unroll
+    for (int kk = 0; kk < BK / 16; ++kk) {
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+#pragma unroll
+            for (int t = 0; t + s < S; ++t) {
+                const int j = (s + t + 2 < 5 ? s + t + 2 : 5) - 2;
+                const uint64_t ad = smem_desc_kmajor(sA + s * a_plane_bytes + kk * 32, BK * 2);
+                const uint64_t bd = smem_desc_kmajor(sB + t * b_plane_bytes + kk * 32, BK * 2);
+                mma_bf16(tmem + j * kAccStride, ad, bd, idesc, first[j] ? 0u : 1u);
+                first[j] = false;
+            }
+        }
+    }
+}
+
+struct EriArgs {
+    int nv, nchol, a0, na, b0, nb, kpad, ntiles;
+    size_t plane_stride;  // elements between V planes
+    const int2* tiles;
+    const int* row_start;
+    const int* lt_exp;
+    const int* f_tab;
+    __nv_bfloat16* vplanes;
+    unsigned* status;
+};
+
+// ------------------------------------------------------------------ ERI kernel
+template <int S>
+__global__ void __launch_bounds__(kThreadsTC, 1) eri_emu_kernel(const __grid_constant__ CUtensorMap tm_lt, EriArgs p) {
+    constexpr int BK = bk_for(S), STAGES = stages_for(S);
+    constexpr uint32_t PLANE = kEmuTile * BK * 2;  // bytes of one 128-row plane
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    __shared__ uint64_t full[STAGES], empty[STAGES], acc_full, acc_empty, done;
+    __shared__ uint32_t tmem_base;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < STAGES; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        mbar_init(&acc_full, 1);
+        mbar_init(&acc_empty, kEpiWarps);
+        mbar_init(&done, 1);
+        fence_barrier_init();
+        tma_prefetch_desc(&tm_lt);
+    }
+    if (warp == 1) tmem_alloc(&tmem_base, kTmemCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    const int nkb = (p.nchol + BK - 1) / BK;
+
+    if (warp == 0 && lane == 0) {
+        // ---------------- TMA producer
+        Ring ring;
+        int issued[STAGES] = {};
+        bool ok = true;
+        for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
+            const int2 tq = p.tiles[t];
+            const int arow = p.a0 * p.nv + tq.x * kEmuTile;
+            const int brow = p.b0 * p.nv + tq.y * kEmuTile;
+            for (int kb = 0; kb < nkb && ok; ++kb) {
+                if (!(ok = mbar_wait(&empty[ring.stage], ring.phase ^ 1u, p.status, kStatusTimeout))) break;
+                unsigned char* st = smem + ring.stage * stage_bytes(S);
+                mbar_arrive_expect_tx(&full[ring.stage], stage_bytes(S));
+                tma_load_3d(st, &tm_lt, &full[ring.stage], kb * BK, arow, 0);
+                tma_load_3d(st + S * PLANE, &tm_lt, &full[ring.stage], kb * BK, brow, 0);
+                ++issued[ring.stage];
+                ring.next(STAGES);
+            }
+        }
+        // Wait (bounded) for every copy still in flight before the CTA can exit.
+        for (int i = 0; i < STAGES; ++i)
+            if (issued[i]) mbar_wait(&full[i], (uint32_t)((issued[i] - 1) & 1), p.status, kStatusTimeout);
+    } else if (warp == 1 && lane == 0) {
+        // ---------------- MMA issuer
+        Ring ring;
+        const uint32_t idesc = idesc_bf16_f32(kEmuTile, kEmuTile);
+        bool ok = true;
+        int it = 0;
+        for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x, ++it) {
+            if (!(ok = mbar_wait(&acc_empty, (uint32_t)(it & 1) ^ 1u, p.status, kStatusTimeout))) break;
+            tc_fence_after();
+            bool first[4] = {true, true, true, true};
+            for (int kb = 0; kb < nkb && ok; ++kb) {
+                if (!(ok = mbar_wait(&full[ring.stage], ring.phase, p.status, kStatusTimeout))) break;
+                tc_fence_after();
+                const uint32_t st = smem_u32(smem + ring.stage * stage_bytes(S));
+                issue_pairs<S>(tmem, st, st + S * PLANE, PLANE, PLANE, idesc, first);
+                mma_commit(&empty[ring.stage]);
+                ring.next(STAGES);
+            }
+            if (ok) mma_commit(&acc_full);
+        }
+        mma_commit(&done);
+        mbar_wait(&done, 0, p.status, kStatusTimeout);
+    } else if (warp >= 2) {
+        // ---------------- epilogue: exact recombination and re-slicing into the V planes
+        const int q = warp & 3, h = (warp - 2) >> 2;
+        const int Mrows = p.na * p.nv, Ncols = p.nb * p.nv;
+        int it = 0;
+        for (int t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++it) {
+            if (!mbar_wait(&acc_full, (uint32_t)(it & 1), p.status, kStatusTimeout)) break;
+            tc_fence_after();
+            const int2 tq = p.tiles[t];
+            const int r_local = tq.x * kEmuTile + 32 * q + lane;
+            const bool valid_r = r_local < Mrows;
+            const int a = p.a0 + r_local / p.nv, c = r_local % p.nv;
+            const int e_ac = valid_r ? p.lt_exp[(p.a0 * p.nv + r_local) / kG] : 0;
+            const int rs = valid_r ? p.row_start[a - p.a0] : 0;
+#pragma unroll 1
+            for (int c0 = 0; c0 < 64; c0 += 16) {
+                uint32_t acc[4][16];
+                const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + 64 * h + c0;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) tmem_ld16(taddr + j * kAccStride, acc[j]);
+                tmem_ld_wait();
+                int col = tq.y * kEmuTile + 64 * h + c0;
+                int b = p.b0 + col / p.nv, d = col % p.nv;
+#pragma unroll
+                for (int k = 0; k < 16; ++k, ++col) {
+                    if (valid_r && col < Ncols && a <= b) {
+                        const long long i2 = __float2int_rn(__uint_as_float(acc[0][k]) * 0x1p14f);
+                        const long long i3 = __float2int_rn(__uint_as_float(acc[1][k]) * 0x1p21f);
+                        const long long i4 = __float2int_rn(__uint_as_float(acc[2][k]) * 0x1p28f);
+                        const long long i5 = __float2ll_rn(__uint_as_float(acc[3][k]) * 0x1p49f);
+                        const long long I = (i2 << 35) + (i3 << 28) + (i4 << 21) + i5;
+                        const int e_bd = p.lt_exp[(p.b0 * p.nv + col) / kG];
+                        const int sh = p.f_tab[a * p.nv + b] - e_ac - e_bd + 49 - 7 * S;
+                        const long long Np = rescale(I, sh, 1LL << (7 * S - 1), p.status);
+                        __nv_bfloat16 dg[S];
+                        digits_of<S>(Np, dg);
+                        const size_t off = (size_t)(rs + (b - max(a, p.b0))) * p.kpad + (size_t)c * p.nv + d;
+#pragma unroll
+                        for (int s = 0; s < S; ++s) p.vplanes[s * p.plane_stride + off] = dg[s];
+                    }
+                    if (++d == p.nv) {
+                        d = 0;
+                        ++b;
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, kTmemCols);
+    }
+}
+
+// ------------------------------------------------------------------ ladder kernel
+struct LadArgs {
+    int npairs, no2, BN, n_mt, n_nt, n_ch, kb_per_chunk, nkb;
+    long long units;
+    unsigned long long* rp;  // int64 fixed-point accumulator [npairs][no2]
+    unsigned* status;
+};
+
+template <int S>
+__global__ void __launch_bounds__(kThreadsTC, 1) ladder_emu_kernel(const __grid_constant__ CUtensorMap tm_v,
+                                                                   const __grid_constant__ CUtensorMap tm_t,
+                                                                   LadArgs p) {
+    constexpr int BK = bk_for(S), STAGES = stages_for(S);
+    constexpr uint32_t APLANE = kEmuTile * BK * 2;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    __shared__ uint64_t full[STAGES], empty[STAGES], acc_full, acc_empty, done;
+    __shared__ uint32_t tmem_base;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t BPLANE = (uint32_t)p.BN * BK * 2;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < STAGES; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        mbar_init(&acc_full, 1);
+        mbar_init(&acc_empty, kEpiWarps);
+        mbar_init(&done, 1);
+        fence_barrier_init();
+        tma_prefetch_desc(&tm_v);
+        tma_prefetch_desc(&tm_t);
+    }
+    if (warp == 1) tmem_alloc(&tmem_base, kTmemCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    const long long u0 = p.units * blockIdx.x / gridDim.x, u1 = p.units * (blockIdx.x + 1) / gridDim.x;
+
+    if (warp == 0 && lane == 0) {
+        Ring ring;
+        int issued[STAGES] = {};
+        bool ok = true;
+        const uint32_t bytes = (uint32_t)S * (kEmuTile + p.BN) * BK * 2;
+        for (long long u = u0; u < u1 && ok; ++u) {
+            const int ch = (int)(u % p.n_ch);
+            const long long tile = u / p.n_ch;
+            const int nt = (int)(tile % p.n_nt), mt = (int)(tile / p.n_nt);
+            const int kb1 = min((ch + 1) * p.kb_per_chunk, p.nkb);
+            for (int kb = ch * p.kb_per_chunk; kb < kb1 && ok; ++kb) {
+                if (!(ok = mbar_wait(&empty[ring.stage], ring.phase ^ 1u, p.status, kStatusTimeout))) break;
+                unsigned char* st = smem + ring.stage * stage_bytes(S);
+                mbar_arrive_expect_tx(&full[ring.stage], bytes);
+                tma_load_3d(st, &tm_v, &full[ring.stage], kb * BK, mt * kEmuTile, 0);
+                tma_load_3d(st + S * APLANE, &tm_t, &full[ring.stage], kb * BK, nt * p.BN, 0);
+                ++issued[ring.stage];
+                ring.next(STAGES);
+            }
+        }
+        for (int i = 0; i < STAGES; ++i)
+            if (issued[i]) mbar_wait(&full[i], (uint32_t)((issued[i] - 1) & 1), p.status, kStatusTimeout);
+    } else if (warp == 1 && lane == 0) {
+        Ring ring;
+        const uint32_t idesc = idesc_bf16_f32(kEmuTile, p.BN);
+        bool ok = true;
+        int it = 0;
+        for (long long u = u0; u < u1 && ok; ++u, ++it) {
+            const int ch = (int)(u % p.n_ch);
+            if (!(ok = mbar_wait(&acc_empty, (uint32_t)(it & 1) ^ 1u, p.status, kStatusTimeout))) break;
+            tc_fence_after();
+            bool first[4] = {true, true, true, true};
+            const int kb1 = min((ch + 1) * p.kb_per_chunk, p.nkb);
+            for (int kb = ch * p.kb_per_chunk; kb < kb1 && ok; ++kb) {
+                if (!(ok = mbar_wait(&full[ring.stage], ring.phase, p.status, kStatusTimeout))) break;
+                tc_fence_after();
+                const uint32_t st = smem_u32(smem + ring.stage * stage_bytes(S));
+                issue_pairs<S>(tmem, st, st + S * APLANE, APLANE, BPLANE, idesc, first);
+                mma_commit(&empty[ring.stage]);
+                ring.next(STAGES);
+            }
+            if (ok) mma_commit(&acc_full);
+        }
+        mma_commit(&done);
+        mbar_wait(&done, 0, p.status, kStatusTimeout);
+    } else if (warp >= 2) {
+        // Each warp: TMEM lane quadrant q, column chunks ci = h, h+2, h+4, h+6 (16 columns each).
+        const int q = warp & 3, h = (warp - 2) >> 2;
+        const int nchunks = p.BN / 16;
+        long long run[4][16];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int k = 0; k < 16; ++k) run[i][k] = 0;
+        int it = 0;
+        for (long long u = u0; u < u1; ++u, ++it) {
+            if (!mbar_wait(&acc_full, (uint32_t)(it & 1), p.status, kStatusTimeout)) break;
+            tc_fence_after();
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int ci = h + 2 * i;
+                if (ci < nchunks) {
+                    uint32_t acc[4][16];
+                    const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + 16 * ci;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) tmem_ld16(taddr + j * kAccStride, acc[j]);
+                    tmem_ld_wait();
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) {
+                        const long long i2 = __float2int_rn(__uint_as_float(acc[0][k]) * 0x1p14f);
+                        const long long i3 = __float2int_rn(__uint_as_float(acc[1][k]) * 0x1p21f);
+                        const long long i4 = __float2int_rn(__uint_as_float(acc[2][k]) * 0x1p28f);
+                        const long long i5 = __float2ll_rn(__uint_as_float(acc[3][k]) * 0x1p42f);
+                        run[i][k] += (i2 << 28) + (i3 << 21) + (i4 << 14) + i5;
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty);
+            // Flush at the end of a (row tile, column tile) run or of this CTA's range.
+            const long long tile = u / p.n_ch;
+            if (u + 1 == u1 || (u + 1) / p.n_ch != tile) {
+                const int nt = (int)(tile % p.n_nt), mt = (int)(tile / p.n_nt);
+                const int m = mt * kEmuTile + 32 * q + lane;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int ci = h + 2 * i;
+                    if (ci < nchunks) {
+#pragma unroll
+                        for (int k = 0; k < 16; ++k) {
+                            const int n = nt * p.BN + 16 * ci + k;
+                            if (m < p.npairs && n < p.no2 && run[i][k] != 0)
+                                atomicAdd(p.rp + (size_t)m * p.no2 + n, (unsigned long long)run[i][k]);
+                            run[i][k] = 0;
+                        }
+                    }
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, kTmemCols);
+    }
+}
+
+// R[i,j,a,b] += 2^(f_ab + g_ij - 42) J[(a,b), (i,j)] and the mirror R[j,i,b,a] for a < b.
+__global__ void finalize_kernel(const unsigned long long* __restrict__ rp, int npairs, int no, int nv,
+                                const int2* __restrict__ pairs, const int* __restrict__ f_tab,
+                                const int* __restrict__ t_exp, double* __restrict__ R) {
+    const int no2 = no * no;
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= (long long)npairs * no2) return;
+    const int m = (int)(k / no2), n = (int)(k % no2);
+    const int2 ab = pairs[m];
+    const long long J = (long long)rp[k];
+    const double v = ldexp((double)J, f_tab[ab.x * nv + ab.y] + t_exp[n / kG] - 42);
+    const int i = n / no, j = n % no;
+    R[(((size_t)i * no + j) * nv + ab.x) * nv + ab.y] += v;
+    if (ab.x < ab.y) R[(((size_t)j * no + i) * nv + ab.y) * nv + ab.x] += v;
+}
+
+// ------------------------------------------------------------------ host side
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    });
+    return fn;
+}
+
+// 3-D BF16 map over planes[z][y][x]: x = K (extent `inner`, row stride `row_bytes`),
+// y = rows, z = planes (stride `plane_bytes`).  Box {bk, box_rows, planes}; OOB reads give 0.
+bool make_tmap(CUtensorMap* m, const void* base, uint64_t inner, uint64_t rows, uint64_t planes, uint64_t row_bytes,
+               uint64_t plane_bytes, uint32_t bk, uint32_t box_rows) {
+    auto enc = encode_fn();
+    if (!enc) return false;
+    cuuint64_t dims[3] = {inner, rows, planes};
+    cuuint64_t strides[2] = {row_bytes, plane_bytes};
+    cuuint32_t box[3] = {bk, box_rows, (cuuint32_t)planes};
+    cuuint32_t es[3] = {1, 1, 1};
+    const CUtensorMapSwizzle sw = bk * 2 == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                  : bk * 2 == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                                 : CU_TENSOR_MAP_SWIZZLE_32B;
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <class T>
+T* at(void* ws, size_t off) {
+    return reinterpret_cast<T*>(static_cast<char*>(ws) + off);
+}
+
+int ladder_bn(int no2) {
+    const int nt = (no2 + kEmuTile - 1) / kEmuTile;
+    const int per = (no2 + nt - 1) / nt;
+    return std::max(16, (per + 15) / 16 * 16);
+}
+
+template <int S>
+cudaError_t prep_impl(const ladder_plan_s& p, const double* L, const double* t2, void* ws, cudaStream_t s) {
+    const long long nv2 = (long long)p.nv * p.nv;
+    const int no2 = p.no * p.no;
+    const int xpad = (int)align_up((size_t)p.nchol, 8);
+    const int kpad = (int)align_up((size_t)nv2, 8);
+    const int ngt = (no2 + kG - 1) / kG;
+    LaunchTimer tm(p, s, LADDER_KERNEL_PREP);
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(at<char>(ws, p.ws.lnorm), 0, (size_t)p.nv * 8, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(at<char>(ws, p.ws.t_gmax), 0, (size_t)ngt * 8, s)) != cudaSuccess) return e;
+    lt_rowstats_kernel<<<(unsigned)((nv2 + kG - 1) / kG), kG, 0, s>>>(L, p.nchol, p.nv, at<int>(ws, p.ws.lt_exp),
+                                                                       at<unsigned long long>(ws, p.ws.lnorm));
+    f_table_kernel<<<(unsigned)((nv2 + 255) / 256), 256, 0, s>>>(at<unsigned long long>(ws, p.ws.lnorm), p.nv,
+                                                                   at<int>(ws, p.ws.v_exp));
+    lt_slice_kernel<S><<<dim3((p.nchol + 63) / 64, (unsigned)((nv2 + 63) / 64)), 256, 0, s>>>(
+        L, p.nchol, p.nv, xpad, at<int>(ws, p.ws.lt_exp), at<__nv_bfloat16>(ws, p.ws.lt_slices));
+    t_rowmax_kernel<<<dim3((unsigned)((nv2 + 8191) / 8192), no2), 256, 0, s>>>(t2, nv2, no2,
+                                                                              at<unsigned long long>(ws, p.ws.t_gmax));
+    exp_from_max_kernel<<<(ngt + 255) / 256, 256, 0, s>>>(at<unsigned long long>(ws, p.ws.t_gmax), ngt,
+                                                           at<int>(ws, p.ws.t_exp));
+    const long long units = (long long)((kpad + 7) / 8) * no2;
+    t_slice_kernel<S><<<(unsigned)((units + 255) / 256), 256, 0, s>>>(t2, nv2, no2, kpad, at<int>(ws, p.ws.t_exp),
+                                                                      at<__nv_bfloat16>(ws, p.ws.t_slices));
+    return cudaGetLastError();
+}
+
+template <int S>
+cudaError_t block_impl(const ladder_plan_s& p, const BlockPair& bp, double* R, void* ws, cudaStream_t s) {
+    constexpr int BK = bk_for(S);
+    const long long nv2 = (long long)p.nv * p.nv;
+    const int no2 = p.no * p.no;
+    const int xpad = (int)align_up((size_t)p.nchol, 8);
+    const int kpad = (int)align_up((size_t)nv2, 8);
+    const size_t vplane = (size_t)p.max_pairs * kpad;
+    const int smem = smem_bytes_for(S);
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(eri_emu_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(ladder_emu_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) !=
+            cudaSuccess)
+        return e;
+    // int64 ladder accumulator of this block pair starts at zero
+    if ((e = cudaMemsetAsync(at<char>(ws, p.ws.rp_int), 0, (size_t)bp.npairs * no2 * 8, s)) != cudaSuccess) return e;
+
+    const int2* table = reinterpret_cast<const int2*>(p.d_tables);
+    const int* row_start = reinterpret_cast<const int*>(p.d_tables) + bp.rows_off;
+    CUtensorMap tm_lt, tm_v, tm_t;
+    if (!make_tmap(&tm_lt, at<char>(ws, p.ws.lt_slices), p.nchol, nv2, S, (uint64_t)xpad * 2, (uint64_t)nv2 * xpad * 2,
+                   BK, kEmuTile))
+        return cudaErrorInvalidValue;
+    EriArgs ea{p.nv, p.nchol, bp.a0, bp.a1 - bp.a0, bp.b0, bp.b1 - bp.b0, kpad, bp.ntiles, vplane,
+               table + bp.tiles_off, row_start, at<int>(ws, p.ws.lt_exp), at<int>(ws, p.ws.v_exp),
+               at<__nv_bfloat16>(ws, p.ws.v_blk), p.d_status};
+    {
+        LaunchTimer tm(p, s, LADDER_KERNEL_ERI);
+        eri_emu_kernel<S><<<std::max(1, std::min(bp.ntiles, p.num_sms)), kThreadsTC, smem, s>>>(tm_lt, ea);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+
+    const int BN = ladder_bn(no2);
+    if (!make_tmap(&tm_v, at<char>(ws, p.ws.v_blk), nv2, bp.npairs, S, (uint64_t)kpad * 2, (uint64_t)vplane * 2, BK,
+                   kEmuTile) ||
+        !make_tmap(&tm_t, at<char>(ws, p.ws.t_slices), nv2, no2, S, (uint64_t)kpad * 2, (uint64_t)no2 * kpad * 2, BK,
+                   BN))
+        return cudaErrorInvalidValue;
+    LadArgs la{};
+    la.npairs = bp.npairs;
+    la.no2 = no2;
+    la.BN = BN;
+    la.n_mt = (bp.npairs + kEmuTile - 1) / kEmuTile;
+    la.n_nt = (no2 + BN - 1) / BN;
+    la.nkb = (int)((nv2 + BK - 1) / BK);
+    la.kb_per_chunk = kEmuChunkK / BK;
+    la.n_ch = (la.nkb + la.kb_per_chunk - 1) / la.kb_per_chunk;
+    la.units = (long long)la.n_mt * la.n_nt * la.n_ch;
+    la.rp = at<unsigned long long>(ws, p.ws.rp_int);
+    la.status = p.d_status;
+    {
+        LaunchTimer tm(p, s, LADDER_KERNEL_LADDER);
+        ladder_emu_kernel<S><<<(unsigned)std::max<long long>(1, std::min<long long>(la.units, p.num_sms)),
+                               kThreadsTC, smem, s>>>(tm_v, tm_t, la);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    {
+        LaunchTimer tm(p, s, LADDER_KERNEL_FINISH);
+        const long long n = (long long)bp.npairs * no2;
+        finalize_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(at<unsigned long long>(ws, p.ws.rp_int),
+                                                                    bp.npairs, p.no, p.nv, table + bp.pairs_off,
+                                                                    at<int>(ws, p.ws.v_exp), at<int>(ws, p.ws.t_exp), R);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool emu_supported(int no, int nv, int nchol, int nslices) {
+    (void)no;
+    (void)nv;
+    return nchol <= kEmuMaxExactK && nslices >= 4 && nslices <= 8;
+}
+
+cudaError_t launch_emu_prep(const ladder_plan_s& p, const double* L, const double* t2, void* ws, cudaStream_t s) {
+    switch (p.nslices) {
+        case 4: return prep_impl<4>(p, L, t2, ws, s);
+        case 5: return prep_impl<5>(p, L, t2, ws, s);
+        case 6: return prep_impl<6>(p, L, t2, ws, s);
+        case 7: return prep_impl<7>(p, L, t2, ws, s);
+        case 8: return prep_impl<8>(p, L, t2, ws, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_emu_block(const ladder_plan_s& p, const BlockPair& bp, double* R, void* ws, cudaStream_t s) {
+    switch (p.nslices) {
+        case 4: return block_impl<4>(p, bp, R, ws, s);
+        case 5: return block_impl<5>(p, bp, R, ws, s);
+        case 6: return block_impl<6>(p, bp, R, ws, s);
+        case 7: return block_impl<7>(p, bp, R, ws, s);
+        case 8: return block_impl<8>(p, bp, R, ws, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace ladder

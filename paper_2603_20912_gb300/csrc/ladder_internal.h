@@ -18,6 +18,7 @@ constexpr int kDigitBits = 7;               // bits per signed digit, |digit| <=
 constexpr int kExpGroupRows = 64;           // rows sharing one power-of-two exponent
 constexpr int kEmuMaxExactK = 1365;         // K per exact accumulation chunk: 3 * 64^2 * K <= 2^24
 constexpr int kEmuChunkK = 1280;            // ladder K chunk (multiple of 64, <= kEmuMaxExactK)
+constexpr int kEmuTile = 128;               // tcgen05 tile rows (M) and ERI tile columns (N)
 
 // Device status bits (ORed into the plan's status word by kernels).
 constexpr unsigned kStatusTimeout = 1u;
@@ -32,6 +33,8 @@ struct BlockPair {
     int npairs;        // number of (a, b) with a <= b in the block pair
     size_t pairs_off;  // offset (in int2) of this block pair's pair list in the device table
     size_t rows_off;   // offset (in int) of this block pair's row_start table (a1 - a0 + 1 ints)
+    size_t tiles_off = 0;  // emulated path: offset (in int2) of the ERI tile list (rt, qt)
+    int ntiles = 0;        // emulated path: number of 128x128 ERI tiles holding some a <= b
 };
 
 // Workspace layout of one plan (byte offsets from the workspace base).
@@ -41,9 +44,10 @@ struct WsLayout {
     size_t lt_slices = 0;  // EMU: L^T slices [S][nv*nv][xpad] bf16
     size_t lt_exp = 0;     // EMU: exponent per group of L^T rows (int)
     size_t t_slices = 0;   // EMU: T slices [S][no*no][kpad] bf16
+    size_t t_gmax = 0;     // EMU: max |T| per group of T rows (IEEE bits, u64)
     size_t t_exp = 0;      // EMU: exponent per group of T rows (int)
     size_t v_exp = 0;      // EMU: exponent bound per (a, b) pair [nv][nv] (int)
-    size_t lnorm = 0;      // EMU: max_c ||L[:, a, c]||_2 per a (double)
+    size_t lnorm = 0;      // EMU: max_c ||L[:, a, c]||_2 per a (IEEE bits, u64)
     size_t total = 0;
 };
 

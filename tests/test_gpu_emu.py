@@ -1,0 +1,142 @@
+"""GPU parity of the emulated-FP64 path (BF16 digit slices on tcgen05) against
+the CPU oracle, through the C ABI.
+
+Tolerances (stated for the emulated path): ||R - R_oracle||_F / ||R_oracle||_F
+<= 1e-10 and |E_L - E_L(oracle)| <= 1e-8 Eh at the default 6 slices.
+Every cross-chunk and cross-block sum of the path is an exact integer, so the
+result must not depend on the blocking or on the split-K partition at all:
+those tests compare bit for bit.
+"""
+import json
+import os
+import sys
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2603_20912_gb300 as lad
+from ladder_inputs import CONFIGS, make_inputs, make_integer_inputs
+from conftest import rel_fro
+
+sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+from emu_model import emulated_ladder  # noqa: E402
+from test_gpu_fp64 import check_sampled, dev, gpu_ladder, assert_pair_symmetry, _golden_energy  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+EMU = lad.LADDER_EMU_BF16
+TOL_R = 1e-10
+TOL_E = 1e-8
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2603_20912_gb300 import build
+    build.build()
+
+
+def test_c1_parity_energy_and_symmetry():
+    s = CONFIGS["c1"]
+    L, t2, _, _ = make_inputs(s.no, s.nv, s.nchol, s.seed)
+    R, plan = gpu_ladder(L, t2, EMU)
+    ref = oracle.ladder(L, t2)
+    assert rel_fro(R, ref) <= TOL_R
+    E = lad.ladder_energy(plan, dev(t2), dev(R))
+    assert abs(E - oracle.energy(t2, ref)) <= TOL_E
+    assert_pair_symmetry(R)
+
+
+def test_c1_matches_cpu_model_of_the_scheme():
+    s = CONFIGS["c1"]
+    L, t2, _, _ = make_inputs(s.no, s.nv, s.nchol, s.seed)
+    R, _ = gpu_ladder(L, t2, EMU)
+    model = emulated_ladder(L, t2, S=6)
+    # The model is exact except for the FP32 rounding order of the level >= 5 accumulator.
+    assert rel_fro(R, model) <= 1e-13
+
+
+@pytest.mark.parametrize("S,tol", [(4, 3e-6), (5, 3e-8), (6, 1e-10), (7, 1e-11), (8, 1e-12)])
+def test_slice_count_controls_the_error(S, tol):
+    s = CONFIGS["c1"]
+    L, t2, _, _ = make_inputs(s.no, s.nv, s.nchol, s.seed)
+    R, plan = gpu_ladder(L, t2, EMU, nslices=S)
+    assert plan.describe()["nslices"] == S
+    assert rel_fro(R, oracle.ladder(L, t2)) <= tol
+
+
+def test_integer_grid_is_bit_exact():
+    L, t2 = make_integer_inputs(4, 23, 40, seed=5)
+    R, _ = gpu_ladder(L, t2, EMU)
+    assert np.array_equal(R, oracle.ladder(L, t2))
+
+
+@pytest.mark.parametrize("blocks", [(1, 1), (3, 7), (7, 3), (5, 19), (19, 2), (10, 4)])
+def test_blocking_does_not_change_a_single_bit(blocks):
+    s = CONFIGS["c1"]
+    L, t2, _, _ = make_inputs(s.no, s.nv, s.nchol, s.seed)
+    R1, _ = gpu_ladder(L, t2, EMU)
+    Rb, plan = gpu_ladder(L, t2, EMU, blocks=blocks)
+    d = plan.describe()
+    assert (d["n_a"], d["n_b"]) == blocks
+    assert np.array_equal(Rb, R1)
+
+
+def test_small_budget_split_and_accumulation():
+    no, nv, nchol = 3, 37, 45
+    L, t2, _, _ = make_inputs(no, nv, nchol, seed=21)
+    R0 = np.random.default_rng(4).standard_normal(t2.shape)
+    full = lad.ladder_plan(no, nv, nchol, EMU).workspace_bytes()
+    R, plan = gpu_ladder(L, t2, EMU, R0=R0, budget=int(full * 0.6))
+    assert plan.describe()["n_block_pairs"] > 1
+    assert rel_fro(R - R0, oracle.ladder(L, t2)) <= TOL_R
+
+
+@pytest.mark.parametrize("no,nv,nchol", [(1, 1, 1), (1, 2, 3), (2, 1, 5), (4, 9, 1), (6, 65, 17), (9, 33, 130),
+                                         (12, 20, 70), (3, 130, 200)])
+def test_edge_shapes(no, nv, nchol):
+    L, t2, _, _ = make_inputs(no, nv, nchol, seed=no * 1000 + nv)
+    R, _ = gpu_ladder(L, t2, EMU)
+    assert rel_fro(R, oracle.ladder(L, t2)) <= TOL_R
+
+
+def test_deterministic():
+    L, t2, _, _ = make_inputs(5, 45, 60, seed=41)
+    R1, _ = gpu_ladder(L, t2, EMU)
+    R2, _ = gpu_ladder(L, t2, EMU)
+    assert np.array_equal(R1, R2)
+
+
+def test_zero_inputs_give_zero():
+    L = np.zeros((7, 11, 11))
+    t2 = np.zeros((3, 3, 11, 11))
+    R, _ = gpu_ladder(L, t2, EMU)
+    assert np.all(R == 0.0)
+
+
+def test_rejects_unsupported_requests():
+    with pytest.raises(lad.LadderError) as e:
+        lad.ladder_plan(5, 19, 72, lad.LADDER_EMU_INT8)
+    assert e.value.status == lad.LADDER_ERR_UNSUPPORTED
+    with pytest.raises(lad.LadderError) as e:
+        lad.ladder_plan(5, 19, 2000, EMU)          # nchol beyond one exact chunk
+    assert e.value.status == lad.LADDER_ERR_UNSUPPORTED
+    with pytest.raises(lad.LadderError) as e:
+        lad.ladder_plan(5, 19, 72, EMU, nslices=3)
+    assert e.value.status == lad.LADDER_ERR_ARG
+
+
+@pytest.mark.parametrize("name", ["c2", "c3"])
+def test_full_size_sampled_parity(name):
+    s = CONFIGS[name]
+    L, t2, _, _ = make_inputs(s.no, s.nv, s.nchol, s.seed)
+    R, plan = gpu_ladder(L, t2, EMU)
+    check_sampled(R, L, t2, TOL_R, nsample=32)
+    assert_pair_symmetry(R)
+    E = lad.ladder_energy(plan, dev(t2), dev(R))
+    assert E == pytest.approx(oracle.energy(t2, R), rel=1e-12)
+    Eg = _golden_energy(name)
+    if Eg is not None:
+        assert abs(E - Eg) <= TOL_E
