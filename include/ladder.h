@@ -78,13 +78,13 @@ enum {
  *   nchol      number of Cholesky vectors (>= 1).
  *   precision  LADDER_FP64 or LADDER_EMU_BF16.
  *   nslices    digit slices per operand for the emulated path, 0 = default (6);
- *              ignored for LADDER_FP64.  Valid range 4..8.
+ *              ignored for LADDER_FP64.  Valid range 5..8.
  *   ws_budget_bytes  workspace budget; 0 = 0.9 * 0.98 * free device memory
  *              (the safety factors of the paper's C-split rule).
  *   device     CUDA device ordinal.
  *
  * Returns LADDER_OK, LADDER_ERR_ARG, LADDER_ERR_BUDGET (no blocking fits),
- * LADDER_ERR_UNSUPPORTED (LADDER_EMU_INT8, or emulated nchol > 1365) or
+ * LADDER_ERR_UNSUPPORTED (LADDER_EMU_INT8) or
  * LADDER_ERR_CUDA.  Allocates a small device table (freed by
  * ladder_plan_destroy).
  */

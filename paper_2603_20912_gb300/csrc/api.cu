@@ -57,9 +57,10 @@ Geometry geometry_for(const ladder_plan_s& p) {
         // BF16 tcgen05: ~1.5 PFLOP/s sustained; S(S+1)/2 slice products per element.
         const double pairs = 0.5 * p.nslices * (p.nslices + 1);
         const double sm_rate = 1.5e15 / std::max(1, p.num_sms);
-        const int ltn = std::min(128, ((p.no * p.no + 15) / 16) * 16);
-        g = {128, 128, 1, 128, ltn, 1, 0, 0, 25e-6};
-        g.eri_tile_s = 2.0 * 128 * 128 * X * pairs / sm_rate + 3e-6;
+        const int nnt = (p.no * p.no + ladder::kEmuTileN - 1) / ladder::kEmuTileN;
+        const int ltn = ((p.no * p.no + nnt - 1) / nnt + 15) / 16 * 16;
+        g = {128, ladder::kEmuTileN, 1, 128, ltn, 1, 0, 0, 25e-6};
+        g.eri_tile_s = 2.0 * 128 * ladder::kEmuTileN * X * pairs / sm_rate + 3e-6;
         g.lad_tile_s = 2.0 * 128 * ltn * v2 * pairs / sm_rate + 3e-6;
     }
     return g;
@@ -149,16 +150,16 @@ double model_time(const ladder_plan_s& p, const std::vector<BlockPair>& bps) {
 // (int2 (a, b), a-major) and row_start (first packed row of each a).
 // ERI tiles (rt, qt) of one block pair that hold at least one a <= b, in an
 // L2-friendly order: bands of 8 row tiles, all column tiles of a band, then the next band.
-std::vector<int> eri_tiles(const BlockPair& bp, int nv, int tile) {
+std::vector<int> eri_tiles(const BlockPair& bp, int nv, int tile, int tile_n) {
     std::vector<int> out;
     const long long M = (long long)(bp.a1 - bp.a0) * nv, N = (long long)(bp.b1 - bp.b0) * nv;
-    const int nrt = (int)((M + tile - 1) / tile), nqt = (int)((N + tile - 1) / tile);
+    const int nrt = (int)((M + tile - 1) / tile), nqt = (int)((N + tile_n - 1) / tile_n);
     const int band = 8;
     for (int r0 = 0; r0 < nrt; r0 += band)
         for (int qt = 0; qt < nqt; ++qt)
             for (int rt = r0; rt < std::min(nrt, r0 + band); ++rt) {
                 const int a_min = bp.a0 + (int)((long long)rt * tile / nv);
-                const long long last = std::min((long long)(qt + 1) * tile, N) - 1;
+                const long long last = std::min((long long)(qt + 1) * tile_n, N) - 1;
                 const int b_max = bp.b0 + (int)(last / nv);
                 if (a_min <= b_max) {
                     out.push_back(rt);
@@ -174,7 +175,7 @@ int build_tables(ladder_plan_s& p) {
     for (auto& bp : p.bps) n_int2 += bp.npairs;
     if (p.precision != LADDER_FP64)
         for (auto& bp : p.bps) {
-            tiles.push_back(eri_tiles(bp, p.nv, ladder::kEmuTile));
+            tiles.push_back(eri_tiles(bp, p.nv, ladder::kEmuTile, ladder::kEmuTileN));
             n_int2 += tiles.back().size() / 2;
         }
     for (auto& bp : p.bps) n_int += (size_t)(bp.a1 - bp.a0 + 1);
@@ -311,7 +312,7 @@ int make_plan(ladder_plan_s** out, int no, int nv, int nchol, int precision, int
     if (precision != LADDER_FP64 && precision != LADDER_EMU_BF16) return LADDER_ERR_ARG;
     if (nslices == 0) nslices = ladder::kDefaultSlices;
     if (precision == LADDER_EMU_BF16) {
-        if (nslices < 4 || nslices > 8) return LADDER_ERR_ARG;
+        if (nslices < 5 || nslices > 8) return LADDER_ERR_ARG;
         if (!ladder::emu_supported(no, nv, nchol, nslices)) return LADDER_ERR_UNSUPPORTED;
     }
     int ndev = 0;
@@ -556,7 +557,7 @@ int ladder_plan_dry(int no, int nv, int nchol, int precision, int nslices, size_
     if (precision == LADDER_EMU_INT8) return LADDER_ERR_UNSUPPORTED;
     if (precision != LADDER_FP64 && precision != LADDER_EMU_BF16) return LADDER_ERR_ARG;
     if (nslices == 0) nslices = ladder::kDefaultSlices;
-    if (precision == LADDER_EMU_BF16 && (nslices < 4 || nslices > 8)) return LADDER_ERR_ARG;
+    if (precision == LADDER_EMU_BF16 && (nslices < 5 || nslices > 8)) return LADDER_ERR_ARG;
     ladder_plan_s p;
     p.no = no;
     p.nv = nv;

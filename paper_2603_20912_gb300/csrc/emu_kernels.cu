@@ -3,29 +3,32 @@
 // recombined exactly in integer arithmetic; FP64 is used only to scale the
 // final integer sums into R.
 //
-// Digit slices (FP64 emulation by splitting, the approach cited in the
-// introduction; this file fixes the variant): rows of an operand are grouped
-// (64 rows per group) and share one power-of-two exponent e with
+// Digit slices (FP64 emulation by splitting, the approach the introduction
+// cites for Blackwell; this file fixes the variant): rows of an operand are
+// grouped (64 rows per group) and share one power-of-two exponent e with
 // max|x| < 2^(e-1).  N = rint(x 2^(7S-e)) is written in balanced base 128,
 // N = sum_s d_s 128^(S-s) with |d_s| <= 64, and slice plane s holds the BF16
 // value d_s 2^(-7s) (7 significant bits: exact).  A product sum over K keeps
 // the slice pairs with s + t <= S + 1.  Every product d_s d_t fits in 12 bits,
-// so the level sums l = s + t = 2, 3, 4 stay exact FP32 integers (times
-// 2^(-7l)) for K <= 1365; they get separate TMEM accumulators, and the levels
-// >= 5 share a fourth (weight <= 2^-35, rounded in FP32).
+// so each level sum l = s + t (l - 1 pairs) is an exact FP32 integer times
+// 2^(-7l) while K (l - 1) 2^12 <= 2^24.  Levels 2..5 therefore get one exact
+// TMEM accumulator each over chunks of K <= 1024; the levels >= 6 (weight
+// <= 2^-28 of the leading level) share a fifth accumulator whose FP32
+// rounding (the tensor core truncates while aligning) stays below 2^-40.
+// Exactness of the leading levels does not depend on how the hardware rounds.
 //
 // ERI (C-split step 0, 'xac,xbd->acbd'): rows (a,c) and columns (b,d) of the
-// Gram matrix of L^T, K = nchol (one exact chunk).  The epilogue forms the
-// exact fixed-point value I = acc2 2^35 + acc3 2^28 + acc4 2^21 + rn(A5 2^49),
-// V = 2^(e_ac + e_bd - 49) I, and re-slices it for the ladder with one
-// exponent per (a,b) row taken from the Cauchy-Schwarz bound
+// Gram matrix of L^T, K = nchol in chunks of 1024.  Per chunk the epilogue adds
+// I = acc2 2^35 + acc3 2^28 + acc4 2^21 + acc5 2^14 + rn(A6 2^49) into int64
+// registers; V = 2^(e_ac + e_bd - 49) I.  V is re-sliced for the ladder with
+// one exponent per (a,b) row taken from the Cauchy-Schwarz bound
 // |(ac|bd)| <= max_c ||L_ac|| max_d ||L_bd|| (the ERI is a Gram matrix), so no
 // pass over a whole V row is needed before slicing.
 //
 // Ladder (C-split step 1, 'acbd,ecfd->efab'): rows (a,b), columns (i,j),
-// K = (c,d) = nv^2 in exact chunks of 1280.  Per chunk J = acc2 2^28 +
-// acc3 2^21 + acc4 2^14 + rn(A5 2^42); chunk sums are added in int64 (exact,
-// so the order of the split-K atomics does not matter and the result is
+// K = (c,d) = nv^2 in chunks of 1024.  Per chunk J = acc2 2^28 + acc3 2^21 +
+// acc4 2^14 + acc5 2^7 + rn(A6 2^42); chunk sums are added in int64 (exact, so
+// the order of the split-K atomics does not matter and the result is
 // deterministic).  R_ij^ab += 2^(f_ab + g_ij - 42) sum J and the mirror
 // R_ji^ba gets the same value.
 #include <cuda.h>
@@ -48,12 +51,14 @@ using namespace tc;
 constexpr int kG = kExpGroupRows;  // rows per exponent group
 constexpr int kEpiWarps = 8;       // epilogue warps (2 per TMEM lane quadrant)
 constexpr int kThreadsTC = 32 * (2 + kEpiWarps);
-constexpr int kTmemCols = 512;     // 4 accumulators x 128 columns
-constexpr int kAccStride = 128;    // TMEM columns between accumulators
+constexpr int kNumAcc = 5;         // exact levels 2, 3, 4, 5 and the shared levels >= 6
+constexpr int kTmemCols = 512;     // 5 accumulators x 96 columns, rounded up to a power of two
+constexpr int kAccStride = kEmuTileN;  // TMEM columns between accumulators
 constexpr int kSmemBudget = 200 * 1024;
 
 __host__ __device__ constexpr int bk_for(int S) { return S <= 6 ? 32 : 16; }
-__host__ __device__ constexpr int stage_bytes(int S) { return 2 * S * kEmuTile * bk_for(S) * 2; }
+// One stage: S planes of a 128-row tile (A) and S planes of a <= 96-row tile (B), BK columns.
+__host__ __device__ constexpr int stage_bytes(int S) { return S * (kEmuTile + kEmuTileN) * bk_for(S) * 2; }
 __host__ __device__ constexpr int stages_for(int S) {
     return kSmemBudget / stage_bytes(S) < 4 ? kSmemBudget / stage_bytes(S) : 4;
 }
@@ -236,7 +241,7 @@ struct Ring {
 // Issue the S(S+1)/2 slice-pair MMAs of one stage (BK / 16 K-steps) into the 4 accumulators.
 template <int S>
 __device__ __forceinline__ void issue_pairs(uint32_t tmem, uint32_t sA, uint32_t sB, uint32_t a_plane_bytes,
-                                            uint32_t b_plane_bytes, uint32_t idesc, bool (&first)[4]) {
+                                            uint32_t b_plane_bytes, uint32_t idesc, bool (&first)[kNumAcc]) {
     constexpr int BK = bk_for(S);
 #pragma unroll
     for (int kk = 0; kk < BK / 16; ++kk) {
@@ -244,7 +249,7 @@ __device__ __forceinline__ void issue_pairs(uint32_t tmem, uint32_t sA, uint32_t
         for (int s = 0; s < S; ++s) {
 #pragma unroll
             for (int t = 0; t + s < S; ++t) {
-                const int j = (s + t + 2 < 5 ? s + t + 2 : 5) - 2;
+                const int j = (s + t + 2 < 6 ? s + t + 2 : 6) - 2;
                 const uint64_t ad = smem_desc_kmajor(sA + s * a_plane_bytes + kk * 32, BK * 2);
                 const uint64_t bd = smem_desc_kmajor(sB + t * b_plane_bytes + kk * 32, BK * 2);
                 mma_bf16(tmem + j * kAccStride, ad, bd, idesc, first[j] ? 0u : 1u);
@@ -252,6 +257,19 @@ __device__ __forceinline__ void issue_pairs(uint32_t tmem, uint32_t sA, uint32_t
             }
         }
     }
+}
+
+// Integer value of one accumulator in the fixed-point unit 2^(-7 unit_level):
+// accumulator j holds level j+2 (exact, value = integer * 2^(-7(j+2))) for j < 4,
+// and the levels >= 6 (rounded) for j = 4.
+template <int UNIT_LEVEL>
+__device__ __forceinline__ long long acc_fixed(int j, uint32_t bits) {
+    const float x = __uint_as_float(bits);
+    if (j < 4) {
+        const int lvl = j + 2;
+        return (long long)__float2int_rn(x * pow2f(7 * lvl)) << (7 * (UNIT_LEVEL - lvl));
+    }
+    return __float2ll_rn(x * pow2f(7 * UNIT_LEVEL));
 }
 
 struct EriArgs {
@@ -266,10 +284,12 @@ struct EriArgs {
 };
 
 // ------------------------------------------------------------------ ERI kernel
+// One 128 (a,c) x 96 (b,d) tile per work item; K = nchol in chunks of kEmuChunkK.
 template <int S>
-__global__ void __launch_bounds__(kThreadsTC, 1) eri_emu_kernel(const __grid_constant__ CUtensorMap tm_lt, EriArgs p) {
+__global__ void __launch_bounds__(kThreadsTC, 1) eri_emu_kernel(const __grid_constant__ CUtensorMap tm_a,
+                                                                const __grid_constant__ CUtensorMap tm_b, EriArgs p) {
     constexpr int BK = bk_for(S), STAGES = stages_for(S);
-    constexpr uint32_t PLANE = kEmuTile * BK * 2;  // bytes of one 128-row plane
+    constexpr uint32_t APLANE = kEmuTile * BK * 2, BPLANE = kEmuTileN * BK * 2;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     __shared__ uint64_t full[STAGES], empty[STAGES], acc_full, acc_empty, done;
@@ -284,7 +304,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1) eri_emu_kernel(const __grid_con
         mbar_init(&acc_empty, kEpiWarps);
         mbar_init(&done, 1);
         fence_barrier_init();
-        tma_prefetch_desc(&tm_lt);
+        tma_prefetch_desc(&tm_a);
+        tma_prefetch_desc(&tm_b);
     }
     if (warp == 1) tmem_alloc(&tmem_base, kTmemCols);
     tc_fence_before();
@@ -292,6 +313,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1) eri_emu_kernel(const __grid_con
     tc_fence_after();
     const uint32_t tmem = tmem_base;
     const int nkb = (p.nchol + BK - 1) / BK;
+    const int kb_per_chunk = kEmuChunkK / BK;
+    const int nch = (nkb + kb_per_chunk - 1) / kb_per_chunk;
 
     if (warp == 0 && lane == 0) {
         // ---------------- TMA producer
@@ -301,13 +324,13 @@ __global__ void __launch_bounds__(kThreadsTC, 1) eri_emu_kernel(const __grid_con
         for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
             const int2 tq = p.tiles[t];
             const int arow = p.a0 * p.nv + tq.x * kEmuTile;
-            const int brow = p.b0 * p.nv + tq.y * kEmuTile;
+            const int brow = p.b0 * p.nv + tq.y * kEmuTileN;
             for (int kb = 0; kb < nkb && ok; ++kb) {
                 if (!(ok = mbar_wait(&empty[ring.stage], ring.phase ^ 1u, p.status, kStatusTimeout))) break;
                 unsigned char* st = smem + ring.stage * stage_bytes(S);
                 mbar_arrive_expect_tx(&full[ring.stage], stage_bytes(S));
-                tma_load_3d(st, &tm_lt, &full[ring.stage], kb * BK, arow, 0);
-                tma_load_3d(st + S * PLANE, &tm_lt, &full[ring.stage], kb * BK, brow, 0);
+                tma_load_3d(st, &tm_a, &full[ring.stage], kb * BK, arow, 0);
+                tma_load_3d(st + S * APLANE, &tm_b, &full[ring.stage], kb * BK, brow, 0);
                 ++issued[ring.stage];
                 ring.next(STAGES);
             }
@@ -318,64 +341,81 @@ __global__ void __launch_bounds__(kThreadsTC, 1) eri_emu_kernel(const __grid_con
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer
         Ring ring;
-        const uint32_t idesc = idesc_bf16_f32(kEmuTile, kEmuTile);
+        const uint32_t idesc = idesc_bf16_f32(kEmuTile, kEmuTileN);
         bool ok = true;
         int it = 0;
-        for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x, ++it) {
-            if (!(ok = mbar_wait(&acc_empty, (uint32_t)(it & 1) ^ 1u, p.status, kStatusTimeout))) break;
-            tc_fence_after();
-            bool first[4] = {true, true, true, true};
-            for (int kb = 0; kb < nkb && ok; ++kb) {
-                if (!(ok = mbar_wait(&full[ring.stage], ring.phase, p.status, kStatusTimeout))) break;
+        for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
+            for (int ch = 0; ch < nch && ok; ++ch, ++it) {
+                if (!(ok = mbar_wait(&acc_empty, (uint32_t)(it & 1) ^ 1u, p.status, kStatusTimeout))) break;
                 tc_fence_after();
-                const uint32_t st = smem_u32(smem + ring.stage * stage_bytes(S));
-                issue_pairs<S>(tmem, st, st + S * PLANE, PLANE, PLANE, idesc, first);
-                mma_commit(&empty[ring.stage]);
-                ring.next(STAGES);
+                bool first[kNumAcc] = {true, true, true, true, true};
+                const int kb1 = min((ch + 1) * kb_per_chunk, nkb);
+                for (int kb = ch * kb_per_chunk; kb < kb1 && ok; ++kb) {
+                    if (!(ok = mbar_wait(&full[ring.stage], ring.phase, p.status, kStatusTimeout))) break;
+                    tc_fence_after();
+                    const uint32_t st = smem_u32(smem + ring.stage * stage_bytes(S));
+                    issue_pairs<S>(tmem, st, st + S * APLANE, APLANE, BPLANE, idesc, first);
+                    mma_commit(&empty[ring.stage]);
+                    ring.next(STAGES);
+                }
+                if (ok) mma_commit(&acc_full);
             }
-            if (ok) mma_commit(&acc_full);
         }
         mma_commit(&done);
         mbar_wait(&done, 0, p.status, kStatusTimeout);
     } else if (warp >= 2) {
-        // ---------------- epilogue: exact recombination and re-slicing into the V planes
+        // ---------------- epilogue: exact int64 recombination, then re-slicing into the V planes.
+        // Warp: TMEM lane quadrant q (tile rows 32q..32q+31), columns 48h..48h+47 (3 chunks of 16).
         const int q = warp & 3, h = (warp - 2) >> 2;
         const int Mrows = p.na * p.nv, Ncols = p.nb * p.nv;
+        long long run[3][16];
         int it = 0;
-        for (int t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++it) {
-            if (!mbar_wait(&acc_full, (uint32_t)(it & 1), p.status, kStatusTimeout)) break;
-            tc_fence_after();
+        bool ok = true;
+        for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc)
+#pragma unroll
+                for (int k = 0; k < 16; ++k) run[cc][k] = 0;
+            for (int ch = 0; ch < nch; ++ch, ++it) {
+                if (!(ok = mbar_wait(&acc_full, (uint32_t)(it & 1), p.status, kStatusTimeout))) break;
+                tc_fence_after();
+#pragma unroll
+                for (int cc = 0; cc < 3; ++cc) {
+#pragma unroll
+                    for (int j = 0; j < kNumAcc; ++j) {
+                        uint32_t v[16];
+                        tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + j * kAccStride + 48 * h + 16 * cc, v);
+                        tmem_ld_wait();
+#pragma unroll
+                        for (int k = 0; k < 16; ++k) run[cc][k] += acc_fixed<7>(j, v[k]);
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&acc_empty);
+            }
+            if (!ok) break;
             const int2 tq = p.tiles[t];
             const int r_local = tq.x * kEmuTile + 32 * q + lane;
-            const bool valid_r = r_local < Mrows;
+            if (r_local >= Mrows) continue;
             const int a = p.a0 + r_local / p.nv, c = r_local % p.nv;
-            const int e_ac = valid_r ? p.lt_exp[(p.a0 * p.nv + r_local) / kG] : 0;
-            const int rs = valid_r ? p.row_start[a - p.a0] : 0;
-#pragma unroll 1
-            for (int c0 = 0; c0 < 64; c0 += 16) {
-                uint32_t acc[4][16];
-                const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + 64 * h + c0;
+            const int e_ac = p.lt_exp[(p.a0 * p.nv + r_local) / kG];
+            const int rs = p.row_start[a - p.a0];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) tmem_ld16(taddr + j * kAccStride, acc[j]);
-                tmem_ld_wait();
-                int col = tq.y * kEmuTile + 64 * h + c0;
+            for (int cc = 0; cc < 3; ++cc) {
+                int col = tq.y * kEmuTileN + 48 * h + 16 * cc;
                 int b = p.b0 + col / p.nv, d = col % p.nv;
 #pragma unroll
                 for (int k = 0; k < 16; ++k, ++col) {
-                    if (valid_r && col < Ncols && a <= b) {
-                        const long long i2 = __float2int_rn(__uint_as_float(acc[0][k]) * 0x1p14f);
-                        const long long i3 = __float2int_rn(__uint_as_float(acc[1][k]) * 0x1p21f);
-                        const long long i4 = __float2int_rn(__uint_as_float(acc[2][k]) * 0x1p28f);
-                        const long long i5 = __float2ll_rn(__uint_as_float(acc[3][k]) * 0x1p49f);
-                        const long long I = (i2 << 35) + (i3 << 28) + (i4 << 21) + i5;
+                    if (col < Ncols && a <= b) {
                         const int e_bd = p.lt_exp[(p.b0 * p.nv + col) / kG];
                         const int sh = p.f_tab[a * p.nv + b] - e_ac - e_bd + 49 - 7 * S;
-                        const long long Np = rescale(I, sh, 1LL << (7 * S - 1), p.status);
+                        const long long Np = rescale(run[cc][k], sh, 1LL << (7 * S - 1), p.status);
                         __nv_bfloat16 dg[S];
                         digits_of<S>(Np, dg);
                         const size_t off = (size_t)(rs + (b - max(a, p.b0))) * p.kpad + (size_t)c * p.nv + d;
 #pragma unroll
-                        for (int s = 0; s < S; ++s) p.vplanes[s * p.plane_stride + off] = dg[s];
+                        for (int s2 = 0; s2 < S; ++s2) p.vplanes[s2 * p.plane_stride + off] = dg[s2];
                     }
                     if (++d == p.nv) {
                         d = 0;
@@ -383,9 +423,6 @@ __global__ void __launch_bounds__(kThreadsTC, 1) eri_emu_kernel(const __grid_con
                     }
                 }
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&acc_empty);
         }
     }
     tc_fence_before();
@@ -404,6 +441,9 @@ struct LadArgs {
     unsigned* status;
 };
 
+// Work unit = (row tile, column tile, K chunk), chunk fastest; each CTA takes a
+// contiguous range of units (stream-K) and flushes its int64 sums with atomics
+// whenever its (row tile, column tile) changes.
 template <int S>
 __global__ void __launch_bounds__(kThreadsTC, 1) ladder_emu_kernel(const __grid_constant__ CUtensorMap tm_v,
                                                                    const __grid_constant__ CUtensorMap tm_t,
@@ -466,7 +506,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) ladder_emu_kernel(const __grid_
             const int ch = (int)(u % p.n_ch);
             if (!(ok = mbar_wait(&acc_empty, (uint32_t)(it & 1) ^ 1u, p.status, kStatusTimeout))) break;
             tc_fence_after();
-            bool first[4] = {true, true, true, true};
+            bool first[kNumAcc] = {true, true, true, true, true};
             const int kb1 = min((ch + 1) * p.kb_per_chunk, p.nkb);
             for (int kb = ch * p.kb_per_chunk; kb < kb1 && ok; ++kb) {
                 if (!(ok = mbar_wait(&full[ring.stage], ring.phase, p.status, kStatusTimeout))) break;
@@ -481,12 +521,12 @@ __global__ void __launch_bounds__(kThreadsTC, 1) ladder_emu_kernel(const __grid_
         mma_commit(&done);
         mbar_wait(&done, 0, p.status, kStatusTimeout);
     } else if (warp >= 2) {
-        // Each warp: TMEM lane quadrant q, column chunks ci = h, h+2, h+4, h+6 (16 columns each).
+        // Each warp: TMEM lane quadrant q, column chunks ci = h, h+2, h+4 (16 columns each).
         const int q = warp & 3, h = (warp - 2) >> 2;
         const int nchunks = p.BN / 16;
-        long long run[4][16];
+        long long run[3][16];
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < 3; ++i)
 #pragma unroll
             for (int k = 0; k < 16; ++k) run[i][k] = 0;
         int it = 0;
@@ -494,21 +534,16 @@ __global__ void __launch_bounds__(kThreadsTC, 1) ladder_emu_kernel(const __grid_
             if (!mbar_wait(&acc_full, (uint32_t)(it & 1), p.status, kStatusTimeout)) break;
             tc_fence_after();
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
+            for (int i = 0; i < 3; ++i) {
                 const int ci = h + 2 * i;
                 if (ci < nchunks) {
-                    uint32_t acc[4][16];
-                    const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + 16 * ci;
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) tmem_ld16(taddr + j * kAccStride, acc[j]);
-                    tmem_ld_wait();
+                    for (int j = 0; j < kNumAcc; ++j) {
+                        uint32_t v[16];
+                        tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + j * kAccStride + 16 * ci, v);
+                        tmem_ld_wait();
 #pragma unroll
-                    for (int k = 0; k < 16; ++k) {
-                        const long long i2 = __float2int_rn(__uint_as_float(acc[0][k]) * 0x1p14f);
-                        const long long i3 = __float2int_rn(__uint_as_float(acc[1][k]) * 0x1p21f);
-                        const long long i4 = __float2int_rn(__uint_as_float(acc[2][k]) * 0x1p28f);
-                        const long long i5 = __float2ll_rn(__uint_as_float(acc[3][k]) * 0x1p42f);
-                        run[i][k] += (i2 << 28) + (i3 << 21) + (i4 << 14) + i5;
+                        for (int k = 0; k < 16; ++k) run[i][k] += acc_fixed<6>(j, v[k]);
                     }
                 }
             }
@@ -521,7 +556,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) ladder_emu_kernel(const __grid_
                 const int nt = (int)(tile % p.n_nt), mt = (int)(tile / p.n_nt);
                 const int m = mt * kEmuTile + 32 * q + lane;
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
+                for (int i = 0; i < 3; ++i) {
                     const int ci = h + 2 * i;
                     if (ci < nchunks) {
 #pragma unroll
@@ -599,7 +634,7 @@ T* at(void* ws, size_t off) {
 }
 
 int ladder_bn(int no2) {
-    const int nt = (no2 + kEmuTile - 1) / kEmuTile;
+    const int nt = (no2 + kEmuTileN - 1) / kEmuTileN;
     const int per = (no2 + nt - 1) / nt;
     return std::max(16, (per + 15) / 16 * 16);
 }
@@ -650,16 +685,18 @@ cudaError_t block_impl(const ladder_plan_s& p, const BlockPair& bp, double* R, v
 
     const int2* table = reinterpret_cast<const int2*>(p.d_tables);
     const int* row_start = reinterpret_cast<const int*>(p.d_tables) + bp.rows_off;
-    CUtensorMap tm_lt, tm_v, tm_t;
-    if (!make_tmap(&tm_lt, at<char>(ws, p.ws.lt_slices), p.nchol, nv2, S, (uint64_t)xpad * 2, (uint64_t)nv2 * xpad * 2,
-                   BK, kEmuTile))
+    CUtensorMap tm_la, tm_lb, tm_v, tm_t;
+    if (!make_tmap(&tm_la, at<char>(ws, p.ws.lt_slices), p.nchol, nv2, S, (uint64_t)xpad * 2, (uint64_t)nv2 * xpad * 2,
+                   BK, kEmuTile) ||
+        !make_tmap(&tm_lb, at<char>(ws, p.ws.lt_slices), p.nchol, nv2, S, (uint64_t)xpad * 2, (uint64_t)nv2 * xpad * 2,
+                   BK, kEmuTileN))
         return cudaErrorInvalidValue;
     EriArgs ea{p.nv, p.nchol, bp.a0, bp.a1 - bp.a0, bp.b0, bp.b1 - bp.b0, kpad, bp.ntiles, vplane,
                table + bp.tiles_off, row_start, at<int>(ws, p.ws.lt_exp), at<int>(ws, p.ws.v_exp),
                at<__nv_bfloat16>(ws, p.ws.v_blk), p.d_status};
     {
         LaunchTimer tm(p, s, LADDER_KERNEL_ERI);
-        eri_emu_kernel<S><<<std::max(1, std::min(bp.ntiles, p.num_sms)), kThreadsTC, smem, s>>>(tm_lt, ea);
+        eri_emu_kernel<S><<<std::max(1, std::min(bp.ntiles, p.num_sms)), kThreadsTC, smem, s>>>(tm_la, tm_lb, ea);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
 
@@ -702,12 +739,12 @@ cudaError_t block_impl(const ladder_plan_s& p, const BlockPair& bp, double* R, v
 bool emu_supported(int no, int nv, int nchol, int nslices) {
     (void)no;
     (void)nv;
-    return nchol <= kEmuMaxExactK && nslices >= 4 && nslices <= 8;
+    (void)nchol;
+    return nslices >= 5 && nslices <= 8;
 }
 
 cudaError_t launch_emu_prep(const ladder_plan_s& p, const double* L, const double* t2, void* ws, cudaStream_t s) {
     switch (p.nslices) {
-        case 4: return prep_impl<4>(p, L, t2, ws, s);
         case 5: return prep_impl<5>(p, L, t2, ws, s);
         case 6: return prep_impl<6>(p, L, t2, ws, s);
         case 7: return prep_impl<7>(p, L, t2, ws, s);
@@ -718,7 +755,6 @@ cudaError_t launch_emu_prep(const ladder_plan_s& p, const double* L, const doubl
 
 cudaError_t launch_emu_block(const ladder_plan_s& p, const BlockPair& bp, double* R, void* ws, cudaStream_t s) {
     switch (p.nslices) {
-        case 4: return block_impl<4>(p, bp, R, ws, s);
         case 5: return block_impl<5>(p, bp, R, ws, s);
         case 6: return block_impl<6>(p, bp, R, ws, s);
         case 7: return block_impl<7>(p, bp, R, ws, s);

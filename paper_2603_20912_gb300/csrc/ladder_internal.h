@@ -16,9 +16,9 @@ constexpr int kAlign = 256;                 // workspace sub-buffer alignment (b
 constexpr int kDefaultSlices = 6;           // digit slices per operand (emulated path)
 constexpr int kDigitBits = 7;               // bits per signed digit, |digit| <= 64
 constexpr int kExpGroupRows = 64;           // rows sharing one power-of-two exponent
-constexpr int kEmuMaxExactK = 1365;         // K per exact accumulation chunk: 3 * 64^2 * K <= 2^24
-constexpr int kEmuChunkK = 1280;            // ladder K chunk (multiple of 64, <= kEmuMaxExactK)
-constexpr int kEmuTile = 128;               // tcgen05 tile rows (M) and ERI tile columns (N)
+constexpr int kEmuChunkK = 1024;            // K per exact chunk: level 5 has 4 pairs, 4 * 64^2 * K <= 2^24
+constexpr int kEmuTile = 128;               // tcgen05 tile rows (M)
+constexpr int kEmuTileN = 96;               // widest tile N: 5 TMEM accumulators x 96 <= 512 columns
 
 // Device status bits (ORed into the plan's status word by kernels).
 constexpr unsigned kStatusTimeout = 1u;

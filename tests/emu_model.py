@@ -14,16 +14,16 @@ Scheme (FP64 emulated by BF16 digit slices, Ozaki-style splitting):
   balanced base 128: N = sum_s d_s 128^(S-s), |d_s| <= 64.  Slice plane s
   holds d_s 2^(-7s) (exact in BF16: 7 significant bits).
 * A product sum over K of two sliced operands keeps the pairs s + t <= S + 1.
-  Levels l = s + t = 2, 3, 4 are exact integers while K * (l-1) * 64^2
-  <= 2^24 (K <= 1365): they accumulate in separate FP32 accumulators; the
-  levels >= 5 share a fourth FP32 accumulator (inexact, weight <= 2^-35).
+  Levels l = s + t = 2..5 are exact integers while K * (l-1) * 64^2 <= 2^24
+  (chunks of K <= 1024): each has its own FP32 accumulator; the levels >= 6
+  share a fifth (inexact, weight <= 2^-28 of the leading level).
 * ERI (K = nchol): the level sums form I = acc2 2^35 + acc3 2^28 + acc4 2^21
-  + round(A5 2^49), V = 2^(e_ac + e_bd - 49) I.  V is re-sliced per pair row
-  (a, b) with the exponent f_ab of the Cauchy-Schwarz bound
+  + acc5 2^14 + round(A6 2^49), V = 2^(e_ac + e_bd - 49) I.  V is re-sliced
+  per pair row (a, b) with the exponent f_ab of the Cauchy-Schwarz bound
   |(ac|bd)| <= max_c ||L_ac|| max_d ||L_bd||.
-* Ladder (K = nv^2, chunks of 1280): per chunk J = acc2 2^28 + acc3 2^21
-  + acc4 2^14 + round(A5 2^42), summed exactly over chunks in int64;
-  R_ij^ab = 2^(f_ab + g_ij - 42) sum J.
+* Ladder (K = nv^2, chunks of 1024): per chunk J = acc2 2^28 + acc3 2^21
+  + acc4 2^14 + acc5 2^7 + round(A6 2^42), summed exactly over chunks in
+  int64; R_ij^ab = 2^(f_ab + g_ij - 42) sum J.
 """
 from __future__ import annotations
 
@@ -33,7 +33,7 @@ import numpy as np
 
 DIGIT_BITS = 7
 GROUP = 64
-CHUNK = 1280
+CHUNK = 1024
 
 
 def group_exponents(x2d: np.ndarray, group: int = GROUP) -> np.ndarray:
@@ -72,22 +72,21 @@ def from_digits(d: np.ndarray, erow: np.ndarray) -> np.ndarray:
 
 
 def level_sums(dA: np.ndarray, dB: np.ndarray):
-    """Exact integer level sums acc2, acc3, acc4 and the weighted tail A5 (float64) of
+    """Exact integer level sums acc2..acc5 and the weighted tail A6 (float64) of
     sum_k A[m,k] B[n,k] over slice pairs s + t <= S + 1 (s, t 1-based)."""
     S = dA.shape[0]
-    acc = {2: 0, 3: 0, 4: 0}
-    a5 = 0.0
+    z = np.zeros((dA.shape[1], dB.shape[1]), dtype=np.int64)
+    acc = {2: z.copy(), 3: z.copy(), 4: z.copy(), 5: z.copy()}
+    a6 = np.zeros(z.shape)
     for s in range(1, S + 1):
         for t in range(1, S + 2 - s):
             prod = dA[s - 1] @ dB[t - 1].T
             lvl = s + t
-            if lvl <= 4:
+            if lvl <= 5:
                 acc[lvl] = acc[lvl] + prod
             else:
-                a5 = a5 + np.ldexp(prod.astype(np.float64), -DIGIT_BITS * lvl)
-    z = np.zeros((dA.shape[1], dB.shape[1]), dtype=np.int64)
-    return (acc[2] if not np.isscalar(acc[2]) else z, acc[3] if not np.isscalar(acc[3]) else z,
-            acc[4] if not np.isscalar(acc[4]) else z, a5 if not np.isscalar(a5) else np.zeros(z.shape))
+                a6 = a6 + np.ldexp(prod.astype(np.float64), -DIGIT_BITS * lvl)
+    return acc[2], acc[3], acc[4], acc[5], a6
 
 
 def _round_shift(I: np.ndarray, sh: np.ndarray) -> np.ndarray:
@@ -117,11 +116,13 @@ def emulated_ladder(L: np.ndarray, t2: np.ndarray, S: int = 6, group: int = GROU
     """R = ladder(L, t2) through the emulation scheme (all pairs, no a <= b packing)."""
     nchol, nv, _ = L.shape
     no = t2.shape[0]
-    assert nchol <= 1365
     Lt = np.ascontiguousarray(L.reshape(nchol, nv * nv).T)     # rows (a, c), K = P
     dL, eL = to_digits(Lt, S, group)
-    a2, a3, a4, a5 = level_sums(dL, dL)                          # [(ac), (bd)]
-    I = (a2 << 35) + (a3 << 28) + (a4 << 21) + np.rint(np.ldexp(a5, 49)).astype(np.int64)
+    I = np.zeros((nv * nv, nv * nv), dtype=np.int64)
+    for k0 in range(0, nchol, chunk):
+        sl = slice(k0, min(nchol, k0 + chunk))
+        a2, a3, a4, a5, a6 = level_sums(dL[:, :, sl], dL[:, :, sl])   # [(ac), (bd)]
+        I += (a2 << 35) + (a3 << 28) + (a4 << 21) + (a5 << 14) + np.rint(np.ldexp(a6, 49)).astype(np.int64)
     f = pair_exponent_bound(L)
     # rows (a, c), cols (b, d) -> V[(a, b), (c, d)]
     I4 = I.reshape(nv, nv, nv, nv).transpose(0, 2, 1, 3)          # [a, b, c, d]
@@ -142,8 +143,8 @@ def emulated_ladder(L: np.ndarray, t2: np.ndarray, S: int = 6, group: int = GROU
     J = np.zeros((nv * nv, no * no), dtype=np.int64)
     for k0 in range(0, K, chunk):
         sl = slice(k0, min(K, k0 + chunk))
-        b2, b3, b4, b5 = level_sums(dV[:, :, sl], dT[:, :, sl])
-        J += (b2 << 28) + (b3 << 21) + (b4 << 14) + np.rint(np.ldexp(b5, 42)).astype(np.int64)
+        b2, b3, b4, b5, b6 = level_sums(dV[:, :, sl], dT[:, :, sl])
+        J += (b2 << 28) + (b3 << 21) + (b4 << 14) + (b5 << 7) + np.rint(np.ldexp(b6, 42)).astype(np.int64)
     fab = f.reshape(nv * nv)
     Rp = np.ldexp(J.astype(np.float64), fab[:, None] + eT[None, :] - 42)   # [(a, b), (i, j)]
     return Rp.T.reshape(no, no, nv, nv)

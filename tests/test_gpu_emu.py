@@ -54,11 +54,14 @@ def test_c1_matches_cpu_model_of_the_scheme():
     L, t2, _, _ = make_inputs(s.no, s.nv, s.nchol, s.seed)
     R, _ = gpu_ladder(L, t2, EMU)
     model = emulated_ladder(L, t2, S=6)
-    # The model is exact except for the FP32 rounding order of the level >= 5 accumulator.
-    assert rel_fro(R, model) <= 1e-13
+    # The model computes every (a, b) from its own V row; the library forms a > b from the
+    # mirror R_ji^ba, so compare the a <= b half, where both evaluate the same digits.  The only
+    # difference left is the FP32 rounding of the levels >= 6 (weight <= 2^-28).
+    iu = np.triu_indices(s.nv)
+    assert rel_fro(R[:, :, iu[0], iu[1]], model[:, :, iu[0], iu[1]]) <= 1e-13
 
 
-@pytest.mark.parametrize("S,tol", [(4, 3e-6), (5, 3e-8), (6, 1e-10), (7, 1e-11), (8, 1e-12)])
+@pytest.mark.parametrize("S,tol", [(5, 1e-8), (6, 1e-10), (7, 1e-11), (8, 1e-12)])
 def test_slice_count_controls_the_error(S, tol):
     s = CONFIGS["c1"]
     L, t2, _, _ = make_inputs(s.no, s.nv, s.nchol, s.seed)
@@ -120,12 +123,17 @@ def test_rejects_unsupported_requests():
     with pytest.raises(lad.LadderError) as e:
         lad.ladder_plan(5, 19, 72, lad.LADDER_EMU_INT8)
     assert e.value.status == lad.LADDER_ERR_UNSUPPORTED
-    with pytest.raises(lad.LadderError) as e:
-        lad.ladder_plan(5, 19, 2000, EMU)          # nchol beyond one exact chunk
-    assert e.value.status == lad.LADDER_ERR_UNSUPPORTED
-    with pytest.raises(lad.LadderError) as e:
-        lad.ladder_plan(5, 19, 72, EMU, nslices=3)
-    assert e.value.status == lad.LADDER_ERR_ARG
+    for bad in (4, 9):
+        with pytest.raises(lad.LadderError) as e:
+            lad.ladder_plan(5, 19, 72, EMU, nslices=bad)
+        assert e.value.status == lad.LADDER_ERR_ARG
+
+
+def test_nchol_spanning_several_exact_chunks():
+    # nchol > 1024: the ERI accumulates two exact chunks in int64 registers.
+    L, t2, _, _ = make_inputs(3, 23, 1500, seed=55)
+    R, _ = gpu_ladder(L, t2, EMU)
+    assert rel_fro(R, oracle.ladder(L, t2)) <= TOL_R
 
 
 @pytest.mark.parametrize("name", ["c2", "c3"])
