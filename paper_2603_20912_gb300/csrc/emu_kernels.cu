@@ -401,25 +401,52 @@ __global__ void __launch_bounds__(kThreadsTC, 1) eri_emu_kernel(const __grid_con
             const int a = p.a0 + r_local / p.nv, c = r_local % p.nv;
             const int e_ac = p.lt_exp[(p.a0 * p.nv + r_local) / kG];
             const int rs = p.row_start[a - p.a0];
+            const bool vec = (p.nv & 7) == 0;  // 8 consecutive d of one (a,b) row are 16-byte aligned
 #pragma unroll
             for (int cc = 0; cc < 3; ++cc) {
-                int col = tq.y * kEmuTileN + 48 * h + 16 * cc;
-                int b = p.b0 + col / p.nv, d = col % p.nv;
+                const int col0 = tq.y * kEmuTileN + 48 * h + 16 * cc;
+                if (vec) {
+                    // Two runs of 8 columns; each lies in one b (nv % 8 == 0) and starts at d % 8 == 0.
 #pragma unroll
-                for (int k = 0; k < 16; ++k, ++col) {
-                    if (col < Ncols && a <= b) {
+                    for (int half = 0; half < 2; ++half) {
+                        const int col = col0 + 8 * half;
+                        const int b = p.b0 + col / p.nv, d = col % p.nv;
+                        if (col >= Ncols || a > b) continue;
                         const int e_bd = p.lt_exp[(p.b0 * p.nv + col) / kG];
                         const int sh = p.f_tab[a * p.nv + b] - e_ac - e_bd + 49 - 7 * S;
-                        const long long Np = rescale(run[cc][k], sh, 1LL << (7 * S - 1), p.status);
-                        __nv_bfloat16 dg[S];
-                        digits_of<S>(Np, dg);
+                        __align__(16) __nv_bfloat16 out[S][8];
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) {
+                            __nv_bfloat16 dg[S];
+                            digits_of<S>(rescale(run[cc][8 * half + k], sh, 1LL << (7 * S - 1), p.status), dg);
+#pragma unroll
+                            for (int s2 = 0; s2 < S; ++s2) out[s2][k] = dg[s2];
+                        }
                         const size_t off = (size_t)(rs + (b - max(a, p.b0))) * p.kpad + (size_t)c * p.nv + d;
 #pragma unroll
-                        for (int s2 = 0; s2 < S; ++s2) p.vplanes[s2 * p.plane_stride + off] = dg[s2];
+                        for (int s2 = 0; s2 < S; ++s2)
+                            *reinterpret_cast<uint4*>(p.vplanes + s2 * p.plane_stride + off) =
+                                *reinterpret_cast<const uint4*>(out[s2]);
                     }
-                    if (++d == p.nv) {
-                        d = 0;
-                        ++b;
+                } else {
+                    int col = col0;
+                    int b = p.b0 + col / p.nv, d = col % p.nv;
+#pragma unroll
+                    for (int k = 0; k < 16; ++k, ++col) {
+                        if (col < Ncols && a <= b) {
+                            const int e_bd = p.lt_exp[(p.b0 * p.nv + col) / kG];
+                            const int sh = p.f_tab[a * p.nv + b] - e_ac - e_bd + 49 - 7 * S;
+                            const long long Np = rescale(run[cc][k], sh, 1LL << (7 * S - 1), p.status);
+                            __nv_bfloat16 dg[S];
+                            digits_of<S>(Np, dg);
+                            const size_t off = (size_t)(rs + (b - max(a, p.b0))) * p.kpad + (size_t)c * p.nv + d;
+#pragma unroll
+                            for (int s2 = 0; s2 < S; ++s2) p.vplanes[s2 * p.plane_stride + off] = dg[s2];
+                        }
+                        if (++d == p.nv) {
+                            d = 0;
+                            ++b;
+                        }
                     }
                 }
             }
