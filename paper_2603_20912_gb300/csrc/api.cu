@@ -149,12 +149,13 @@ double model_time(const ladder_plan_s& p, const std::vector<BlockPair>& bps) {
 // Build device tables for the chosen blocking: per block pair its pair list
 // (int2 (a, b), a-major) and row_start (first packed row of each a).
 // ERI tiles (rt, qt) of one block pair that hold at least one a <= b, in an
-// L2-friendly order: bands of 8 row tiles, all column tiles of a band, then the next band.
-std::vector<int> eri_tiles(const BlockPair& bp, int nv, int tile, int tile_n) {
+// L2-friendly order: a band of row tiles whose operand slices take ~40 MB of L2
+// stays resident while every column tile of the band streams past it.
+std::vector<int> eri_tiles(const BlockPair& bp, int nv, int tile, int tile_n, size_t row_bytes) {
     std::vector<int> out;
     const long long M = (long long)(bp.a1 - bp.a0) * nv, N = (long long)(bp.b1 - bp.b0) * nv;
     const int nrt = (int)((M + tile - 1) / tile), nqt = (int)((N + tile_n - 1) / tile_n);
-    const int band = 8;
+    const int band = (int)std::max<size_t>(8, std::min<size_t>(64, (40u << 20) / std::max<size_t>(1, row_bytes * tile)));
     for (int r0 = 0; r0 < nrt; r0 += band)
         for (int qt = 0; qt < nqt; ++qt)
             for (int rt = r0; rt < std::min(nrt, r0 + band); ++rt) {
@@ -175,7 +176,8 @@ int build_tables(ladder_plan_s& p) {
     for (auto& bp : p.bps) n_int2 += bp.npairs;
     if (p.precision != LADDER_FP64)
         for (auto& bp : p.bps) {
-            tiles.push_back(eri_tiles(bp, p.nv, ladder::kEmuTile, ladder::kEmuTileN));
+            tiles.push_back(eri_tiles(bp, p.nv, ladder::kEmuTile, ladder::kEmuTileN,
+                                      (size_t)p.nslices * 2 * ladder::align_up((size_t)p.nchol, 8)));
             n_int2 += tiles.back().size() / 2;
         }
     for (auto& bp : p.bps) n_int += (size_t)(bp.a1 - bp.a0 + 1);

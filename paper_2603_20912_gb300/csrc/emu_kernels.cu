@@ -56,7 +56,7 @@ constexpr int kTmemCols = 512;     // 5 accumulators x 96 columns, rounded up to
 constexpr int kAccStride = kEmuTileN;  // TMEM columns between accumulators
 constexpr int kSmemBudget = 200 * 1024;
 
-__host__ __device__ constexpr int bk_for(int S) { return S <= 6 ? 32 : 16; }
+__host__ __device__ constexpr int bk_for(int S) { return S <= 4 ? 32 : 16; }
 // One stage: S planes of a 128-row tile (A) and S planes of a <= 96-row tile (B), BK columns.
 __host__ __device__ constexpr int stage_bytes(int S) { return S * (kEmuTile + kEmuTileN) * bk_for(S) * 2; }
 __host__ __device__ constexpr int stages_for(int S) {
@@ -381,14 +381,20 @@ __global__ void __launch_bounds__(kThreadsTC, 1) eri_emu_kernel(const __grid_con
                 tc_fence_after();
 #pragma unroll
                 for (int cc = 0; cc < 3; ++cc) {
+                    const uint32_t base = tmem + ((uint32_t)(32 * q) << 16) + 48 * h + 16 * cc;
+                    uint32_t v[3][16];
+                    tmem_ld16(base, v[0]);
+                    tmem_ld16(base + kAccStride, v[1]);
+                    tmem_ld16(base + 2 * kAccStride, v[2]);
+                    tmem_ld_wait();
 #pragma unroll
-                    for (int j = 0; j < kNumAcc; ++j) {
-                        uint32_t v[16];
-                        tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + j * kAccStride + 48 * h + 16 * cc, v);
-                        tmem_ld_wait();
+                    for (int k = 0; k < 16; ++k)
+                        run[cc][k] += acc_fixed<7>(0, v[0][k]) + acc_fixed<7>(1, v[1][k]) + acc_fixed<7>(2, v[2][k]);
+                    tmem_ld16(base + 3 * kAccStride, v[0]);
+                    tmem_ld16(base + 4 * kAccStride, v[1]);
+                    tmem_ld_wait();
 #pragma unroll
-                        for (int k = 0; k < 16; ++k) run[cc][k] += acc_fixed<7>(j, v[k]);
-                    }
+                    for (int k = 0; k < 16; ++k) run[cc][k] += acc_fixed<7>(3, v[0][k]) + acc_fixed<7>(4, v[1][k]);
                 }
                 tc_fence_before();
                 __syncwarp();
@@ -564,14 +570,20 @@ __global__ void __launch_bounds__(kThreadsTC, 1) ladder_emu_kernel(const __grid_
             for (int i = 0; i < 3; ++i) {
                 const int ci = h + 2 * i;
                 if (ci < nchunks) {
+                    const uint32_t base = tmem + ((uint32_t)(32 * q) << 16) + 16 * ci;
+                    uint32_t v[3][16];
+                    tmem_ld16(base, v[0]);
+                    tmem_ld16(base + kAccStride, v[1]);
+                    tmem_ld16(base + 2 * kAccStride, v[2]);
+                    tmem_ld_wait();
 #pragma unroll
-                    for (int j = 0; j < kNumAcc; ++j) {
-                        uint32_t v[16];
-                        tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + j * kAccStride + 16 * ci, v);
-                        tmem_ld_wait();
+                    for (int k = 0; k < 16; ++k)
+                        run[i][k] += acc_fixed<6>(0, v[0][k]) + acc_fixed<6>(1, v[1][k]) + acc_fixed<6>(2, v[2][k]);
+                    tmem_ld16(base + 3 * kAccStride, v[0]);
+                    tmem_ld16(base + 4 * kAccStride, v[1]);
+                    tmem_ld_wait();
 #pragma unroll
-                        for (int k = 0; k < 16; ++k) run[i][k] += acc_fixed<6>(j, v[k]);
-                    }
+                    for (int k = 0; k < 16; ++k) run[i][k] += acc_fixed<6>(3, v[0][k]) + acc_fixed<6>(4, v[1][k]);
                 }
             }
             tc_fence_before();
