@@ -56,7 +56,7 @@ constexpr int kTmemCols = 512;     // 5 accumulators x 96 columns, rounded up to
 constexpr int kAccStride = kEmuTileN;  // TMEM columns between accumulators
 constexpr int kSmemBudget = 200 * 1024;
 
-__host__ __device__ constexpr int bk_for(int S) { return S <= 4 ? 32 : 16; }
+__host__ __device__ constexpr int bk_for(int S) { return S <= 6 ? 32 : 16; }
 // One stage: S planes of a 128-row tile (A) and S planes of a <= 96-row tile (B), BK columns.
 __host__ __device__ constexpr int stage_bytes(int S) { return S * (kEmuTile + kEmuTileN) * bk_for(S) * 2; }
 __host__ __device__ constexpr int stages_for(int S) {
