@@ -148,24 +148,31 @@ double model_time(const ladder_plan_s& p, const std::vector<BlockPair>& bps) {
 
 // Build device tables for the chosen blocking: per block pair its pair list
 // (int2 (a, b), a-major) and row_start (first packed row of each a).
-// ERI tiles (rt, qt) of one block pair that hold at least one a <= b, in an
-// L2-friendly order: a band of row tiles whose operand slices take ~40 MB of L2
-// stays resident while every column tile of the band streams past it.
-std::vector<int> eri_tiles(const BlockPair& bp, int nv, int tile, int tile_n, size_t row_bytes) {
+// ERI work entries of one block pair, (rt, qt0, qt1, 0): one 128-row tile rt of
+// (a,c) and two adjacent 96-column tiles of (b,d), each -1 when it holds no a <= b.
+// A two-CTA cluster takes one entry (both CTAs share the A tile).  Order: a band of
+// row tiles whose operand slices take ~40 MB of L2 stays resident while every
+// column pair of the band streams past it.
+std::vector<int> eri_entries(const BlockPair& bp, int nv, int tile, int tile_n, size_t row_bytes) {
     std::vector<int> out;
     const long long M = (long long)(bp.a1 - bp.a0) * nv, N = (long long)(bp.b1 - bp.b0) * nv;
     const int nrt = (int)((M + tile - 1) / tile), nqt = (int)((N + tile_n - 1) / tile_n);
     const int band = (int)std::max<size_t>(8, std::min<size_t>(64, (40u << 20) / std::max<size_t>(1, row_bytes * tile)));
+    auto valid = [&](int rt, int qt) {
+        if (qt >= nqt) return false;
+        const int a_min = bp.a0 + (int)((long long)rt * tile / nv);
+        const long long last = std::min((long long)(qt + 1) * tile_n, N) - 1;
+        return a_min <= bp.b0 + (int)(last / nv);
+    };
     for (int r0 = 0; r0 < nrt; r0 += band)
-        for (int qt = 0; qt < nqt; ++qt)
+        for (int qt = 0; qt < nqt; qt += 2)
             for (int rt = r0; rt < std::min(nrt, r0 + band); ++rt) {
-                const int a_min = bp.a0 + (int)((long long)rt * tile / nv);
-                const long long last = std::min((long long)(qt + 1) * tile_n, N) - 1;
-                const int b_max = bp.b0 + (int)(last / nv);
-                if (a_min <= b_max) {
-                    out.push_back(rt);
-                    out.push_back(qt);
-                }
+                const bool v0 = valid(rt, qt), v1 = valid(rt, qt + 1);
+                if (!v0 && !v1) continue;
+                out.push_back(rt);
+                out.push_back(v0 ? qt : -1);
+                out.push_back(v1 ? qt + 1 : -1);
+                out.push_back(0);
             }
     return out;
 }
@@ -176,10 +183,11 @@ int build_tables(ladder_plan_s& p) {
     for (auto& bp : p.bps) n_int2 += bp.npairs;
     if (p.precision != LADDER_FP64)
         for (auto& bp : p.bps) {
-            tiles.push_back(eri_tiles(bp, p.nv, ladder::kEmuTile, ladder::kEmuTileN,
-                                      (size_t)p.nslices * 2 * ladder::align_up((size_t)p.nchol, 8)));
+            tiles.push_back(eri_entries(bp, p.nv, ladder::kEmuTile, ladder::kEmuTileN,
+                                        (size_t)p.nslices * 2 * ladder::align_up((size_t)p.nchol, 8)));
             n_int2 += tiles.back().size() / 2;
         }
+    n_int2 += 1;  // room to align the int4 ERI entries to 16 bytes
     for (auto& bp : p.bps) n_int += (size_t)(bp.a1 - bp.a0 + 1);
     std::vector<int> host(2 * n_int2 + n_int);
     size_t o2 = 0, oi = 2 * n_int2;
@@ -198,9 +206,10 @@ int build_tables(ladder_plan_s& p) {
         }
         host[oi++] = row;
     }
+    o2 += o2 & 1;  // int4 entries start on a 16-byte boundary
     for (size_t k = 0; k < tiles.size(); ++k) {
-        p.bps[k].tiles_off = o2;
-        p.bps[k].ntiles = (int)(tiles[k].size() / 2);
+        p.bps[k].tiles_off = o2;                       // in int2 units; entries are int4 = 2 int2
+        p.bps[k].ntiles = (int)(tiles[k].size() / 4);  // number of entries
         for (size_t t = 0; t < tiles[k].size(); ++t) host[2 * o2 + t] = tiles[k][t];
         o2 += tiles[k].size() / 2;
     }

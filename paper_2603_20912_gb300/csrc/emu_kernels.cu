@@ -273,9 +273,9 @@ __device__ __forceinline__ long long acc_fixed(int j, uint32_t bits) {
 }
 
 struct EriArgs {
-    int nv, nchol, a0, na, b0, nb, kpad, ntiles;
+    int nv, nchol, a0, na, b0, nb, kpad, nentries;
     size_t plane_stride;  // elements between V planes
-    const int2* tiles;
+    const int4* entries;  // (rt, qt for CTA rank 0 or -1, qt for CTA rank 1 or -1, 0)
     const int* row_start;
     const int* lt_exp;
     const int* f_tab;
@@ -284,32 +284,40 @@ struct EriArgs {
 };
 
 // ------------------------------------------------------------------ ERI kernel
-// One 128 (a,c) x 96 (b,d) tile per work item; K = nchol in chunks of kEmuChunkK.
+// A cluster of two CTAs takes one entry = one 128-row (a,c) tile and two 96-column
+// (b,d) tiles.  Each CTA loads half of the shared A tile and multicasts it to both
+// (halving the A operand traffic); each CTA's MMA commit frees the stage in both
+// CTAs, so a stage is refilled only after both have consumed it.  K = nchol runs in
+// exact chunks of kEmuChunkK.
 template <int S>
-__global__ void __launch_bounds__(kThreadsTC, 1) eri_emu_kernel(const __grid_constant__ CUtensorMap tm_a,
-                                                                const __grid_constant__ CUtensorMap tm_b, EriArgs p) {
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
+    eri_emu_kernel(const __grid_constant__ CUtensorMap tm_ahalf, const __grid_constant__ CUtensorMap tm_b,
+                   EriArgs p) {
     constexpr int BK = bk_for(S), STAGES = stages_for(S);
     constexpr uint32_t APLANE = kEmuTile * BK * 2, BPLANE = kEmuTileN * BK * 2;
+    constexpr uint32_t ABYTES = S * APLANE, BBYTES = S * BPLANE;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     __shared__ uint64_t full[STAGES], empty[STAGES], acc_full, acc_empty, done;
     __shared__ uint32_t tmem_base;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rank = (int)cluster_ctarank();
+    const int cluster = blockIdx.x >> 1, nclusters = gridDim.x >> 1;
     if (threadIdx.x == 0) {
         for (int i = 0; i < STAGES; ++i) {
             mbar_init(&full[i], 1);
-            mbar_init(&empty[i], 1);
+            mbar_init(&empty[i], 2);  // one commit from each CTA's MMA thread
         }
         mbar_init(&acc_full, 1);
         mbar_init(&acc_empty, kEpiWarps);
         mbar_init(&done, 1);
         fence_barrier_init();
-        tma_prefetch_desc(&tm_a);
+        tma_prefetch_desc(&tm_ahalf);
         tma_prefetch_desc(&tm_b);
     }
     if (warp == 1) tmem_alloc(&tmem_base, kTmemCols);
     tc_fence_before();
-    __syncthreads();
+    cluster_sync();  // the peer may multicast into this CTA only after its barriers exist
     tc_fence_after();
     const uint32_t tmem = tmem_base;
     const int nkb = (p.nchol + BK - 1) / BK;
@@ -321,16 +329,20 @@ __global__ void __launch_bounds__(kThreadsTC, 1) eri_emu_kernel(const __grid_con
         Ring ring;
         int issued[STAGES] = {};
         bool ok = true;
-        for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
-            const int2 tq = p.tiles[t];
-            const int arow = p.a0 * p.nv + tq.x * kEmuTile;
-            const int brow = p.b0 * p.nv + tq.y * kEmuTileN;
+        for (int e = cluster; e < p.nentries && ok; e += nclusters) {
+            const int4 en = p.entries[e];
+            const int qt = rank == 0 ? en.y : en.z;
+            const int arow = p.a0 * p.nv + en.x * kEmuTile + 64 * rank;
+            const int brow = p.b0 * p.nv + qt * kEmuTileN;
             for (int kb = 0; kb < nkb && ok; ++kb) {
                 if (!(ok = mbar_wait(&empty[ring.stage], ring.phase ^ 1u, p.status, kStatusTimeout))) break;
                 unsigned char* st = smem + ring.stage * stage_bytes(S);
-                mbar_arrive_expect_tx(&full[ring.stage], stage_bytes(S));
-                tma_load_3d(st, &tm_a, &full[ring.stage], kb * BK, arow, 0);
-                tma_load_3d(st + S * APLANE, &tm_b, &full[ring.stage], kb * BK, brow, 0);
+                mbar_arrive_expect_tx(&full[ring.stage], ABYTES + (qt >= 0 ? BBYTES : 0u));
+#pragma unroll
+                for (int s = 0; s < S; ++s)
+                    tma_load_3d_mc(st + s * APLANE + rank * (APLANE / 2), &tm_ahalf, &full[ring.stage], kb * BK, arow,
+                                   s, (uint16_t)0x3);
+                if (qt >= 0) tma_load_3d(st + ABYTES, &tm_b, &full[ring.stage], kb * BK, brow, 0);
                 ++issued[ring.stage];
                 ring.next(STAGES);
             }
@@ -344,21 +356,30 @@ __global__ void __launch_bounds__(kThreadsTC, 1) eri_emu_kernel(const __grid_con
         const uint32_t idesc = idesc_bf16_f32(kEmuTile, kEmuTileN);
         bool ok = true;
         int it = 0;
-        for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
-            for (int ch = 0; ch < nch && ok; ++ch, ++it) {
-                if (!(ok = mbar_wait(&acc_empty, (uint32_t)(it & 1) ^ 1u, p.status, kStatusTimeout))) break;
-                tc_fence_after();
+        for (int e = cluster; e < p.nentries && ok; e += nclusters) {
+            const int4 en = p.entries[e];
+            const bool mine = (rank == 0 ? en.y : en.z) >= 0;
+            for (int ch = 0; ch < nch && ok; ++ch) {
+                if (mine) {
+                    if (!(ok = mbar_wait(&acc_empty, (uint32_t)(it & 1) ^ 1u, p.status, kStatusTimeout))) break;
+                    tc_fence_after();
+                }
                 bool first[kNumAcc] = {true, true, true, true, true};
                 const int kb1 = min((ch + 1) * kb_per_chunk, nkb);
                 for (int kb = ch * kb_per_chunk; kb < kb1 && ok; ++kb) {
                     if (!(ok = mbar_wait(&full[ring.stage], ring.phase, p.status, kStatusTimeout))) break;
                     tc_fence_after();
-                    const uint32_t st = smem_u32(smem + ring.stage * stage_bytes(S));
-                    issue_pairs<S>(tmem, st, st + S * APLANE, APLANE, BPLANE, idesc, first);
-                    mma_commit(&empty[ring.stage]);
+                    if (mine) {
+                        const uint32_t st = smem_u32(smem + ring.stage * stage_bytes(S));
+                        issue_pairs<S>(tmem, st, st + ABYTES, APLANE, BPLANE, idesc, first);
+                    }
+                    mma_commit_mc(&empty[ring.stage], (uint16_t)0x3);
                     ring.next(STAGES);
                 }
-                if (ok) mma_commit(&acc_full);
+                if (ok && mine) {
+                    mma_commit(&acc_full);
+                    ++it;
+                }
             }
         }
         mma_commit(&done);
@@ -371,7 +392,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1) eri_emu_kernel(const __grid_con
         long long run[3][16];
         int it = 0;
         bool ok = true;
-        for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
+        for (int e = cluster; e < p.nentries && ok; e += nclusters) {
+            const int4 en = p.entries[e];
+            const int qt = rank == 0 ? en.y : en.z;
+            if (qt < 0) continue;
 #pragma unroll
             for (int cc = 0; cc < 3; ++cc)
 #pragma unroll
@@ -401,8 +425,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) eri_emu_kernel(const __grid_con
                 if (lane == 0) mbar_arrive(&acc_empty);
             }
             if (!ok) break;
-            const int2 tq = p.tiles[t];
-            const int r_local = tq.x * kEmuTile + 32 * q + lane;
+            const int r_local = en.x * kEmuTile + 32 * q + lane;
             if (r_local >= Mrows) continue;
             const int a = p.a0 + r_local / p.nv, c = r_local % p.nv;
             const int e_ac = p.lt_exp[(p.a0 * p.nv + r_local) / kG];
@@ -410,7 +433,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) eri_emu_kernel(const __grid_con
             const bool vec = (p.nv & 7) == 0;  // 8 consecutive d of one (a,b) row are 16-byte aligned
 #pragma unroll
             for (int cc = 0; cc < 3; ++cc) {
-                const int col0 = tq.y * kEmuTileN + 48 * h + 16 * cc;
+                const int col0 = qt * kEmuTileN + 48 * h + 16 * cc;
                 if (vec) {
                     // Two runs of 8 columns; each lies in one b (nv % 8 == 0) and starts at d % 8 == 0.
 #pragma unroll
@@ -459,7 +482,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) eri_emu_kernel(const __grid_con
         }
     }
     tc_fence_before();
-    __syncthreads();
+    cluster_sync();  // no CTA leaves while its peer may still multicast into it or commit to it
     if (warp == 1) {
         tc_fence_after();
         tmem_dealloc(tmem, kTmemCols);
@@ -652,12 +675,12 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 // 3-D BF16 map over planes[z][y][x]: x = K (extent `inner`, row stride `row_bytes`),
 // y = rows, z = planes (stride `plane_bytes`).  Box {bk, box_rows, planes}; OOB reads give 0.
 bool make_tmap(CUtensorMap* m, const void* base, uint64_t inner, uint64_t rows, uint64_t planes, uint64_t row_bytes,
-               uint64_t plane_bytes, uint32_t bk, uint32_t box_rows) {
+               uint64_t plane_bytes, uint32_t bk, uint32_t box_rows, uint32_t box_planes = 0) {
     auto enc = encode_fn();
     if (!enc) return false;
     cuuint64_t dims[3] = {inner, rows, planes};
     cuuint64_t strides[2] = {row_bytes, plane_bytes};
-    cuuint32_t box[3] = {bk, box_rows, (cuuint32_t)planes};
+    cuuint32_t box[3] = {bk, box_rows, box_planes ? box_planes : (cuuint32_t)planes};
     cuuint32_t es[3] = {1, 1, 1};
     const CUtensorMapSwizzle sw = bk * 2 == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
                                   : bk * 2 == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
@@ -726,16 +749,17 @@ cudaError_t block_impl(const ladder_plan_s& p, const BlockPair& bp, double* R, v
     const int* row_start = reinterpret_cast<const int*>(p.d_tables) + bp.rows_off;
     CUtensorMap tm_la, tm_lb, tm_v, tm_t;
     if (!make_tmap(&tm_la, at<char>(ws, p.ws.lt_slices), p.nchol, nv2, S, (uint64_t)xpad * 2, (uint64_t)nv2 * xpad * 2,
-                   BK, kEmuTile) ||
+                   BK, kEmuTile / 2, 1) ||
         !make_tmap(&tm_lb, at<char>(ws, p.ws.lt_slices), p.nchol, nv2, S, (uint64_t)xpad * 2, (uint64_t)nv2 * xpad * 2,
                    BK, kEmuTileN))
         return cudaErrorInvalidValue;
     EriArgs ea{p.nv, p.nchol, bp.a0, bp.a1 - bp.a0, bp.b0, bp.b1 - bp.b0, kpad, bp.ntiles, vplane,
-               table + bp.tiles_off, row_start, at<int>(ws, p.ws.lt_exp), at<int>(ws, p.ws.v_exp),
-               at<__nv_bfloat16>(ws, p.ws.v_blk), p.d_status};
+               reinterpret_cast<const int4*>(table + bp.tiles_off), row_start, at<int>(ws, p.ws.lt_exp),
+               at<int>(ws, p.ws.v_exp), at<__nv_bfloat16>(ws, p.ws.v_blk), p.d_status};
     {
         LaunchTimer tm(p, s, LADDER_KERNEL_ERI);
-        eri_emu_kernel<S><<<std::max(1, std::min(bp.ntiles, p.num_sms)), kThreadsTC, smem, s>>>(tm_la, tm_lb, ea);
+        const int clusters = std::max(1, std::min(bp.ntiles, p.num_sms / 2));
+        eri_emu_kernel<S><<<2 * clusters, kThreadsTC, smem, s>>>(tm_la, tm_lb, ea);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
 

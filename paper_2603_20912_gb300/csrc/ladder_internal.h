@@ -33,8 +33,8 @@ struct BlockPair {
     int npairs;        // number of (a, b) with a <= b in the block pair
     size_t pairs_off;  // offset (in int2) of this block pair's pair list in the device table
     size_t rows_off;   // offset (in int) of this block pair's row_start table (a1 - a0 + 1 ints)
-    size_t tiles_off = 0;  // emulated path: offset (in int2) of the ERI tile list (rt, qt)
-    int ntiles = 0;        // emulated path: number of 128x128 ERI tiles holding some a <= b
+    size_t tiles_off = 0;  // emulated path: offset (in int2) of the ERI entries (int4: rt, qt0, qt1, 0)
+    int ntiles = 0;        // emulated path: number of ERI entries (one 2-CTA cluster each)
 };
 
 // Workspace layout of one plan (byte offsets from the workspace base).
