@@ -59,8 +59,8 @@ Geometry geometry_for(const ladder_plan_s& p) {
         const double sm_rate = 1.5e15 / std::max(1, p.num_sms);
         const int nnt = (p.no * p.no + ladder::kEmuTileN - 1) / ladder::kEmuTileN;
         const int ltn = ((p.no * p.no + nnt - 1) / nnt + 15) / 16 * 16;
-        g = {128, ladder::kEmuTileN, 1, 128, ltn, 1, 0, 0, 25e-6};
-        g.eri_tile_s = 2.0 * 128 * ladder::kEmuTileN * X * pairs / sm_rate + 3e-6;
+        g = {256, ladder::kEmuTileN, 1, 128, ltn, 1, 0, 0, 25e-6};
+        g.eri_tile_s = 2.0 * 128 * ladder::kEmuTileN * X * pairs / sm_rate + 3e-6;  // per SM of the pair
         g.lad_tile_s = 2.0 * 128 * ltn * v2 * pairs / sm_rate + 3e-6;
     }
     return g;
@@ -139,7 +139,7 @@ double model_time(const ladder_plan_s& p, const std::vector<BlockPair>& bps) {
     for (auto& bp : bps) {
         const long long te = count_eri_tiles(bp, p.nv, g.eri_tm, g.eri_tn);
         const long long tl = ((long long)(bp.npairs + g.lad_tm - 1) / g.lad_tm) * nt;
-        t += std::ceil(te / slots_e) * g.eri_occ * g.eri_tile_s;
+        t += std::ceil(te / (p.precision == LADDER_FP64 ? slots_e : slots_e / 2)) * g.eri_occ * g.eri_tile_s;
         t += std::ceil(tl / slots_l) * g.lad_occ * g.lad_tile_s;
         t += g.overhead_s;
     }
@@ -148,30 +148,24 @@ double model_time(const ladder_plan_s& p, const std::vector<BlockPair>& bps) {
 
 // Build device tables for the chosen blocking: per block pair its pair list
 // (int2 (a, b), a-major) and row_start (first packed row of each a).
-// ERI work entries of one block pair, (rt, qt0, qt1, 0): one 128-row tile rt of
-// (a,c) and two adjacent 96-column tiles of (b,d), each -1 when it holds no a <= b.
-// A two-CTA cluster takes one entry (both CTAs share the A tile).  Order: a band of
-// row tiles whose operand slices take ~40 MB of L2 stays resident while every
-// column pair of the band streams past it.
+// ERI work entries of one block pair, (rt, qt, 0, 0): a 256-row tile rt of (a,c)
+// (computed by a CTA pair, 128 rows each) and a 96-column tile qt of (b,d), kept
+// when it holds some a <= b.  Order: a band of row tiles whose operand slices take
+// ~40 MB of L2 stays resident while every column tile of the band streams past it.
 std::vector<int> eri_entries(const BlockPair& bp, int nv, int tile, int tile_n, size_t row_bytes) {
     std::vector<int> out;
     const long long M = (long long)(bp.a1 - bp.a0) * nv, N = (long long)(bp.b1 - bp.b0) * nv;
     const int nrt = (int)((M + tile - 1) / tile), nqt = (int)((N + tile_n - 1) / tile_n);
-    const int band = (int)std::max<size_t>(8, std::min<size_t>(64, (40u << 20) / std::max<size_t>(1, row_bytes * tile)));
-    auto valid = [&](int rt, int qt) {
-        if (qt >= nqt) return false;
-        const int a_min = bp.a0 + (int)((long long)rt * tile / nv);
-        const long long last = std::min((long long)(qt + 1) * tile_n, N) - 1;
-        return a_min <= bp.b0 + (int)(last / nv);
-    };
+    const int band = (int)std::max<size_t>(4, std::min<size_t>(32, (40u << 20) / std::max<size_t>(1, row_bytes * tile)));
     for (int r0 = 0; r0 < nrt; r0 += band)
-        for (int qt = 0; qt < nqt; qt += 2)
+        for (int qt = 0; qt < nqt; ++qt)
             for (int rt = r0; rt < std::min(nrt, r0 + band); ++rt) {
-                const bool v0 = valid(rt, qt), v1 = valid(rt, qt + 1);
-                if (!v0 && !v1) continue;
+                const int a_min = bp.a0 + (int)((long long)rt * tile / nv);
+                const long long last = std::min((long long)(qt + 1) * tile_n, N) - 1;
+                if (a_min > bp.b0 + (int)(last / nv)) continue;
                 out.push_back(rt);
-                out.push_back(v0 ? qt : -1);
-                out.push_back(v1 ? qt + 1 : -1);
+                out.push_back(qt);
+                out.push_back(0);
                 out.push_back(0);
             }
     return out;
@@ -183,7 +177,7 @@ int build_tables(ladder_plan_s& p) {
     for (auto& bp : p.bps) n_int2 += bp.npairs;
     if (p.precision != LADDER_FP64)
         for (auto& bp : p.bps) {
-            tiles.push_back(eri_entries(bp, p.nv, ladder::kEmuTile, ladder::kEmuTileN,
+            tiles.push_back(eri_entries(bp, p.nv, 2 * ladder::kEmuTile, ladder::kEmuTileN,
                                         (size_t)p.nslices * 2 * ladder::align_up((size_t)p.nchol, 8)));
             n_int2 += tiles.back().size() / 2;
         }

@@ -54,11 +54,17 @@ constexpr int kThreadsTC = 32 * (2 + kEpiWarps);
 constexpr int kNumAcc = 5;         // exact levels 2, 3, 4, 5 and the shared levels >= 6
 constexpr int kTmemCols = 512;     // 5 accumulators x 96 columns, rounded up to a power of two
 constexpr int kAccStride = kEmuTileN;  // TMEM columns between accumulators
-constexpr int kSmemBudget = 200 * 1024;
+constexpr int kSmemBudget = 210 * 1024;
 
 __host__ __device__ constexpr int bk_for(int S) { return S <= 6 ? 32 : 16; }
 // One stage: S planes of a 128-row tile (A) and S planes of a <= 96-row tile (B), BK columns.
 __host__ __device__ constexpr int stage_bytes(int S) { return S * (kEmuTile + kEmuTileN) * bk_for(S) * 2; }
+// ERI stage on a CTA pair: 128 rows of A and half (48 rows) of the 96-row B tile per CTA.
+__host__ __device__ constexpr int eri_stage_bytes(int S) { return S * (kEmuTile + kEmuTileN / 2) * bk_for(S) * 2; }
+__host__ __device__ constexpr int eri_stages_for(int S) {
+    return kSmemBudget / eri_stage_bytes(S) < 4 ? kSmemBudget / eri_stage_bytes(S) : 4;
+}
+__host__ __device__ constexpr int eri_smem_bytes_for(int S) { return eri_stages_for(S) * eri_stage_bytes(S) + 1024; }
 __host__ __device__ constexpr int stages_for(int S) {
     return kSmemBudget / stage_bytes(S) < 4 ? kSmemBudget / stage_bytes(S) : 4;
 }
@@ -239,7 +245,7 @@ struct Ring {
 };
 
 // Issue the S(S+1)/2 slice-pair MMAs of one stage (BK / 16 K-steps) into the 4 accumulators.
-template <int S>
+template <int S, bool PAIR = false>
 __device__ __forceinline__ void issue_pairs(uint32_t tmem, uint32_t sA, uint32_t sB, uint32_t a_plane_bytes,
                                             uint32_t b_plane_bytes, uint32_t idesc, bool (&first)[kNumAcc]) {
     constexpr int BK = bk_for(S);
@@ -252,7 +258,10 @@ __device__ __forceinline__ void issue_pairs(uint32_t tmem, uint32_t sA, uint32_t
                 const int j = (s + t + 2 < 6 ? s + t + 2 : 6) - 2;
                 const uint64_t ad = smem_desc_kmajor(sA + s * a_plane_bytes + kk * 32, BK * 2);
                 const uint64_t bd = smem_desc_kmajor(sB + t * b_plane_bytes + kk * 32, BK * 2);
-                mma_bf16(tmem + j * kAccStride, ad, bd, idesc, first[j] ? 0u : 1u);
+                if (PAIR)
+                    mma_bf16_pair(tmem + j * kAccStride, ad, bd, idesc, first[j] ? 0u : 1u);
+                else
+                    mma_bf16(tmem + j * kAccStride, ad, bd, idesc, first[j] ? 0u : 1u);
                 first[j] = false;
             }
         }
@@ -284,118 +293,103 @@ struct EriArgs {
 };
 
 // ------------------------------------------------------------------ ERI kernel
-// A cluster of two CTAs takes one entry = one 128-row (a,c) tile and two 96-column
-// (b,d) tiles.  Each CTA loads half of the shared A tile and multicasts it to both
-// (halving the A operand traffic); each CTA's MMA commit frees the stage in both
-// CTAs, so a stage is refilled only after both have consumed it.  K = nchol runs in
-// exact chunks of kEmuChunkK.
+// A CTA pair computes one 256-row (a,c) x 96-column (b,d) tile with 2-SM MMAs
+// (cta_group::2, M = 256): CTA r holds A rows [128r, 128r+128) and B rows
+// [48r, 48r+48) of every stage and the accumulators of its 128 rows.  Both CTAs'
+// TMA loads complete on the leader's (rank 0) full barrier; the leader issues the
+// MMAs and its commits release the stage and publish the accumulators in both CTAs;
+// the epilogue warps of both CTAs release the accumulators to the leader.
+// K = nchol runs in exact chunks of kEmuChunkK.
 template <int S>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
-    eri_emu_kernel(const __grid_constant__ CUtensorMap tm_ahalf, const __grid_constant__ CUtensorMap tm_b,
-                   EriArgs p) {
-    constexpr int BK = bk_for(S), STAGES = stages_for(S);
-    constexpr uint32_t APLANE = kEmuTile * BK * 2, BPLANE = kEmuTileN * BK * 2;
-    constexpr uint32_t ABYTES = S * APLANE, BBYTES = S * BPLANE;
+    eri_emu_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ CUtensorMap tm_b, EriArgs p) {
+    constexpr int BK = bk_for(S), STAGES = eri_stages_for(S);
+    constexpr uint32_t APLANE = kEmuTile * BK * 2, BPLANE = (kEmuTileN / 2) * BK * 2;
+    constexpr uint32_t ABYTES = S * APLANE;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     __shared__ uint64_t full[STAGES], empty[STAGES], acc_full, acc_empty, done;
     __shared__ uint32_t tmem_base;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int rank = (int)cluster_ctarank();
+    const uint32_t rank = cluster_ctarank();
     const int cluster = blockIdx.x >> 1, nclusters = gridDim.x >> 1;
     if (threadIdx.x == 0) {
         for (int i = 0; i < STAGES; ++i) {
-            mbar_init(&full[i], 1);
-            mbar_init(&empty[i], 2);  // one commit from each CTA's MMA thread
+            mbar_init(&full[i], 1);   // leader: its producer's arrive + both CTAs' bytes
+            mbar_init(&empty[i], 1);  // the leader's multicast commit
         }
         mbar_init(&acc_full, 1);
-        mbar_init(&acc_empty, kEpiWarps);
+        mbar_init(&acc_empty, 2 * kEpiWarps);
         mbar_init(&done, 1);
         fence_barrier_init();
-        tma_prefetch_desc(&tm_ahalf);
+        tma_prefetch_desc(&tm_a);
         tma_prefetch_desc(&tm_b);
     }
-    if (warp == 1) tmem_alloc(&tmem_base, kTmemCols);
+    if (warp == 1) tmem_alloc_pair(&tmem_base, kTmemCols);
     tc_fence_before();
-    cluster_sync();  // the peer may multicast into this CTA only after its barriers exist
+    cluster_sync();
     tc_fence_after();
     const uint32_t tmem = tmem_base;
     const int nkb = (p.nchol + BK - 1) / BK;
     const int kb_per_chunk = kEmuChunkK / BK;
     const int nch = (nkb + kb_per_chunk - 1) / kb_per_chunk;
+    bool failed = false;
 
     if (warp == 0 && lane == 0) {
-        // ---------------- TMA producer
+        // ---------------- TMA producer (both CTAs)
         Ring ring;
-        int issued[STAGES] = {};
         bool ok = true;
         for (int e = cluster; e < p.nentries && ok; e += nclusters) {
             const int4 en = p.entries[e];
-            const int qt = rank == 0 ? en.y : en.z;
-            const int arow = p.a0 * p.nv + en.x * kEmuTile + 64 * rank;
-            const int brow = p.b0 * p.nv + qt * kEmuTileN;
+            const int arow = p.a0 * p.nv + en.x * (2 * kEmuTile) + kEmuTile * (int)rank;
+            const int brow = p.b0 * p.nv + en.y * kEmuTileN + (kEmuTileN / 2) * (int)rank;
             for (int kb = 0; kb < nkb && ok; ++kb) {
                 if (!(ok = mbar_wait(&empty[ring.stage], ring.phase ^ 1u, p.status, kStatusTimeout))) break;
-                unsigned char* st = smem + ring.stage * stage_bytes(S);
-                mbar_arrive_expect_tx(&full[ring.stage], ABYTES + (qt >= 0 ? BBYTES : 0u));
-#pragma unroll
-                for (int s = 0; s < S; ++s)
-                    tma_load_3d_mc(st + s * APLANE + rank * (APLANE / 2), &tm_ahalf, &full[ring.stage], kb * BK, arow,
-                                   s, (uint16_t)0x3);
-                if (qt >= 0) tma_load_3d(st + ABYTES, &tm_b, &full[ring.stage], kb * BK, brow, 0);
-                ++issued[ring.stage];
+                unsigned char* st = smem + ring.stage * eri_stage_bytes(S);
+                if (rank == 0) mbar_arrive_expect_tx(&full[ring.stage], 2 * eri_stage_bytes(S));
+                const uint32_t fb = mapa_rank(smem_u32(&full[ring.stage]), 0);
+                tma_load_3d_2sm(st, &tm_a, fb, kb * BK, arow, 0);
+                tma_load_3d_2sm(st + ABYTES, &tm_b, fb, kb * BK, brow, 0);
                 ring.next(STAGES);
             }
         }
-        // Wait (bounded) for every copy still in flight before the CTA can exit.
-        for (int i = 0; i < STAGES; ++i)
-            if (issued[i]) mbar_wait(&full[i], (uint32_t)((issued[i] - 1) & 1), p.status, kStatusTimeout);
-    } else if (warp == 1 && lane == 0) {
-        // ---------------- MMA issuer
+        failed = !ok;
+    } else if (warp == 1 && lane == 0 && rank == 0) {
+        // ---------------- MMA issuer (leader CTA only)
         Ring ring;
-        const uint32_t idesc = idesc_bf16_f32(kEmuTile, kEmuTileN);
+        const uint32_t idesc = idesc_bf16_f32(2 * kEmuTile, kEmuTileN);
         bool ok = true;
         int it = 0;
         for (int e = cluster; e < p.nentries && ok; e += nclusters) {
-            const int4 en = p.entries[e];
-            const bool mine = (rank == 0 ? en.y : en.z) >= 0;
-            for (int ch = 0; ch < nch && ok; ++ch) {
-                if (mine) {
-                    if (!(ok = mbar_wait(&acc_empty, (uint32_t)(it & 1) ^ 1u, p.status, kStatusTimeout))) break;
-                    tc_fence_after();
-                }
+            for (int ch = 0; ch < nch && ok; ++ch, ++it) {
+                if (!(ok = mbar_wait(&acc_empty, (uint32_t)(it & 1) ^ 1u, p.status, kStatusTimeout))) break;
+                tc_fence_after();
                 bool first[kNumAcc] = {true, true, true, true, true};
                 const int kb1 = min((ch + 1) * kb_per_chunk, nkb);
                 for (int kb = ch * kb_per_chunk; kb < kb1 && ok; ++kb) {
                     if (!(ok = mbar_wait(&full[ring.stage], ring.phase, p.status, kStatusTimeout))) break;
                     tc_fence_after();
-                    if (mine) {
-                        const uint32_t st = smem_u32(smem + ring.stage * stage_bytes(S));
-                        issue_pairs<S>(tmem, st, st + ABYTES, APLANE, BPLANE, idesc, first);
-                    }
-                    mma_commit_mc(&empty[ring.stage], (uint16_t)0x3);
+                    const uint32_t st = smem_u32(smem + ring.stage * eri_stage_bytes(S));
+                    issue_pairs<S, true>(tmem, st, st + ABYTES, APLANE, BPLANE, idesc, first);
+                    mma_commit_pair_mc(&empty[ring.stage], (uint16_t)0x3);
                     ring.next(STAGES);
                 }
-                if (ok && mine) {
-                    mma_commit(&acc_full);
-                    ++it;
-                }
+                if (ok) mma_commit_pair_mc(&acc_full, (uint16_t)0x3);
             }
         }
-        mma_commit(&done);
-        mbar_wait(&done, 0, p.status, kStatusTimeout);
+        mma_commit_pair_mc(&done, (uint16_t)0x3);
+        failed = !ok;
     } else if (warp >= 2) {
         // ---------------- epilogue: exact int64 recombination, then re-slicing into the V planes.
-        // Warp: TMEM lane quadrant q (tile rows 32q..32q+31), columns 48h..48h+47 (3 chunks of 16).
+        // Warp: TMEM lane quadrant q (this CTA's tile rows 32q..32q+31), columns 48h..48h+47.
         const int q = warp & 3, h = (warp - 2) >> 2;
         const int Mrows = p.na * p.nv, Ncols = p.nb * p.nv;
+        const uint32_t acc_empty_leader = mapa_rank(smem_u32(&acc_empty), 0);
         long long run[3][16];
         int it = 0;
         bool ok = true;
         for (int e = cluster; e < p.nentries && ok; e += nclusters) {
             const int4 en = p.entries[e];
-            const int qt = rank == 0 ? en.y : en.z;
-            if (qt < 0) continue;
 #pragma unroll
             for (int cc = 0; cc < 3; ++cc)
 #pragma unroll
@@ -422,10 +416,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
                 }
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&acc_empty);
+                if (lane == 0) mbar_arrive_remote(acc_empty_leader);
             }
             if (!ok) break;
-            const int r_local = en.x * kEmuTile + 32 * q + lane;
+            const int qt = en.y;
+            const int r_local = en.x * (2 * kEmuTile) + kEmuTile * (int)rank + 32 * q + lane;
             if (r_local >= Mrows) continue;
             const int a = p.a0 + r_local / p.nv, c = r_local % p.nv;
             const int e_ac = p.lt_exp[(p.a0 * p.nv + r_local) / kG];
@@ -480,18 +475,24 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
                 }
             }
         }
+        failed = !ok;
     }
+    // Every CTA waits for the leader's last commit (all MMAs that read its shared memory are done).
+    if (threadIdx.x == 64) mbar_wait(&done, 0, p.status, kStatusTimeout);
+    if (failed) grace_delay(2000000);  // an aborted pipeline: let copies already in flight land
     tc_fence_before();
-    cluster_sync();  // no CTA leaves while its peer may still multicast into it or commit to it
+    cluster_sync();  // no CTA leaves while its peer may still write into it or signal it
     if (warp == 1) {
         tc_fence_after();
-        tmem_dealloc(tmem, kTmemCols);
+        tmem_dealloc_pair(tmem, kTmemCols);
     }
 }
 
 // ------------------------------------------------------------------ ladder kernel
 struct LadArgs {
-    int npairs, no2, BN, n_mt, n_nt, n_ch, kb_per_chunk, nkb;
+    int M, N, BN, n_mt, n_nt, n_ch, kb_per_chunk, nkb;
+    int swap;                // 0: rows m = pairs, columns n = (i,j); 1: rows m = (i,j), columns n = pairs
+    int no2;
     long long units;
     unsigned long long* rp;  // int64 fixed-point accumulator [npairs][no2]
     unsigned* status;
@@ -501,8 +502,8 @@ struct LadArgs {
 // contiguous range of units (stream-K) and flushes its int64 sums with atomics
 // whenever its (row tile, column tile) changes.
 template <int S>
-__global__ void __launch_bounds__(kThreadsTC, 1) ladder_emu_kernel(const __grid_constant__ CUtensorMap tm_v,
-                                                                   const __grid_constant__ CUtensorMap tm_t,
+__global__ void __launch_bounds__(kThreadsTC, 1) ladder_emu_kernel(const __grid_constant__ CUtensorMap tm_a,
+                                                                   const __grid_constant__ CUtensorMap tm_b,
                                                                    LadArgs p) {
     constexpr int BK = bk_for(S), STAGES = stages_for(S);
     constexpr uint32_t APLANE = kEmuTile * BK * 2;
@@ -521,8 +522,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1) ladder_emu_kernel(const __grid_
         mbar_init(&acc_empty, kEpiWarps);
         mbar_init(&done, 1);
         fence_barrier_init();
-        tma_prefetch_desc(&tm_v);
-        tma_prefetch_desc(&tm_t);
+        tma_prefetch_desc(&tm_a);
+        tma_prefetch_desc(&tm_b);
     }
     if (warp == 1) tmem_alloc(&tmem_base, kTmemCols);
     tc_fence_before();
@@ -545,8 +546,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1) ladder_emu_kernel(const __grid_
                 if (!(ok = mbar_wait(&empty[ring.stage], ring.phase ^ 1u, p.status, kStatusTimeout))) break;
                 unsigned char* st = smem + ring.stage * stage_bytes(S);
                 mbar_arrive_expect_tx(&full[ring.stage], bytes);
-                tma_load_3d(st, &tm_v, &full[ring.stage], kb * BK, mt * kEmuTile, 0);
-                tma_load_3d(st + S * APLANE, &tm_t, &full[ring.stage], kb * BK, nt * p.BN, 0);
+                tma_load_3d(st, &tm_a, &full[ring.stage], kb * BK, mt * kEmuTile, 0);
+                tma_load_3d(st + S * APLANE, &tm_b, &full[ring.stage], kb * BK, nt * p.BN, 0);
                 ++issued[ring.stage];
                 ring.next(STAGES);
             }
@@ -624,8 +625,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1) ladder_emu_kernel(const __grid_
 #pragma unroll
                         for (int k = 0; k < 16; ++k) {
                             const int n = nt * p.BN + 16 * ci + k;
-                            if (m < p.npairs && n < p.no2 && run[i][k] != 0)
-                                atomicAdd(p.rp + (size_t)m * p.no2 + n, (unsigned long long)run[i][k]);
+                            if (m < p.M && n < p.N && run[i][k] != 0) {
+                                const size_t idx = p.swap ? (size_t)n * p.no2 + m : (size_t)m * p.no2 + n;
+                                atomicAdd(p.rp + idx, (unsigned long long)run[i][k]);
+                            }
                             run[i][k] = 0;
                         }
                     }
@@ -738,7 +741,8 @@ cudaError_t block_impl(const ladder_plan_s& p, const BlockPair& bp, double* R, v
     const size_t vplane = (size_t)p.max_pairs * kpad;
     const int smem = smem_bytes_for(S);
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(eri_emu_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess ||
+    if ((e = cudaFuncSetAttribute(eri_emu_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  eri_smem_bytes_for(S))) != cudaSuccess ||
         (e = cudaFuncSetAttribute(ladder_emu_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) !=
             cudaSuccess)
         return e;
@@ -749,9 +753,9 @@ cudaError_t block_impl(const ladder_plan_s& p, const BlockPair& bp, double* R, v
     const int* row_start = reinterpret_cast<const int*>(p.d_tables) + bp.rows_off;
     CUtensorMap tm_la, tm_lb, tm_v, tm_t;
     if (!make_tmap(&tm_la, at<char>(ws, p.ws.lt_slices), p.nchol, nv2, S, (uint64_t)xpad * 2, (uint64_t)nv2 * xpad * 2,
-                   BK, kEmuTile / 2, 1) ||
+                   BK, kEmuTile) ||
         !make_tmap(&tm_lb, at<char>(ws, p.ws.lt_slices), p.nchol, nv2, S, (uint64_t)xpad * 2, (uint64_t)nv2 * xpad * 2,
-                   BK, kEmuTileN))
+                   BK, kEmuTileN / 2))
         return cudaErrorInvalidValue;
     EriArgs ea{p.nv, p.nchol, bp.a0, bp.a1 - bp.a0, bp.b0, bp.b1 - bp.b0, kpad, bp.ntiles, vplane,
                reinterpret_cast<const int4*>(table + bp.tiles_off), row_start, at<int>(ws, p.ws.lt_exp),
@@ -759,22 +763,35 @@ cudaError_t block_impl(const ladder_plan_s& p, const BlockPair& bp, double* R, v
     {
         LaunchTimer tm(p, s, LADDER_KERNEL_ERI);
         const int clusters = std::max(1, std::min(bp.ntiles, p.num_sms / 2));
-        eri_emu_kernel<S><<<2 * clusters, kThreadsTC, smem, s>>>(tm_la, tm_lb, ea);
+        eri_emu_kernel<S><<<2 * clusters, kThreadsTC, eri_smem_bytes_for(S), s>>>(tm_la, tm_lb, ea);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
 
-    const int BN = ladder_bn(no2);
-    if (!make_tmap(&tm_v, at<char>(ws, p.ws.v_blk), nv2, bp.npairs, S, (uint64_t)kpad * 2, (uint64_t)vplane * 2, BK,
-                   kEmuTile) ||
-        !make_tmap(&tm_t, at<char>(ws, p.ws.t_slices), nv2, no2, S, (uint64_t)kpad * 2, (uint64_t)no2 * kpad * 2, BK,
-                   BN))
-        return cudaErrorInvalidValue;
+    // Small o^2: rows (i,j) in one 128-row tile, columns = 96 pairs, so the V planes stream
+    // from HBM exactly once.  Larger o^2: rows = pairs, columns = (i,j) tiles of <= 96.
+    const bool swap = no2 <= kEmuTile;
+    const int BN = swap ? kEmuTileN : ladder_bn(no2);
     LadArgs la{};
-    la.npairs = bp.npairs;
+    la.swap = swap ? 1 : 0;
     la.no2 = no2;
+    la.M = swap ? no2 : bp.npairs;
+    la.N = swap ? bp.npairs : no2;
     la.BN = BN;
-    la.n_mt = (bp.npairs + kEmuTile - 1) / kEmuTile;
-    la.n_nt = (no2 + BN - 1) / BN;
+    if (swap) {
+        if (!make_tmap(&tm_t, at<char>(ws, p.ws.t_slices), nv2, no2, S, (uint64_t)kpad * 2, (uint64_t)no2 * kpad * 2,
+                       BK, kEmuTile) ||
+            !make_tmap(&tm_v, at<char>(ws, p.ws.v_blk), nv2, bp.npairs, S, (uint64_t)kpad * 2, (uint64_t)vplane * 2, BK,
+                       BN))
+            return cudaErrorInvalidValue;
+    } else {
+        if (!make_tmap(&tm_v, at<char>(ws, p.ws.v_blk), nv2, bp.npairs, S, (uint64_t)kpad * 2, (uint64_t)vplane * 2, BK,
+                       kEmuTile) ||
+            !make_tmap(&tm_t, at<char>(ws, p.ws.t_slices), nv2, no2, S, (uint64_t)kpad * 2, (uint64_t)no2 * kpad * 2,
+                       BK, BN))
+            return cudaErrorInvalidValue;
+    }
+    la.n_mt = (la.M + kEmuTile - 1) / kEmuTile;
+    la.n_nt = (la.N + BN - 1) / BN;
     la.nkb = (int)((nv2 + BK - 1) / BK);
     la.kb_per_chunk = kEmuChunkK / BK;
     la.n_ch = (la.nkb + la.kb_per_chunk - 1) / la.kb_per_chunk;
@@ -784,7 +801,7 @@ cudaError_t block_impl(const ladder_plan_s& p, const BlockPair& bp, double* R, v
     {
         LaunchTimer tm(p, s, LADDER_KERNEL_LADDER);
         ladder_emu_kernel<S><<<(unsigned)std::max<long long>(1, std::min<long long>(la.units, p.num_sms)),
-                               kThreadsTC, smem, s>>>(tm_v, tm_t, la);
+                               kThreadsTC, smem, s>>>(swap ? tm_t : tm_v, swap ? tm_v : tm_t, la);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     {
