@@ -244,11 +244,15 @@ struct Ring {
     }
 };
 
-// Issue the S(S+1)/2 slice-pair MMAs of one stage (BK / 16 K-steps) into the 4 accumulators.
+// Issue the S(S+1)/2 slice-pair MMAs of one stage (BK / 16 K-steps) into the 5 accumulators.
+// The shared-memory descriptors are built once per stage; each MMA only adds the plane
+// and K-step offset (in 16-byte units) to the start-address field.
 template <int S, bool PAIR = false>
 __device__ __forceinline__ void issue_pairs(uint32_t tmem, uint32_t sA, uint32_t sB, uint32_t a_plane_bytes,
                                             uint32_t b_plane_bytes, uint32_t idesc, bool (&first)[kNumAcc]) {
     constexpr int BK = bk_for(S);
+    const uint64_t da = smem_desc_kmajor(sA, BK * 2), db = smem_desc_kmajor(sB, BK * 2);
+    const uint32_t ap = a_plane_bytes >> 4, bp = b_plane_bytes >> 4;
 #pragma unroll
     for (int kk = 0; kk < BK / 16; ++kk) {
 #pragma unroll
@@ -256,8 +260,8 @@ __device__ __forceinline__ void issue_pairs(uint32_t tmem, uint32_t sA, uint32_t
 #pragma unroll
             for (int t = 0; t + s < S; ++t) {
                 const int j = (s + t + 2 < 6 ? s + t + 2 : 6) - 2;
-                const uint64_t ad = smem_desc_kmajor(sA + s * a_plane_bytes + kk * 32, BK * 2);
-                const uint64_t bd = smem_desc_kmajor(sB + t * b_plane_bytes + kk * 32, BK * 2);
+                const uint64_t ad = da + (uint64_t)(s * ap + kk * 2);
+                const uint64_t bd = db + (uint64_t)(t * bp + kk * 2);
                 if (PAIR)
                     mma_bf16_pair(tmem + j * kAccStride, ad, bd, idesc, first[j] ? 0u : 1u);
                 else
