@@ -151,20 +151,36 @@ int ladder_energy(ladder_plan_t plan, const double* t2, const double* R, double*
 
 /*
  * ladder_plan_batched -- one plan for n independent ladder instances of
- * uneven shape (no[k], nv[k], nchol[k]), run by ladder_apply_batched as one
- * persistent launch.  Tile shapes and splits come from the built-in tuner.
- * Same precision / nslices / budget / device meaning as ladder_plan.
+ * uneven shape (no[k], nv[k], nchol[k]), run by ladder_apply_batched.  Each
+ * instance gets its own sub-plan (blocking from the cost model within the
+ * budget share of one worker stream); the default schedule spreads the
+ * instances over enough worker streams that the largest one is the tail
+ * (ladder_tune_batched refines it by measurement).  Same precision / nslices /
+ * budget / device meaning as ladder_plan; the budget covers all streams.
  */
 int ladder_plan_batched(ladder_plan_t* out, int n, const int* no, const int* nv, const int* nchol,
                         int precision, int nslices, size_t ws_budget_bytes, int device);
 
 /*
  * ladder_apply_batched -- R[k] += ladder(L[k], t2[k]) for every instance k.
- * L, t2, R are HOST arrays of n device pointers.  No allocation and no host
- * synchronisation; the work can be captured in a CUDA graph.
+ * L, t2, R are HOST arrays of n device pointers.  The instances run on the
+ * plan's worker streams (longest-first assignment), forked from and joined
+ * back into `stream` with events, each stream with its own workspace slice.
+ * No allocation and no host synchronisation: the whole call can be captured
+ * into one CUDA graph from `stream`.
  */
 int ladder_apply_batched(ladder_plan_t plan, const double* const* L, const double* const* t2,
                          double* const* R, void* ws, cudaStream_t stream);
+
+/*
+ * ladder_tune_batched -- measured tuner of a batched plan: times
+ * ladder_apply_batched with 1, 2, 4, 8 worker streams (capped at the number of
+ * instances) on the given buffers and keeps the fastest schedule.  R[k] is
+ * accumulated into by every trial (pass scratch R).  Synchronises the stream.
+ * *best_streams (may be NULL) receives the chosen stream count.
+ */
+int ladder_tune_batched(ladder_plan_t plan, const double* const* L, const double* const* t2,
+                        double* const* R, void* ws, cudaStream_t stream, int* best_streams);
 
 /*
  * Per-kernel timing for benchmarks.  ladder_plan_set_timing(plan, 1) creates a

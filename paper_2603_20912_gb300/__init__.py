@@ -73,6 +73,8 @@ def _load():
     lib.ladder_plan_batched.restype = ci
     lib.ladder_apply_batched.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), vp, vp]
     lib.ladder_apply_batched.restype = ci
+    lib.ladder_tune_batched.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), vp, vp, pint]
+    lib.ladder_tune_batched.restype = ci
     lib.ladder_last_status.argtypes = [vp, vp]
     lib.ladder_last_status.restype = ci
     lib.ladder_plan_destroy.argtypes = [vp]
@@ -257,6 +259,21 @@ def ladder_apply_batched(plan: Plan, Ls, t2s, Rs, ws=None, stream=None):
     return Rs
 
 
+def ladder_tune_batched(plan: Plan, Ls, t2s, Rs, ws=None, stream=None) -> int:
+    """Measure 1/2/4/8 worker streams on these buffers (R receives every trial) and keep the fastest."""
+    n = len(Ls)
+    arr = ctypes.c_void_p * n
+    a = arr(*[_dev_ptr(x, "L").value for x in Ls])
+    b = arr(*[_dev_ptr(x, "t2").value for x in t2s])
+    c = arr(*[_dev_ptr(x, "R").value for x in Rs])
+    if ws is None:
+        ws = plan.workspace()
+    k = ctypes.c_int()
+    _check(_load().ladder_tune_batched(plan.handle, a, b, c, ctypes.c_void_p(ws.data_ptr()), _stream_handle(stream),
+                                       ctypes.byref(k)), "ladder_tune_batched")
+    return k.value
+
+
 def ladder_energy_noalloc(t2, R, E_dev, stream=None):
     """E_L into the device scalar E_dev without a plan and without any allocation.
 
@@ -282,5 +299,5 @@ EXPORTED_SYMBOLS = [
     "ladder_plan", "ladder_plan_set_blocks", "ladder_workspace_bytes", "ladder_plan_describe", "ladder_apply",
     "ladder_energy", "ladder_plan_batched", "ladder_apply_batched", "ladder_last_status", "ladder_plan_destroy",
     "ladder_strerror", "ladder_flops", "ladder_plan_dry", "ladder_plan_set_timing", "ladder_plan_timing",
-    "ladder_energy_noalloc",
+    "ladder_energy_noalloc", "ladder_tune_batched",
 ]

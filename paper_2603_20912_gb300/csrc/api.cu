@@ -283,6 +283,8 @@ void free_events(ladder_plan_s* p) {
 void destroy_plan(ladder_plan_s* p) {
     if (!p) return;
     for (auto* s : p->sub) destroy_plan(s);
+    for (auto w : p->workers) cudaStreamDestroy(w);
+    for (auto e : p->fork_join) cudaEventDestroy(e);
     int cur = -1;
     cudaGetDevice(&cur);
     if (cur != p->device) cudaSetDevice(p->device);
@@ -346,6 +348,10 @@ int make_plan(ladder_plan_s** out, int no, int nv, int nchol, int precision, int
         budget = (size_t)((double)free_b * 0.98 * 0.9);
     }
     p->budget = budget;
+    if (precision != LADDER_FP64 && ladder::emu_set_attributes(nslices) != cudaSuccess) {
+        destroy_plan(p);
+        return LADDER_ERR_CUDA;
+    }
     int rc = choose_blocking(*p);
     if (rc == LADDER_OK) {
         if (cudaMalloc(&p->d_status, sizeof(unsigned)) != cudaSuccess ||
@@ -364,6 +370,24 @@ int make_plan(ladder_plan_s** out, int no, int nv, int nchol, int precision, int
     }
     *out = p;
     return LADDER_OK;
+}
+
+// Longest-processing-time-first assignment of instances to k worker streams; the
+// workspace of a stream is the largest workspace among its instances.
+void schedule_batched(ladder_plan_s& p, int k) {
+    const int n = (int)p.sub.size();
+    k = std::max(1, std::min(k, std::min(n, p.max_streams)));
+    p.nstreams = k;
+    p.order.resize(n);
+    for (int i = 0; i < n; ++i) p.order[i] = i;
+    std::stable_sort(p.order.begin(), p.order.end(), [&](int x, int y) { return p.model_s[x] > p.model_s[y]; });
+    std::vector<double> load(k, 0.0);
+    p.stream_of.assign(n, 0);
+    for (int i : p.order) {
+        const int w = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        p.stream_of[i] = w;
+        load[w] += p.model_s[i];
+    }
 }
 
 }  // namespace
@@ -455,25 +479,58 @@ int ladder_plan_batched(ladder_plan_t* out, int n, const int* no, const int* nv,
     p->batched = true;
     p->precision = precision;
     p->device = device;
-    size_t ws = ladder::kAlign;
+    // Budget per worker stream: the caller's budget split over the streams the plan can use.
+    const int max_streams = std::min(n, 8);
+    size_t per_stream_budget = ws_budget_bytes;
+    if (per_stream_budget == 0) {
+        DeviceGuard g0(device);
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+            destroy_plan(p);
+            return LADDER_ERR_CUDA;
+        }
+        per_stream_budget = (size_t)((double)free_b * 0.98 * 0.9);
+    }
+    per_stream_budget /= (size_t)max_streams;
     for (int k = 0; k < n; ++k) {
         ladder_plan_s* s = nullptr;
-        const int rc = make_plan(&s, no[k], nv[k], nchol[k], precision, nslices, ws_budget_bytes, device);
+        const int rc = make_plan(&s, no[k], nv[k], nchol[k], precision, nslices, per_stream_budget, device);
         if (rc != LADDER_OK) {
             destroy_plan(p);
             return rc;
         }
         p->sub.push_back(s);
-        ws = std::max(ws, s->ws.total);
+        p->model_s.push_back(model_time(*s, s->bps));
     }
-    p->ws.total = ws;
     p->nslices = p->sub[0]->nslices;
+    p->num_sms = p->sub[0]->num_sms;
+    p->max_streams = max_streams;
     DeviceGuard guard(device);
-    if (cudaMalloc(&p->d_status, sizeof(unsigned)) != cudaSuccess ||
-        cudaMemset(p->d_status, 0, sizeof(unsigned)) != cudaSuccess) {
+    // Workspace: every stream slot large enough for any instance it may get.
+    size_t biggest = ladder::kAlign;
+    for (auto* s : p->sub) biggest = std::max(biggest, s->ws.total);
+    biggest = ladder::align_up(biggest, ladder::kAlign);
+    p->ws_off.resize(max_streams);
+    for (int w = 0; w < max_streams; ++w) p->ws_off[w] = (size_t)w * biggest;
+    p->ws.total = biggest * (size_t)max_streams;
+    p->workers.resize(max_streams, nullptr);
+    p->fork_join.resize(1 + max_streams, nullptr);
+    bool ok = true;
+    for (auto& w : p->workers) ok = ok && cudaStreamCreateWithFlags(&w, cudaStreamNonBlocking) == cudaSuccess;
+    for (auto& e : p->fork_join) ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaMalloc(&p->d_status, sizeof(unsigned)) == cudaSuccess &&
+         cudaMemset(p->d_status, 0, sizeof(unsigned)) == cudaSuccess;
+    if (!ok) {
         destroy_plan(p);
         return LADDER_ERR_CUDA;
     }
+    // Default schedule from the model: enough streams that the largest instance is the tail.
+    double total = 0.0, largest = 0.0;
+    for (double t : p->model_s) {
+        total += t;
+        largest = std::max(largest, t);
+    }
+    schedule_batched(*p, (int)std::ceil(total / std::max(largest, 1e-12)));
     *out = p;
     return LADDER_OK;
 }
@@ -481,11 +538,63 @@ int ladder_plan_batched(ladder_plan_t* out, int n, const int* no, const int* nv,
 int ladder_apply_batched(ladder_plan_t plan, const double* const* L, const double* const* t2, double* const* R,
                          void* ws, cudaStream_t stream) {
     if (!plan || !plan->batched || !L || !t2 || !R || !ws) return LADDER_ERR_ARG;
-    for (size_t k = 0; k < plan->sub.size(); ++k) {
-        const int rc = ladder_apply(plan->sub[k], L[k], t2[k], R[k], ws, stream);
-        if (rc != LADDER_OK) return rc;
+    if (!aligned256(ws)) return LADDER_ERR_ARG;
+    DeviceGuard guard(plan->device);
+    if (!guard.ok) return LADDER_ERR_CUDA;
+    const int k = plan->nstreams;
+    // fork: every worker stream waits for the work already queued on the caller's stream
+    if (cudaEventRecord(plan->fork_join[0], stream) != cudaSuccess) return LADDER_ERR_CUDA;
+    for (int w = 0; w < k; ++w)
+        if (cudaStreamWaitEvent(plan->workers[w], plan->fork_join[0], 0) != cudaSuccess) return LADDER_ERR_CUDA;
+    int rc = LADDER_OK;
+    for (int i : plan->order) {
+        const int w = plan->stream_of[i];
+        rc = ladder_apply(plan->sub[i], L[i], t2[i], R[i], static_cast<char*>(ws) + plan->ws_off[w],
+                          plan->workers[w]);
+        if (rc != LADDER_OK) break;
     }
-    return LADDER_OK;
+    // join: the caller's stream waits for every worker
+    for (int w = 0; w < k; ++w) {
+        if (cudaEventRecord(plan->fork_join[1 + w], plan->workers[w]) != cudaSuccess ||
+            cudaStreamWaitEvent(stream, plan->fork_join[1 + w], 0) != cudaSuccess)
+            return LADDER_ERR_CUDA;
+    }
+    return rc;
+}
+
+int ladder_tune_batched(ladder_plan_t plan, const double* const* L, const double* const* t2, double* const* R,
+                        void* ws, cudaStream_t stream, int* best_streams) {
+    if (!plan || !plan->batched) return LADDER_ERR_ARG;
+    DeviceGuard guard(plan->device);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return LADDER_ERR_CUDA;
+    int best_k = plan->nstreams;
+    float best_ms = 1e30f;
+    int rc = LADDER_OK;
+    std::vector<int> cands;
+    for (int k = 1; k < plan->max_streams; k *= 2) cands.push_back(k);
+    cands.push_back(plan->max_streams);
+    for (int k : cands) {
+        if (rc != LADDER_OK) break;
+        schedule_batched(*plan, k);
+        rc = ladder_apply_batched(plan, L, t2, R, ws, stream);  // warm-up of this schedule
+        if (rc != LADDER_OK) break;
+        if (cudaEventRecord(e0, stream) != cudaSuccess) rc = LADDER_ERR_CUDA;
+        if (rc == LADDER_OK) rc = ladder_apply_batched(plan, L, t2, R, ws, stream);
+        if (rc == LADDER_OK && (cudaEventRecord(e1, stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
+            rc = LADDER_ERR_CUDA;
+        float ms = 0.0f;
+        if (rc == LADDER_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = LADDER_ERR_CUDA;
+        if (rc == LADDER_OK && ms < best_ms) {
+            best_ms = ms;
+            best_k = plan->nstreams;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    schedule_batched(*plan, best_k);
+    if (best_streams) *best_streams = plan->nstreams;
+    return rc;
 }
 
 int ladder_plan_set_timing(ladder_plan_t plan, int enable) {

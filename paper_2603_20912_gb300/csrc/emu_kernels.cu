@@ -745,11 +745,6 @@ cudaError_t block_impl(const ladder_plan_s& p, const BlockPair& bp, double* R, v
     const size_t vplane = (size_t)p.max_pairs * kpad;
     const int smem = smem_bytes_for(S);
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(eri_emu_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  eri_smem_bytes_for(S))) != cudaSuccess ||
-        (e = cudaFuncSetAttribute(ladder_emu_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) !=
-            cudaSuccess)
-        return e;
     // int64 ladder accumulator of this block pair starts at zero
     if ((e = cudaMemsetAsync(at<char>(ws, p.ws.rp_int), 0, (size_t)bp.npairs * no2 * 8, s)) != cudaSuccess) return e;
 
@@ -820,11 +815,30 @@ cudaError_t block_impl(const ladder_plan_s& p, const BlockPair& bp, double* R, v
 
 }  // namespace
 
+template <int S>
+cudaError_t set_attributes() {
+    cudaError_t e = cudaFuncSetAttribute(eri_emu_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         eri_smem_bytes_for(S));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(ladder_emu_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes_for(S));
+    return e;
+}
+
 bool emu_supported(int no, int nv, int nchol, int nslices) {
     (void)no;
     (void)nv;
     (void)nchol;
     return nslices >= 5 && nslices <= 8;
+}
+
+cudaError_t emu_set_attributes(int nslices) {
+    switch (nslices) {
+        case 5: return set_attributes<5>();
+        case 6: return set_attributes<6>();
+        case 7: return set_attributes<7>();
+        case 8: return set_attributes<8>();
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_emu_prep(const ladder_plan_s& p, const double* L, const double* t2, void* ws, cudaStream_t s) {

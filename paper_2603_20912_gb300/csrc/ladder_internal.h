@@ -77,9 +77,19 @@ struct ladder_plan_s {
     std::vector<cudaEvent_t> ev_pool;
     std::vector<int> ev_kind;
     size_t ev_used = 0;
-    // Batched plans: sub-plans per instance.
+    // Batched plans: sub-plans per instance, executed on worker streams forked from the
+    // caller's stream (instance k runs on stream `stream_of[k]` with workspace slice
+    // `ws_off[stream_of[k]]`).
     std::vector<ladder_plan_s*> sub;
     bool batched = false;
+    int nstreams = 1;                  // worker streams used by the current schedule
+    int max_streams = 1;               // streams the workspace is sized for
+    std::vector<int> stream_of;        // per instance
+    std::vector<int> order;            // execution order of instances
+    std::vector<size_t> ws_off;        // per worker stream
+    std::vector<cudaStream_t> workers;
+    std::vector<cudaEvent_t> fork_join;  // [0] fork, [1 + w] join of worker w
+    std::vector<double> model_s;       // modelled seconds per instance
 };
 
 namespace ladder {
@@ -115,5 +125,6 @@ cudaError_t launch_emu_prep(const ladder_plan_s& p, const double* L, const doubl
 cudaError_t launch_emu_block(const ladder_plan_s& p, const BlockPair& bp, double* R, void* ws,
                              cudaStream_t s);
 bool emu_supported(int no, int nv, int nchol, int nslices);
+cudaError_t emu_set_attributes(int nslices);  // per device, before the first launch
 
 }  // namespace ladder

@@ -1,0 +1,111 @@
+"""Batched uneven instances (one call, worker streams, CUDA-graph capture) against the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2603_20912_gb300 as lad
+from ladder_inputs import batched_shapes, make_inputs
+from conftest import rel_fro
+from test_gpu_fp64 import check_sampled
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+EMU = lad.LADDER_EMU_BF16
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2603_20912_gb300 import build
+    build.build()
+
+
+SMALL = [(5, 19, 72), (3, 37, 45), (7, 24, 93), (2, 61, 40), (6, 9, 30), (4, 50, 120)]
+
+
+def _make(shapes, seed0=500):
+    host = [make_inputs(o, v, x, seed=seed0 + k)[:2] for k, (o, v, x) in enumerate(shapes)]
+    Ls = [torch.from_numpy(L).cuda() for L, _ in host]
+    ts = [torch.from_numpy(t).cuda() for _, t in host]
+    return host, Ls, ts
+
+
+@pytest.mark.parametrize("precision,tol", [(lad.LADDER_FP64, 1e-12), (EMU, 1e-10)])
+def test_small_batch_matches_oracle_per_instance(precision, tol):
+    host, Ls, ts = _make(SMALL)
+    plan = lad.ladder_plan_batched([s[0] for s in SMALL], [s[1] for s in SMALL], [s[2] for s in SMALL], precision)
+    Rs = [torch.zeros_like(t) for t in ts]
+    lad.ladder_apply_batched(plan, Ls, ts, Rs)
+    torch.cuda.synchronize()
+    assert plan.last_status() == lad.LADDER_OK
+    for (L, t), R in zip(host, Rs):
+        assert rel_fro(R.cpu().numpy(), oracle.ladder(L, t)) <= tol
+
+
+def test_batched_equals_single_plans_bitwise():
+    host, Ls, ts = _make(SMALL)
+    plan = lad.ladder_plan_batched([s[0] for s in SMALL], [s[1] for s in SMALL], [s[2] for s in SMALL], EMU)
+    Rs = [torch.zeros_like(t) for t in ts]
+    lad.ladder_apply_batched(plan, Ls, ts, Rs)
+    for (o, v, x), L, t, R in zip(SMALL, Ls, ts, Rs):
+        single = lad.ladder_plan(o, v, x, EMU)
+        R1 = torch.zeros_like(t)
+        lad.ladder_apply(single, L, t, R1)
+        torch.cuda.synchronize()
+        assert torch.equal(R, R1)
+
+
+def test_tuner_picks_a_schedule_and_results_stay_exact():
+    host, Ls, ts = _make(SMALL)
+    plan = lad.ladder_plan_batched([s[0] for s in SMALL], [s[1] for s in SMALL], [s[2] for s in SMALL], EMU)
+    ws = plan.workspace()
+    scratch = [torch.zeros_like(t) for t in ts]
+    k = lad.ladder_tune_batched(plan, Ls, ts, scratch, ws)
+    assert k in (1, 2, 4, 6)
+    Rs = [torch.zeros_like(t) for t in ts]
+    lad.ladder_apply_batched(plan, Ls, ts, Rs, ws)
+    torch.cuda.synchronize()
+    for (L, t), R in zip(host, Rs):
+        assert rel_fro(R.cpu().numpy(), oracle.ladder(L, t)) <= 1e-10
+
+
+def test_graph_capture_and_replay_is_deterministic():
+    host, Ls, ts = _make(SMALL)
+    plan = lad.ladder_plan_batched([s[0] for s in SMALL], [s[1] for s in SMALL], [s[2] for s in SMALL], EMU)
+    ws = plan.workspace()
+    Rs = [torch.zeros_like(t) for t in ts]
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        lad.ladder_apply_batched(plan, Ls, ts, Rs, ws, stream=s)   # warm-up outside capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        for R in Rs:
+            R.zero_()
+        lad.ladder_apply_batched(plan, Ls, ts, Rs, ws, stream=s)
+    outs = []
+    for _ in range(2):
+        g.replay()
+        torch.cuda.synchronize()
+        outs.append([R.clone() for R in Rs])
+    for a, b in zip(*outs):
+        assert torch.equal(a, b)
+    for (L, t), R in zip(host, outs[0]):
+        assert rel_fro(R.cpu().numpy(), oracle.ladder(L, t)) <= 1e-10
+
+
+def test_uneven_24_instance_batch_sampled_parity():
+    shapes = batched_shapes()
+    assert len(shapes) == 24
+    host = [make_inputs(s.no, s.nv, s.nchol, s.seed)[:2] for s in shapes]
+    Ls = [torch.from_numpy(L).cuda() for L, _ in host]
+    ts = [torch.from_numpy(t).cuda() for _, t in host]
+    plan = lad.ladder_plan_batched([s.no for s in shapes], [s.nv for s in shapes], [s.nchol for s in shapes], EMU)
+    Rs = [torch.zeros_like(t) for t in ts]
+    lad.ladder_apply_batched(plan, Ls, ts, Rs)
+    torch.cuda.synchronize()
+    assert plan.last_status() == lad.LADDER_OK
+    for k, ((L, t), R) in enumerate(zip(host, Rs)):
+        check_sampled(R.cpu().numpy(), L, t, 1e-10, nsample=8, seed=k)
