@@ -242,23 +242,105 @@ def measure_peaks():
     print(json.dumps(out), flush=True)
 
 
+def run_batched(args):
+    """24 uneven instances (no ~ U{5..30}, nv ~ U{60..320}, nchol = 3(no+nv)) in one
+    ladder_apply_batched call per step, captured once into a CUDA graph and replayed."""
+    import torch
+    import paper_2603_20912_gb300 as lad
+    from paper_2603_20912_gb300 import build
+    from ladder_inputs import batched_shapes, make_batched_inputs
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    build.build()
+    shapes = batched_shapes()
+    host = make_batched_inputs(shapes)
+    Ls = [torch.from_numpy(L).cuda() for L, _ in host]
+    ts = [torch.from_numpy(t).cuda() for _, t in host]
+    Rs = [torch.zeros_like(t) for t in ts]
+    precision = lad.LADDER_EMU_BF16 if args.precision == "emu" else lad.LADDER_FP64
+    plan = lad.ladder_plan_batched([s.no for s in shapes], [s.nv for s in shapes], [s.nchol for s in shapes],
+                                   precision, nslices=args.nslices, device=local)
+    ws = plan.workspace()
+    scratch = [torch.zeros_like(t) for t in ts]
+    k = lad.ladder_tune_batched(plan, Ls, ts, scratch, ws)
+    del scratch
+    flops = sum(lad.ladder_flops(s.no, s.nv, s.nchol) for s in shapes)
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(stream):
+        lad.ladder_apply_batched(plan, Ls, ts, Rs, ws, stream=stream)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        lad.ladder_apply_batched(plan, Ls, ts, Rs, ws, stream=stream)
+    for _ in range(args.warmup):
+        g.replay()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    barrier(world)
+    sampler.start()
+    time.sleep(0.3)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    cur = torch.cuda.current_stream()
+    ev0.record(cur)
+    for _ in range(args.steps):
+        g.replay()
+    ev1.record(cur)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms_total = max_over_ranks(ev0.elapsed_time(ev1), world)
+    value = world * flops * args.steps / (ms_total * 1e-3) / 1e12
+    fp64 = None
+    if args.fp64_reference:
+        ref = lad.ladder_plan_batched([s.no for s in shapes], [s.nv for s in shapes], [s.nchol for s in shapes],
+                                      lad.LADDER_FP64, device=local)
+        refws = ref.workspace()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for sh, L, t in zip(shapes, Ls, ts):   # 24 sequential FP64 calls
+            single = lad.ladder_plan(sh.no, sh.nv, sh.nchol, lad.LADDER_FP64, device=local)
+            lad.ladder_apply(single, L, t, torch.zeros_like(t))
+            torch.cuda.synchronize()
+        fp64_s = time.perf_counter() - t0
+        fp64 = {"seconds": fp64_s, "tflops": flops / fp64_s / 1e12, "speedup": fp64_s / (ms_total * 1e-3 / args.steps)}
+        del refws
+    if rank == 0:
+        line = {
+            "metric": "PP-ladder TFLOP/s", "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64-emulated(bf16 slices)" if precision == lad.LADDER_EMU_BF16 else "f64",
+            "data": "synthetic",
+            "config": {"workload": "c5: 24 uneven instances, no~U{5..30}, nv~U{60..320}, nchol=3(no+nv), seed 1239",
+                       "instances": len(shapes), "total_flops": flops, "worker_streams": k,
+                       "graph": "one CUDA graph replay per step"},
+            "clocks": clocks, "fp64_sequential": fp64,
+        }
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--config", default="c2", choices=sorted(CONFIGS))
+    ap.add_argument("--config", default="c2", choices=sorted(CONFIGS) + ["c5"])
     ap.add_argument("--shape", default=None, help="no,nv,nchol overriding --config (profiling runs)")
     ap.add_argument("--precision", default="emu", choices=["emu", "fp64"])
     ap.add_argument("--nslices", type=int, default=0)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--fp64-reference", action="store_true",
+                    help="c5: also time 24 sequential native-FP64 calls (slow)")
     ap.add_argument("--measure-peaks", action="store_true",
                     help="print torch/cuBLAS matmul throughput for fp64, bf16 and int8 and exit")
     args = ap.parse_args()
     if args.measure_peaks:
         measure_peaks()
+        return
+    if args.config == "c5":
+        run_batched(args)
         return
     cfg = CONFIGS[args.config]
     if args.shape:

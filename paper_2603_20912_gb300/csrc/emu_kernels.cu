@@ -117,6 +117,28 @@ __device__ __forceinline__ long long rescale(long long I, int sh, long long lim,
     return N;
 }
 
+// round-half-even(x * 2^k) from the IEEE bits of x, with integer arithmetic only (the FP64
+// conversion units are slow on this GPU).  Requires |x 2^k| < 2^62.
+__device__ __forceinline__ long long scaled_rint(double x, int k) {
+    const long long bits = __double_as_longlong(x);
+    const int e = (int)((bits >> 52) & 0x7FF);
+    const long long m = (bits & 0xFFFFFFFFFFFFFLL) | (e ? (1LL << 52) : 0LL);
+    const int ee = (e ? e : 1) - 1075 + k;  // |x| = m 2^(e - 1075)
+    long long r;
+    if (m == 0) {
+        r = 0;
+    } else if (ee >= 0) {
+        r = m << (ee < 10 ? ee : 10);
+    } else if (ee < -54) {
+        r = 0;
+    } else {
+        const int sh = -ee;
+        const long long q = m >> sh, rem = m & ((1LL << sh) - 1), half = 1LL << (sh - 1);
+        r = q + ((rem > half || (rem == half && (q & 1))) ? 1 : 0);
+    }
+    return bits < 0 ? -r : r;
+}
+
 __device__ __forceinline__ int exponent_above(double m) {
     // smallest e with m < 2^(e-1); 0 for m == 0
     if (!(m > 0.0)) return 0;
@@ -180,7 +202,7 @@ __global__ void __launch_bounds__(256) lt_slice_kernel(const double* __restrict_
     for (int k = 0; k < 16; ++k) {
         const int P = P0 + pseg + k;
         if (P >= nchol) break;
-        const long long N = __double2ll_rn(scalbn(tile[pseg + k][rr], 7 * S - e));
+        const long long N = scaled_rint(tile[pseg + k][rr], 7 * S - e);
         __nv_bfloat16 d[S];
         digits_of<S>(N, d);
 #pragma unroll
@@ -223,7 +245,7 @@ __global__ void __launch_bounds__(256) t_slice_kernel(const double* __restrict__
         const long long k = k0 + j;
         const double x = k < K ? __ldg(t2 + (size_t)row * K + k) : 0.0;
         __nv_bfloat16 d[S];
-        digits_of<S>(__double2ll_rn(scalbn(x, 7 * S - e)), d);
+        digits_of<S>(scaled_rint(x, 7 * S - e), d);
 #pragma unroll
         for (int s = 0; s < S; ++s) out[s][j] = d[s];
     }
