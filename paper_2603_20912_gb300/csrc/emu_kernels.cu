@@ -198,15 +198,28 @@ __global__ void __launch_bounds__(256) lt_slice_kernel(const double* __restrict_
     if (r >= nv2) return;
     const int e = lt_exp[r0 / kG];
     const size_t plane = (size_t)nv2 * xpad;
-#pragma unroll 4
-    for (int k = 0; k < 16; ++k) {
-        const int P = P0 + pseg + k;
-        if (P >= nchol) break;
-        const long long N = scaled_rint(tile[pseg + k][rr], 7 * S - e);
-        __nv_bfloat16 d[S];
-        digits_of<S>(N, d);
+    const int P0t = P0 + pseg;
+    if (P0t >= nchol) return;
+    __align__(16) __nv_bfloat16 out[S][16];
 #pragma unroll
-        for (int s = 0; s < S; ++s) planes[s * plane + (size_t)r * xpad + P] = d[s];
+    for (int k = 0; k < 16; ++k) {
+        __nv_bfloat16 d[S];
+        digits_of<S>(scaled_rint(tile[pseg + k][rr], 7 * S - e), d);
+#pragma unroll
+        for (int s2 = 0; s2 < S; ++s2) out[s2][k] = d[s2];
+    }
+    if (P0t + 16 <= xpad) {
+        // 16 consecutive P of one row: two 16-byte stores per plane (xpad % 8 == 0, P0t % 16 == 0)
+#pragma unroll
+        for (int s2 = 0; s2 < S; ++s2) {
+            uint4* dst = reinterpret_cast<uint4*>(planes + s2 * plane + (size_t)r * xpad + P0t);
+            dst[0] = reinterpret_cast<const uint4*>(out[s2])[0];
+            dst[1] = reinterpret_cast<const uint4*>(out[s2])[1];
+        }
+    } else {
+        for (int k = 0; k < 16 && P0t + k < xpad; ++k)
+#pragma unroll
+            for (int s2 = 0; s2 < S; ++s2) planes[s2 * plane + (size_t)r * xpad + P0t + k] = out[s2][k];
     }
 }
 
@@ -294,6 +307,44 @@ __device__ __forceinline__ void issue_pairs(uint32_t tmem, uint32_t sA, uint32_t
     }
 }
 
+// Same MMAs in descending level order (levels >= 6 first, level 2 last).  When `wait`
+// is set (first stage of a tile or chunk), the first MMA into accumulator j waits for
+// the epilogue to have released j (per-accumulator barriers), so the next tile's MMAs
+// start while the epilogue still drains the lower-numbered accumulators.
+template <int S, bool PAIR>
+__device__ __forceinline__ bool issue_pairs_ordered(uint32_t tmem, uint32_t sA, uint32_t sB, uint32_t a_plane_bytes,
+                                                    uint32_t b_plane_bytes, uint32_t idesc, bool (&first)[kNumAcc],
+                                                    bool wait, uint64_t* acc_empty, uint32_t parity,
+                                                    unsigned* status) {
+    constexpr int BK = bk_for(S);
+    const uint64_t da = smem_desc_kmajor(sA, BK * 2), db = smem_desc_kmajor(sB, BK * 2);
+    const uint32_t ap = a_plane_bytes >> 4, bp = b_plane_bytes >> 4;
+#pragma unroll
+    for (int kk = 0; kk < BK / 16; ++kk) {
+#pragma unroll
+        for (int l = S + 1; l >= 2; --l) {
+            const int j = (l < 6 ? l : 6) - 2;
+            if (wait && kk == 0 && first[j]) {
+                if (!mbar_wait(&acc_empty[j], parity, status, kStatusTimeout)) return false;
+                tc_fence_after();
+            }
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                const int t = l - 2 - s;  // 0-based: (s+1) + (t+1) = l
+                if (t < 0 || t >= S) continue;
+                const uint64_t ad = da + (uint64_t)(s * ap + kk * 2);
+                const uint64_t bd = db + (uint64_t)(t * bp + kk * 2);
+                if (PAIR)
+                    mma_bf16_pair(tmem + j * kAccStride, ad, bd, idesc, first[j] ? 0u : 1u);
+                else
+                    mma_bf16(tmem + j * kAccStride, ad, bd, idesc, first[j] ? 0u : 1u);
+                first[j] = false;
+            }
+        }
+    }
+    return true;
+}
+
 // Integer value of one accumulator in the fixed-point unit 2^(-7 unit_level):
 // accumulator j holds level j+2 (exact, value = integer * 2^(-7(j+2))) for j < 4,
 // and the levels >= 6 (rounded) for j = 4.
@@ -334,7 +385,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
     constexpr uint32_t ABYTES = S * APLANE;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    __shared__ uint64_t full[STAGES], empty[STAGES], acc_full, acc_empty, done;
+    __shared__ uint64_t full[STAGES], empty[STAGES], acc_full, acc_empty[kNumAcc], done;
     __shared__ uint32_t tmem_base;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t rank = cluster_ctarank();
@@ -345,7 +396,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
             mbar_init(&empty[i], 1);  // the leader's multicast commit
         }
         mbar_init(&acc_full, 1);
-        mbar_init(&acc_empty, 2 * kEpiWarps);
+        for (int j = 0; j < kNumAcc; ++j) mbar_init(&acc_empty[j], 2 * kEpiWarps);
         mbar_init(&done, 1);
         fence_barrier_init();
         tma_prefetch_desc(&tm_a);
@@ -388,15 +439,16 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
         int it = 0;
         for (int e = cluster; e < p.nentries && ok; e += nclusters) {
             for (int ch = 0; ch < nch && ok; ++ch, ++it) {
-                if (!(ok = mbar_wait(&acc_empty, (uint32_t)(it & 1) ^ 1u, p.status, kStatusTimeout))) break;
-                tc_fence_after();
                 bool first[kNumAcc] = {true, true, true, true, true};
-                const int kb1 = min((ch + 1) * kb_per_chunk, nkb);
-                for (int kb = ch * kb_per_chunk; kb < kb1 && ok; ++kb) {
+                const int kb0 = ch * kb_per_chunk, kb1 = min((ch + 1) * kb_per_chunk, nkb);
+                for (int kb = kb0; kb < kb1 && ok; ++kb) {
                     if (!(ok = mbar_wait(&full[ring.stage], ring.phase, p.status, kStatusTimeout))) break;
                     tc_fence_after();
                     const uint32_t st = smem_u32(smem + ring.stage * eri_stage_bytes(S));
-                    issue_pairs<S, true>(tmem, st, st + ABYTES, APLANE, BPLANE, idesc, first);
+                    if (!(ok = issue_pairs_ordered<S, true>(tmem, st, st + ABYTES, APLANE, BPLANE, idesc, first,
+                                                            kb == kb0, acc_empty, (uint32_t)(it & 1) ^ 1u,
+                                                            p.status)))
+                        break;
                     mma_commit_pair_mc(&empty[ring.stage], (uint16_t)0x3);
                     ring.next(STAGES);
                 }
@@ -410,7 +462,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
         // Warp: TMEM lane quadrant q (this CTA's tile rows 32q..32q+31), columns 48h..48h+47.
         const int q = warp & 3, h = (warp - 2) >> 2;
         const int Mrows = p.na * p.nv, Ncols = p.nb * p.nv;
-        const uint32_t acc_empty_leader = mapa_rank(smem_u32(&acc_empty), 0);
+        const uint32_t acc_empty_leader0 = mapa_rank(smem_u32(&acc_empty[0]), 0);  // barriers are 8 bytes apart
         long long run[3][16];
         int it = 0;
         bool ok = true;
@@ -423,26 +475,24 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
             for (int ch = 0; ch < nch; ++ch, ++it) {
                 if (!(ok = mbar_wait(&acc_full, (uint32_t)(it & 1), p.status, kStatusTimeout))) break;
                 tc_fence_after();
+                // Drain one accumulator at a time, levels >= 6 first, and release each at once.
 #pragma unroll
-                for (int cc = 0; cc < 3; ++cc) {
-                    const uint32_t base = tmem + ((uint32_t)(32 * q) << 16) + 48 * h + 16 * cc;
+                for (int jj = 0; jj < kNumAcc; ++jj) {
+                    const int j = kNumAcc - 1 - jj;
+                    const uint32_t base = tmem + ((uint32_t)(32 * q) << 16) + j * kAccStride + 48 * h;
                     uint32_t v[3][16];
                     tmem_ld16(base, v[0]);
-                    tmem_ld16(base + kAccStride, v[1]);
-                    tmem_ld16(base + 2 * kAccStride, v[2]);
+                    tmem_ld16(base + 16, v[1]);
+                    tmem_ld16(base + 32, v[2]);
                     tmem_ld_wait();
 #pragma unroll
-                    for (int k = 0; k < 16; ++k)
-                        run[cc][k] += acc_fixed<7>(0, v[0][k]) + acc_fixed<7>(1, v[1][k]) + acc_fixed<7>(2, v[2][k]);
-                    tmem_ld16(base + 3 * kAccStride, v[0]);
-                    tmem_ld16(base + 4 * kAccStride, v[1]);
-                    tmem_ld_wait();
+                    for (int cc = 0; cc < 3; ++cc)
 #pragma unroll
-                    for (int k = 0; k < 16; ++k) run[cc][k] += acc_fixed<7>(3, v[0][k]) + acc_fixed<7>(4, v[1][k]);
+                        for (int k = 0; k < 16; ++k) run[cc][k] += acc_fixed<7>(j, v[cc][k]);
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive_remote(acc_empty_leader0 + 8u * (uint32_t)j);
                 }
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive_remote(acc_empty_leader);
             }
             if (!ok) break;
             const int qt = en.y;
@@ -535,7 +585,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) ladder_emu_kernel(const __grid_
     constexpr uint32_t APLANE = kEmuTile * BK * 2;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    __shared__ uint64_t full[STAGES], empty[STAGES], acc_full, acc_empty, done;
+    __shared__ uint64_t full[STAGES], empty[STAGES], acc_full, acc_empty[kNumAcc], done;
     __shared__ uint32_t tmem_base;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t BPLANE = (uint32_t)p.BN * BK * 2;
@@ -545,7 +595,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) ladder_emu_kernel(const __grid_
             mbar_init(&empty[i], 1);
         }
         mbar_init(&acc_full, 1);
-        mbar_init(&acc_empty, kEpiWarps);
+        for (int j = 0; j < kNumAcc; ++j) mbar_init(&acc_empty[j], kEpiWarps);
         mbar_init(&done, 1);
         fence_barrier_init();
         tma_prefetch_desc(&tm_a);
@@ -587,15 +637,15 @@ __global__ void __launch_bounds__(kThreadsTC, 1) ladder_emu_kernel(const __grid_
         int it = 0;
         for (long long u = u0; u < u1 && ok; ++u, ++it) {
             const int ch = (int)(u % p.n_ch);
-            if (!(ok = mbar_wait(&acc_empty, (uint32_t)(it & 1) ^ 1u, p.status, kStatusTimeout))) break;
-            tc_fence_after();
             bool first[kNumAcc] = {true, true, true, true, true};
-            const int kb1 = min((ch + 1) * p.kb_per_chunk, p.nkb);
-            for (int kb = ch * p.kb_per_chunk; kb < kb1 && ok; ++kb) {
+            const int kb0 = ch * p.kb_per_chunk, kb1 = min((ch + 1) * p.kb_per_chunk, p.nkb);
+            for (int kb = kb0; kb < kb1 && ok; ++kb) {
                 if (!(ok = mbar_wait(&full[ring.stage], ring.phase, p.status, kStatusTimeout))) break;
                 tc_fence_after();
                 const uint32_t st = smem_u32(smem + ring.stage * stage_bytes(S));
-                issue_pairs<S>(tmem, st, st + S * APLANE, APLANE, BPLANE, idesc, first);
+                if (!(ok = issue_pairs_ordered<S, false>(tmem, st, st + S * APLANE, APLANE, BPLANE, idesc, first,
+                                                         kb == kb0, acc_empty, (uint32_t)(it & 1) ^ 1u, p.status)))
+                    break;
                 mma_commit(&empty[ring.stage]);
                 ring.next(STAGES);
             }
@@ -616,29 +666,25 @@ __global__ void __launch_bounds__(kThreadsTC, 1) ladder_emu_kernel(const __grid_
         for (long long u = u0; u < u1; ++u, ++it) {
             if (!mbar_wait(&acc_full, (uint32_t)(it & 1), p.status, kStatusTimeout)) break;
             tc_fence_after();
+            // Drain one accumulator at a time (levels >= 6 first) and release each at once.
 #pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                const int ci = h + 2 * i;
-                if (ci < nchunks) {
-                    const uint32_t base = tmem + ((uint32_t)(32 * q) << 16) + 16 * ci;
-                    uint32_t v[3][16];
-                    tmem_ld16(base, v[0]);
-                    tmem_ld16(base + kAccStride, v[1]);
-                    tmem_ld16(base + 2 * kAccStride, v[2]);
-                    tmem_ld_wait();
+            for (int jj = 0; jj < kNumAcc; ++jj) {
+                const int j = kNumAcc - 1 - jj;
+                uint32_t v[3][16];
 #pragma unroll
-                    for (int k = 0; k < 16; ++k)
-                        run[i][k] += acc_fixed<6>(0, v[0][k]) + acc_fixed<6>(1, v[1][k]) + acc_fixed<6>(2, v[2][k]);
-                    tmem_ld16(base + 3 * kAccStride, v[0]);
-                    tmem_ld16(base + 4 * kAccStride, v[1]);
-                    tmem_ld_wait();
+                for (int i = 0; i < 3; ++i)
+                    if (h + 2 * i < nchunks)
+                        tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + j * kAccStride + 16 * (h + 2 * i), v[i]);
+                tmem_ld_wait();
 #pragma unroll
-                    for (int k = 0; k < 16; ++k) run[i][k] += acc_fixed<6>(3, v[0][k]) + acc_fixed<6>(4, v[1][k]);
-                }
+                for (int i = 0; i < 3; ++i)
+                    if (h + 2 * i < nchunks)
+#pragma unroll
+                        for (int k = 0; k < 16; ++k) run[i][k] += acc_fixed<6>(j, v[i][k]);
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&acc_empty[j]);
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&acc_empty);
             // Flush at the end of a (row tile, column tile) run or of this CTA's range.
             const long long tile = u / p.n_ch;
             if (u + 1 == u1 || (u + 1) / p.n_ch != tile) {
