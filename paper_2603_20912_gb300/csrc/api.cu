@@ -109,12 +109,14 @@ ladder::WsLayout layout_for(const ladder_plan_s& p, long long max_pairs) {
     if (p.precision == LADDER_FP64) {
         w.v_blk = take((size_t)max_pairs * nv2 * sizeof(double));
     } else {
+        // (c, d) rows padded to vp = nv rounded up to 8: K index c*vp + d, zero for d >= nv.
         const size_t S = p.nslices;
-        const size_t kpad = align_up(nv2, 8), xpad = align_up((size_t)p.nchol, 8);
+        const size_t vp = align_up((size_t)p.nv, 8), nvp = (size_t)p.nv * vp;
+        const size_t kpad = nvp, xpad = align_up((size_t)p.nchol, 8);
         w.v_blk = take(S * (size_t)max_pairs * kpad * 2);
         w.rp_int = take((size_t)max_pairs * no2 * 8);
-        w.lt_slices = take(S * nv2 * xpad * 2);
-        w.lt_exp = take(((nv2 + ladder::kExpGroupRows - 1) / ladder::kExpGroupRows) * 4);
+        w.lt_slices = take(S * nvp * xpad * 2);
+        w.lt_exp = take(((nvp + ladder::kExpGroupRows - 1) / ladder::kExpGroupRows) * 4);
         w.t_slices = take(S * no2 * kpad * 2);
         w.t_gmax = take(((no2 + ladder::kExpGroupRows - 1) / ladder::kExpGroupRows) * 8);
         w.t_exp = take(((no2 + ladder::kExpGroupRows - 1) / ladder::kExpGroupRows) * 4);
@@ -153,6 +155,7 @@ double model_time(const ladder_plan_s& p, const std::vector<BlockPair>& bps) {
 // when it holds some a <= b.  Order: a band of row tiles whose operand slices take
 // ~40 MB of L2 stays resident while every column tile of the band streams past it.
 std::vector<int> eri_entries(const BlockPair& bp, int nv, int tile, int tile_n, size_t row_bytes) {
+    nv = (nv + 7) / 8 * 8;  // rows and columns run over the padded (c, d) range
     std::vector<int> out;
     const long long M = (long long)(bp.a1 - bp.a0) * nv, N = (long long)(bp.b1 - bp.b0) * nv;
     const int nrt = (int)((M + tile - 1) / tile), nqt = (int)((N + tile_n - 1) / tile_n);

@@ -150,15 +150,18 @@ __device__ __forceinline__ int exponent_above(double m) {
 // ------------------------------------------------------------------ prep kernels
 // One block of 64 threads per group of 64 L^T rows r = (a,c): the group's exponent and,
 // per row, ||L[:, a, c]|| folded into max_c by an atomic max on the IEEE bits.
-__global__ void __launch_bounds__(64) lt_rowstats_kernel(const double* __restrict__ L, int nchol, int nv,
+// Rows are padded: r = a*vp + c, c < vp, the pad rows (c >= nv) are zero.
+__global__ void __launch_bounds__(64) lt_rowstats_kernel(const double* __restrict__ L, int nchol, int nv, int vp,
                                                          int* __restrict__ lt_exp,
                                                          unsigned long long* __restrict__ lnorm_bits) {
-    const long long nv2 = (long long)nv * nv;
+    const long long nv2 = (long long)nv * nv, rows = (long long)nv * vp;
     const long long r = (long long)blockIdx.x * kG + threadIdx.x;
+    const int a = (int)(r / vp), c = (int)(r % vp);
+    const bool valid = r < rows && c < nv;
     double m = 0.0, ss = 0.0;
-    if (r < nv2)
+    if (valid)
         for (int P = 0; P < nchol; ++P) {
-            const double x = __ldg(L + (size_t)P * nv2 + r);
+            const double x = __ldg(L + (size_t)P * nv2 + (size_t)a * nv + c);
             m = fmax(m, fabs(x));
             ss = fma(x, x, ss);
         }
@@ -167,7 +170,7 @@ __global__ void __launch_bounds__(64) lt_rowstats_kernel(const double* __restric
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
     __syncthreads();
     if (threadIdx.x == 0) lt_exp[blockIdx.x] = exponent_above(fmax(red[0], red[1]));
-    if (r < nv2) atomicMax(lnorm_bits + r / nv, (unsigned long long)__double_as_longlong(sqrt(ss)));
+    if (valid) atomicMax(lnorm_bits + a, (unsigned long long)__double_as_longlong(sqrt(ss)));
 }
 
 // f[a][b]: smallest f with max_c||L_ac|| max_d||L_bd|| (1 + 2^-20) < 2^(f-1).
@@ -181,23 +184,27 @@ __global__ void f_table_kernel(const unsigned long long* __restrict__ lnorm_bits
 
 // L^T slices: tile of 64 P x 64 rows through shared memory; writes planes[s][r][P].
 template <int S>
-__global__ void __launch_bounds__(256) lt_slice_kernel(const double* __restrict__ L, int nchol, int nv, int xpad,
-                                                       const int* __restrict__ lt_exp,
+__global__ void __launch_bounds__(256) lt_slice_kernel(const double* __restrict__ L, int nchol, int nv, int vp,
+                                                       int xpad, const int* __restrict__ lt_exp,
                                                        __nv_bfloat16* __restrict__ planes) {
     __shared__ double tile[64][65];
-    const long long nv2 = (long long)nv * nv;
+    const long long nv2 = (long long)nv * nv, rows = (long long)nv * vp;
     const int P0 = blockIdx.x * 64;
     const long long r0 = (long long)blockIdx.y * 64;
     for (int i = threadIdx.x; i < 64 * 64; i += 256) {
         const int p = i >> 6, rr = i & 63;
-        tile[p][rr] = (P0 + p < nchol && r0 + rr < nv2) ? __ldg(L + (size_t)(P0 + p) * nv2 + r0 + rr) : 0.0;
+        const long long r = r0 + rr;
+        const int c = (int)(r % vp);
+        tile[p][rr] = (P0 + p < nchol && r < rows && c < nv)
+                          ? __ldg(L + (size_t)(P0 + p) * nv2 + (size_t)(r / vp) * nv + c)
+                          : 0.0;
     }
     __syncthreads();
     const int rr = threadIdx.x >> 2, pseg = (threadIdx.x & 3) * 16;
     const long long r = r0 + rr;
-    if (r >= nv2) return;
+    if (r >= rows) return;
     const int e = lt_exp[r0 / kG];
-    const size_t plane = (size_t)nv2 * xpad;
+    const size_t plane = (size_t)rows * xpad;
     const int P0t = P0 + pseg;
     if (P0t >= nchol) return;
     __align__(16) __nv_bfloat16 out[S][16];
@@ -241,26 +248,29 @@ __global__ void exp_from_max_kernel(const unsigned long long* __restrict__ gmax,
 }
 
 // T slices: 8 consecutive k of one row per thread; planes[s][row][k] (row stride kpad).
+// K index k = c*vp + d of a row; zero for the pad columns d >= nv.
 template <int S>
-__global__ void __launch_bounds__(256) t_slice_kernel(const double* __restrict__ t2, long long K, int rows, int kpad,
-                                                      const int* __restrict__ t_exp,
+__global__ void __launch_bounds__(256) t_slice_kernel(const double* __restrict__ t2, int nv, int vp, int rows,
+                                                      int kpad, const int* __restrict__ t_exp,
                                                       __nv_bfloat16* __restrict__ planes) {
-    const long long per_row = (kpad + 7) / 8;
+    const long long per_row = kpad / 8;
     const long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= per_row * rows) return;
     const int row = (int)(u / per_row);
     const long long k0 = (u % per_row) * 8;
+    const int c = (int)(k0 / vp), d0 = (int)(k0 % vp);  // vp % 8 == 0: the 8 columns share c
     const int e = t_exp[row / kG];
     const size_t plane = (size_t)rows * kpad;
+    const double* src = t2 + ((size_t)row * nv + c) * nv;
     __align__(16) __nv_bfloat16 out[S][8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-        const long long k = k0 + j;
-        const double x = k < K ? __ldg(t2 + (size_t)row * K + k) : 0.0;
-        __nv_bfloat16 d[S];
-        digits_of<S>(scaled_rint(x, 7 * S - e), d);
+        const int dd = d0 + j;
+        const double x = dd < nv ? __ldg(src + dd) : 0.0;
+        __nv_bfloat16 dg[S];
+        digits_of<S>(scaled_rint(x, 7 * S - e), dg);
 #pragma unroll
-        for (int s = 0; s < S; ++s) out[s][j] = d[s];
+        for (int s = 0; s < S; ++s) out[s][j] = dg[s];
     }
 #pragma unroll
     for (int s = 0; s < S; ++s)
@@ -307,44 +317,6 @@ __device__ __forceinline__ void issue_pairs(uint32_t tmem, uint32_t sA, uint32_t
     }
 }
 
-// Same MMAs in descending level order (levels >= 6 first, level 2 last).  When `wait`
-// is set (first stage of a tile or chunk), the first MMA into accumulator j waits for
-// the epilogue to have released j (per-accumulator barriers), so the next tile's MMAs
-// start while the epilogue still drains the lower-numbered accumulators.
-template <int S, bool PAIR>
-__device__ __forceinline__ bool issue_pairs_ordered(uint32_t tmem, uint32_t sA, uint32_t sB, uint32_t a_plane_bytes,
-                                                    uint32_t b_plane_bytes, uint32_t idesc, bool (&first)[kNumAcc],
-                                                    bool wait, uint64_t* acc_empty, uint32_t parity,
-                                                    unsigned* status) {
-    constexpr int BK = bk_for(S);
-    const uint64_t da = smem_desc_kmajor(sA, BK * 2), db = smem_desc_kmajor(sB, BK * 2);
-    const uint32_t ap = a_plane_bytes >> 4, bp = b_plane_bytes >> 4;
-#pragma unroll
-    for (int kk = 0; kk < BK / 16; ++kk) {
-#pragma unroll
-        for (int l = S + 1; l >= 2; --l) {
-            const int j = (l < 6 ? l : 6) - 2;
-            if (wait && kk == 0 && first[j]) {
-                if (!mbar_wait(&acc_empty[j], parity, status, kStatusTimeout)) return false;
-                tc_fence_after();
-            }
-#pragma unroll
-            for (int s = 0; s < S; ++s) {
-                const int t = l - 2 - s;  // 0-based: (s+1) + (t+1) = l
-                if (t < 0 || t >= S) continue;
-                const uint64_t ad = da + (uint64_t)(s * ap + kk * 2);
-                const uint64_t bd = db + (uint64_t)(t * bp + kk * 2);
-                if (PAIR)
-                    mma_bf16_pair(tmem + j * kAccStride, ad, bd, idesc, first[j] ? 0u : 1u);
-                else
-                    mma_bf16(tmem + j * kAccStride, ad, bd, idesc, first[j] ? 0u : 1u);
-                first[j] = false;
-            }
-        }
-    }
-    return true;
-}
-
 // Integer value of one accumulator in the fixed-point unit 2^(-7 unit_level):
 // accumulator j holds level j+2 (exact, value = integer * 2^(-7(j+2))) for j < 4,
 // and the levels >= 6 (rounded) for j = 4.
@@ -359,7 +331,7 @@ __device__ __forceinline__ long long acc_fixed(int j, uint32_t bits) {
 }
 
 struct EriArgs {
-    int nv, nchol, a0, na, b0, nb, kpad, nentries;
+    int nv, vp, nchol, a0, na, b0, nb, kpad, nentries;
     size_t plane_stride;  // elements between V planes
     const int4* entries;  // (rt, qt for CTA rank 0 or -1, qt for CTA rank 1 or -1, 0)
     const int* row_start;
@@ -385,7 +357,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
     constexpr uint32_t ABYTES = S * APLANE;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    __shared__ uint64_t full[STAGES], empty[STAGES], acc_full, acc_empty[kNumAcc], done;
+    __shared__ uint64_t full[STAGES], empty[STAGES], acc_full, acc_empty, done;
     __shared__ uint32_t tmem_base;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t rank = cluster_ctarank();
@@ -396,7 +368,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
             mbar_init(&empty[i], 1);  // the leader's multicast commit
         }
         mbar_init(&acc_full, 1);
-        for (int j = 0; j < kNumAcc; ++j) mbar_init(&acc_empty[j], 2 * kEpiWarps);
+        mbar_init(&acc_empty, 2 * kEpiWarps);
         mbar_init(&done, 1);
         fence_barrier_init();
         tma_prefetch_desc(&tm_a);
@@ -418,8 +390,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
         bool ok = true;
         for (int e = cluster; e < p.nentries && ok; e += nclusters) {
             const int4 en = p.entries[e];
-            const int arow = p.a0 * p.nv + en.x * (2 * kEmuTile) + kEmuTile * (int)rank;
-            const int brow = p.b0 * p.nv + en.y * kEmuTileN + (kEmuTileN / 2) * (int)rank;
+            const int arow = p.a0 * p.vp + en.x * (2 * kEmuTile) + kEmuTile * (int)rank;
+            const int brow = p.b0 * p.vp + en.y * kEmuTileN + (kEmuTileN / 2) * (int)rank;
             for (int kb = 0; kb < nkb && ok; ++kb) {
                 if (!(ok = mbar_wait(&empty[ring.stage], ring.phase ^ 1u, p.status, kStatusTimeout))) break;
                 unsigned char* st = smem + ring.stage * eri_stage_bytes(S);
@@ -439,16 +411,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
         int it = 0;
         for (int e = cluster; e < p.nentries && ok; e += nclusters) {
             for (int ch = 0; ch < nch && ok; ++ch, ++it) {
+                if (!(ok = mbar_wait(&acc_empty, (uint32_t)(it & 1) ^ 1u, p.status, kStatusTimeout))) break;
+                tc_fence_after();
                 bool first[kNumAcc] = {true, true, true, true, true};
-                const int kb0 = ch * kb_per_chunk, kb1 = min((ch + 1) * kb_per_chunk, nkb);
-                for (int kb = kb0; kb < kb1 && ok; ++kb) {
+                const int kb1 = min((ch + 1) * kb_per_chunk, nkb);
+                for (int kb = ch * kb_per_chunk; kb < kb1 && ok; ++kb) {
                     if (!(ok = mbar_wait(&full[ring.stage], ring.phase, p.status, kStatusTimeout))) break;
                     tc_fence_after();
                     const uint32_t st = smem_u32(smem + ring.stage * eri_stage_bytes(S));
-                    if (!(ok = issue_pairs_ordered<S, true>(tmem, st, st + ABYTES, APLANE, BPLANE, idesc, first,
-                                                            kb == kb0, acc_empty, (uint32_t)(it & 1) ^ 1u,
-                                                            p.status)))
-                        break;
+                    issue_pairs<S, true>(tmem, st, st + ABYTES, APLANE, BPLANE, idesc, first);
                     mma_commit_pair_mc(&empty[ring.stage], (uint16_t)0x3);
                     ring.next(STAGES);
                 }
@@ -461,8 +432,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
         // ---------------- epilogue: exact int64 recombination, then re-slicing into the V planes.
         // Warp: TMEM lane quadrant q (this CTA's tile rows 32q..32q+31), columns 48h..48h+47.
         const int q = warp & 3, h = (warp - 2) >> 2;
-        const int Mrows = p.na * p.nv, Ncols = p.nb * p.nv;
-        const uint32_t acc_empty_leader0 = mapa_rank(smem_u32(&acc_empty[0]), 0);  // barriers are 8 bytes apart
+        const int Mrows = p.na * p.vp, Ncols = p.nb * p.vp;
+        const uint32_t acc_empty_leader = mapa_rank(smem_u32(&acc_empty), 0);
         long long run[3][16];
         int it = 0;
         bool ok = true;
@@ -475,79 +446,58 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
             for (int ch = 0; ch < nch; ++ch, ++it) {
                 if (!(ok = mbar_wait(&acc_full, (uint32_t)(it & 1), p.status, kStatusTimeout))) break;
                 tc_fence_after();
-                // Drain one accumulator at a time, levels >= 6 first, and release each at once.
 #pragma unroll
-                for (int jj = 0; jj < kNumAcc; ++jj) {
-                    const int j = kNumAcc - 1 - jj;
-                    const uint32_t base = tmem + ((uint32_t)(32 * q) << 16) + j * kAccStride + 48 * h;
+                for (int cc = 0; cc < 3; ++cc) {
+                    const uint32_t base = tmem + ((uint32_t)(32 * q) << 16) + 48 * h + 16 * cc;
                     uint32_t v[3][16];
                     tmem_ld16(base, v[0]);
-                    tmem_ld16(base + 16, v[1]);
-                    tmem_ld16(base + 32, v[2]);
+                    tmem_ld16(base + kAccStride, v[1]);
+                    tmem_ld16(base + 2 * kAccStride, v[2]);
                     tmem_ld_wait();
 #pragma unroll
-                    for (int cc = 0; cc < 3; ++cc)
+                    for (int k = 0; k < 16; ++k)
+                        run[cc][k] += acc_fixed<7>(0, v[0][k]) + acc_fixed<7>(1, v[1][k]) + acc_fixed<7>(2, v[2][k]);
+                    tmem_ld16(base + 3 * kAccStride, v[0]);
+                    tmem_ld16(base + 4 * kAccStride, v[1]);
+                    tmem_ld_wait();
 #pragma unroll
-                        for (int k = 0; k < 16; ++k) run[cc][k] += acc_fixed<7>(j, v[cc][k]);
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive_remote(acc_empty_leader0 + 8u * (uint32_t)j);
+                    for (int k = 0; k < 16; ++k) run[cc][k] += acc_fixed<7>(3, v[0][k]) + acc_fixed<7>(4, v[1][k]);
                 }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive_remote(acc_empty_leader);
             }
             if (!ok) break;
             const int qt = en.y;
             const int r_local = en.x * (2 * kEmuTile) + kEmuTile * (int)rank + 32 * q + lane;
-            if (r_local >= Mrows) continue;
-            const int a = p.a0 + r_local / p.nv, c = r_local % p.nv;
-            const int e_ac = p.lt_exp[(p.a0 * p.nv + r_local) / kG];
+            const int a = p.a0 + r_local / p.vp, c = r_local % p.vp;
+            if (r_local >= Mrows || c >= p.nv) continue;   // past the block or a pad row
+            const int e_ac = p.lt_exp[(p.a0 * p.vp + r_local) / kG];
             const int rs = p.row_start[a - p.a0];
-            const bool vec = (p.nv & 7) == 0;  // 8 consecutive d of one (a,b) row are 16-byte aligned
+            // Two runs of 8 columns per 16-column chunk; with vp % 8 == 0 each run lies in one b and
+            // starts at d % 8 == 0, so it is one 16-byte store per plane (pad columns come out zero).
 #pragma unroll
             for (int cc = 0; cc < 3; ++cc) {
-                const int col0 = qt * kEmuTileN + 48 * h + 16 * cc;
-                if (vec) {
-                    // Two runs of 8 columns; each lies in one b (nv % 8 == 0) and starts at d % 8 == 0.
 #pragma unroll
-                    for (int half = 0; half < 2; ++half) {
-                        const int col = col0 + 8 * half;
-                        const int b = p.b0 + col / p.nv, d = col % p.nv;
-                        if (col >= Ncols || a > b) continue;
-                        const int e_bd = p.lt_exp[(p.b0 * p.nv + col) / kG];
-                        const int sh = p.f_tab[a * p.nv + b] - e_ac - e_bd + 49 - 7 * S;
-                        __align__(16) __nv_bfloat16 out[S][8];
+                for (int half = 0; half < 2; ++half) {
+                    const int col = qt * kEmuTileN + 48 * h + 16 * cc + 8 * half;
+                    const int b = p.b0 + col / p.vp, d = col % p.vp;
+                    if (col >= Ncols || a > b) continue;
+                    const int e_bd = p.lt_exp[(p.b0 * p.vp + col) / kG];
+                    const int sh = p.f_tab[a * p.nv + b] - e_ac - e_bd + 49 - 7 * S;
+                    __align__(16) __nv_bfloat16 out[S][8];
 #pragma unroll
-                        for (int k = 0; k < 8; ++k) {
-                            __nv_bfloat16 dg[S];
-                            digits_of<S>(rescale(run[cc][8 * half + k], sh, 1LL << (7 * S - 1), p.status), dg);
+                    for (int k = 0; k < 8; ++k) {
+                        __nv_bfloat16 dg[S];
+                        digits_of<S>(rescale(run[cc][8 * half + k], sh, 1LL << (7 * S - 1), p.status), dg);
 #pragma unroll
-                            for (int s2 = 0; s2 < S; ++s2) out[s2][k] = dg[s2];
-                        }
-                        const size_t off = (size_t)(rs + (b - max(a, p.b0))) * p.kpad + (size_t)c * p.nv + d;
-#pragma unroll
-                        for (int s2 = 0; s2 < S; ++s2)
-                            *reinterpret_cast<uint4*>(p.vplanes + s2 * p.plane_stride + off) =
-                                *reinterpret_cast<const uint4*>(out[s2]);
+                        for (int s2 = 0; s2 < S; ++s2) out[s2][k] = dg[s2];
                     }
-                } else {
-                    int col = col0;
-                    int b = p.b0 + col / p.nv, d = col % p.nv;
+                    const size_t off = (size_t)(rs + (b - max(a, p.b0))) * p.kpad + (size_t)c * p.vp + d;
 #pragma unroll
-                    for (int k = 0; k < 16; ++k, ++col) {
-                        if (col < Ncols && a <= b) {
-                            const int e_bd = p.lt_exp[(p.b0 * p.nv + col) / kG];
-                            const int sh = p.f_tab[a * p.nv + b] - e_ac - e_bd + 49 - 7 * S;
-                            const long long Np = rescale(run[cc][k], sh, 1LL << (7 * S - 1), p.status);
-                            __nv_bfloat16 dg[S];
-                            digits_of<S>(Np, dg);
-                            const size_t off = (size_t)(rs + (b - max(a, p.b0))) * p.kpad + (size_t)c * p.nv + d;
-#pragma unroll
-                            for (int s2 = 0; s2 < S; ++s2) p.vplanes[s2 * p.plane_stride + off] = dg[s2];
-                        }
-                        if (++d == p.nv) {
-                            d = 0;
-                            ++b;
-                        }
-                    }
+                    for (int s2 = 0; s2 < S; ++s2)
+                        *reinterpret_cast<uint4*>(p.vplanes + s2 * p.plane_stride + off) =
+                            *reinterpret_cast<const uint4*>(out[s2]);
                 }
             }
         }
@@ -585,7 +535,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) ladder_emu_kernel(const __grid_
     constexpr uint32_t APLANE = kEmuTile * BK * 2;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    __shared__ uint64_t full[STAGES], empty[STAGES], acc_full, acc_empty[kNumAcc], done;
+    __shared__ uint64_t full[STAGES], empty[STAGES], acc_full, acc_empty, done;
     __shared__ uint32_t tmem_base;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t BPLANE = (uint32_t)p.BN * BK * 2;
@@ -595,7 +545,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) ladder_emu_kernel(const __grid_
             mbar_init(&empty[i], 1);
         }
         mbar_init(&acc_full, 1);
-        for (int j = 0; j < kNumAcc; ++j) mbar_init(&acc_empty[j], kEpiWarps);
+        mbar_init(&acc_empty, kEpiWarps);
         mbar_init(&done, 1);
         fence_barrier_init();
         tma_prefetch_desc(&tm_a);
@@ -637,15 +587,15 @@ __global__ void __launch_bounds__(kThreadsTC, 1) ladder_emu_kernel(const __grid_
         int it = 0;
         for (long long u = u0; u < u1 && ok; ++u, ++it) {
             const int ch = (int)(u % p.n_ch);
+            if (!(ok = mbar_wait(&acc_empty, (uint32_t)(it & 1) ^ 1u, p.status, kStatusTimeout))) break;
+            tc_fence_after();
             bool first[kNumAcc] = {true, true, true, true, true};
-            const int kb0 = ch * p.kb_per_chunk, kb1 = min((ch + 1) * p.kb_per_chunk, p.nkb);
-            for (int kb = kb0; kb < kb1 && ok; ++kb) {
+            const int kb1 = min((ch + 1) * p.kb_per_chunk, p.nkb);
+            for (int kb = ch * p.kb_per_chunk; kb < kb1 && ok; ++kb) {
                 if (!(ok = mbar_wait(&full[ring.stage], ring.phase, p.status, kStatusTimeout))) break;
                 tc_fence_after();
                 const uint32_t st = smem_u32(smem + ring.stage * stage_bytes(S));
-                if (!(ok = issue_pairs_ordered<S, false>(tmem, st, st + S * APLANE, APLANE, BPLANE, idesc, first,
-                                                         kb == kb0, acc_empty, (uint32_t)(it & 1) ^ 1u, p.status)))
-                    break;
+                issue_pairs<S>(tmem, st, st + S * APLANE, APLANE, BPLANE, idesc, first);
                 mma_commit(&empty[ring.stage]);
                 ring.next(STAGES);
             }
@@ -666,25 +616,29 @@ __global__ void __launch_bounds__(kThreadsTC, 1) ladder_emu_kernel(const __grid_
         for (long long u = u0; u < u1; ++u, ++it) {
             if (!mbar_wait(&acc_full, (uint32_t)(it & 1), p.status, kStatusTimeout)) break;
             tc_fence_after();
-            // Drain one accumulator at a time (levels >= 6 first) and release each at once.
 #pragma unroll
-            for (int jj = 0; jj < kNumAcc; ++jj) {
-                const int j = kNumAcc - 1 - jj;
-                uint32_t v[3][16];
+            for (int i = 0; i < 3; ++i) {
+                const int ci = h + 2 * i;
+                if (ci < nchunks) {
+                    const uint32_t base = tmem + ((uint32_t)(32 * q) << 16) + 16 * ci;
+                    uint32_t v[3][16];
+                    tmem_ld16(base, v[0]);
+                    tmem_ld16(base + kAccStride, v[1]);
+                    tmem_ld16(base + 2 * kAccStride, v[2]);
+                    tmem_ld_wait();
 #pragma unroll
-                for (int i = 0; i < 3; ++i)
-                    if (h + 2 * i < nchunks)
-                        tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + j * kAccStride + 16 * (h + 2 * i), v[i]);
-                tmem_ld_wait();
+                    for (int k = 0; k < 16; ++k)
+                        run[i][k] += acc_fixed<6>(0, v[0][k]) + acc_fixed<6>(1, v[1][k]) + acc_fixed<6>(2, v[2][k]);
+                    tmem_ld16(base + 3 * kAccStride, v[0]);
+                    tmem_ld16(base + 4 * kAccStride, v[1]);
+                    tmem_ld_wait();
 #pragma unroll
-                for (int i = 0; i < 3; ++i)
-                    if (h + 2 * i < nchunks)
-#pragma unroll
-                        for (int k = 0; k < 16; ++k) run[i][k] += acc_fixed<6>(j, v[i][k]);
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&acc_empty[j]);
+                    for (int k = 0; k < 16; ++k) run[i][k] += acc_fixed<6>(3, v[0][k]) + acc_fixed<6>(4, v[1][k]);
+                }
             }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty);
             // Flush at the end of a (row tile, column tile) run or of this CTA's range.
             const long long tile = u / p.n_ch;
             if (u + 1 == u1 || (u + 1) / p.n_ch != tile) {
@@ -776,29 +730,34 @@ int ladder_bn(int no2) {
     return std::max(16, (per + 15) / 16 * 16);
 }
 
+// Padded (c, d) layout of the emulated path: vp = nv rounded up to 8, K = nv * vp.
+inline int padded_vp(int nv) { return (nv + 7) / 8 * 8; }
+
 template <int S>
 cudaError_t prep_impl(const ladder_plan_s& p, const double* L, const double* t2, void* ws, cudaStream_t s) {
     const long long nv2 = (long long)p.nv * p.nv;
+    const int vp = padded_vp(p.nv);
+    const long long rows = (long long)p.nv * vp;
     const int no2 = p.no * p.no;
     const int xpad = (int)align_up((size_t)p.nchol, 8);
-    const int kpad = (int)align_up((size_t)nv2, 8);
+    const int kpad = (int)rows;
     const int ngt = (no2 + kG - 1) / kG;
     LaunchTimer tm(p, s, LADDER_KERNEL_PREP);
     cudaError_t e;
     if ((e = cudaMemsetAsync(at<char>(ws, p.ws.lnorm), 0, (size_t)p.nv * 8, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(at<char>(ws, p.ws.t_gmax), 0, (size_t)ngt * 8, s)) != cudaSuccess) return e;
-    lt_rowstats_kernel<<<(unsigned)((nv2 + kG - 1) / kG), kG, 0, s>>>(L, p.nchol, p.nv, at<int>(ws, p.ws.lt_exp),
-                                                                       at<unsigned long long>(ws, p.ws.lnorm));
+    lt_rowstats_kernel<<<(unsigned)((rows + kG - 1) / kG), kG, 0, s>>>(L, p.nchol, p.nv, vp, at<int>(ws, p.ws.lt_exp),
+                                                                        at<unsigned long long>(ws, p.ws.lnorm));
     f_table_kernel<<<(unsigned)((nv2 + 255) / 256), 256, 0, s>>>(at<unsigned long long>(ws, p.ws.lnorm), p.nv,
                                                                    at<int>(ws, p.ws.v_exp));
-    lt_slice_kernel<S><<<dim3((p.nchol + 63) / 64, (unsigned)((nv2 + 63) / 64)), 256, 0, s>>>(
-        L, p.nchol, p.nv, xpad, at<int>(ws, p.ws.lt_exp), at<__nv_bfloat16>(ws, p.ws.lt_slices));
+    lt_slice_kernel<S><<<dim3((p.nchol + 63) / 64, (unsigned)((rows + 63) / 64)), 256, 0, s>>>(
+        L, p.nchol, p.nv, vp, xpad, at<int>(ws, p.ws.lt_exp), at<__nv_bfloat16>(ws, p.ws.lt_slices));
     t_rowmax_kernel<<<dim3((unsigned)((nv2 + 8191) / 8192), no2), 256, 0, s>>>(t2, nv2, no2,
                                                                               at<unsigned long long>(ws, p.ws.t_gmax));
     exp_from_max_kernel<<<(ngt + 255) / 256, 256, 0, s>>>(at<unsigned long long>(ws, p.ws.t_gmax), ngt,
                                                            at<int>(ws, p.ws.t_exp));
-    const long long units = (long long)((kpad + 7) / 8) * no2;
-    t_slice_kernel<S><<<(unsigned)((units + 255) / 256), 256, 0, s>>>(t2, nv2, no2, kpad, at<int>(ws, p.ws.t_exp),
+    const long long units = (long long)(kpad / 8) * no2;
+    t_slice_kernel<S><<<(unsigned)((units + 255) / 256), 256, 0, s>>>(t2, p.nv, vp, no2, kpad, at<int>(ws, p.ws.t_exp),
                                                                       at<__nv_bfloat16>(ws, p.ws.t_slices));
     return cudaGetLastError();
 }
@@ -806,10 +765,11 @@ cudaError_t prep_impl(const ladder_plan_s& p, const double* L, const double* t2,
 template <int S>
 cudaError_t block_impl(const ladder_plan_s& p, const BlockPair& bp, double* R, void* ws, cudaStream_t s) {
     constexpr int BK = bk_for(S);
-    const long long nv2 = (long long)p.nv * p.nv;
+    const int vp = padded_vp(p.nv);
+    const long long rows = (long long)p.nv * vp;   // padded L^T rows = padded K of the ladder
     const int no2 = p.no * p.no;
     const int xpad = (int)align_up((size_t)p.nchol, 8);
-    const int kpad = (int)align_up((size_t)nv2, 8);
+    const int kpad = (int)rows;
     const size_t vplane = (size_t)p.max_pairs * kpad;
     const int smem = smem_bytes_for(S);
     cudaError_t e;
@@ -819,12 +779,12 @@ cudaError_t block_impl(const ladder_plan_s& p, const BlockPair& bp, double* R, v
     const int2* table = reinterpret_cast<const int2*>(p.d_tables);
     const int* row_start = reinterpret_cast<const int*>(p.d_tables) + bp.rows_off;
     CUtensorMap tm_la, tm_lb, tm_v, tm_t;
-    if (!make_tmap(&tm_la, at<char>(ws, p.ws.lt_slices), p.nchol, nv2, S, (uint64_t)xpad * 2, (uint64_t)nv2 * xpad * 2,
-                   BK, kEmuTile) ||
-        !make_tmap(&tm_lb, at<char>(ws, p.ws.lt_slices), p.nchol, nv2, S, (uint64_t)xpad * 2, (uint64_t)nv2 * xpad * 2,
-                   BK, kEmuTileN / 2))
+    if (!make_tmap(&tm_la, at<char>(ws, p.ws.lt_slices), p.nchol, rows, S, (uint64_t)xpad * 2,
+                   (uint64_t)rows * xpad * 2, BK, kEmuTile) ||
+        !make_tmap(&tm_lb, at<char>(ws, p.ws.lt_slices), p.nchol, rows, S, (uint64_t)xpad * 2,
+                   (uint64_t)rows * xpad * 2, BK, kEmuTileN / 2))
         return cudaErrorInvalidValue;
-    EriArgs ea{p.nv, p.nchol, bp.a0, bp.a1 - bp.a0, bp.b0, bp.b1 - bp.b0, kpad, bp.ntiles, vplane,
+    EriArgs ea{p.nv, vp, p.nchol, bp.a0, bp.a1 - bp.a0, bp.b0, bp.b1 - bp.b0, kpad, bp.ntiles, vplane,
                reinterpret_cast<const int4*>(table + bp.tiles_off), row_start, at<int>(ws, p.ws.lt_exp),
                at<int>(ws, p.ws.v_exp), at<__nv_bfloat16>(ws, p.ws.v_blk), p.d_status};
     {
@@ -845,21 +805,21 @@ cudaError_t block_impl(const ladder_plan_s& p, const BlockPair& bp, double* R, v
     la.N = swap ? bp.npairs : no2;
     la.BN = BN;
     if (swap) {
-        if (!make_tmap(&tm_t, at<char>(ws, p.ws.t_slices), nv2, no2, S, (uint64_t)kpad * 2, (uint64_t)no2 * kpad * 2,
+        if (!make_tmap(&tm_t, at<char>(ws, p.ws.t_slices), kpad, no2, S, (uint64_t)kpad * 2, (uint64_t)no2 * kpad * 2,
                        BK, kEmuTile) ||
-            !make_tmap(&tm_v, at<char>(ws, p.ws.v_blk), nv2, bp.npairs, S, (uint64_t)kpad * 2, (uint64_t)vplane * 2, BK,
+            !make_tmap(&tm_v, at<char>(ws, p.ws.v_blk), kpad, bp.npairs, S, (uint64_t)kpad * 2, (uint64_t)vplane * 2, BK,
                        BN))
             return cudaErrorInvalidValue;
     } else {
-        if (!make_tmap(&tm_v, at<char>(ws, p.ws.v_blk), nv2, bp.npairs, S, (uint64_t)kpad * 2, (uint64_t)vplane * 2, BK,
+        if (!make_tmap(&tm_v, at<char>(ws, p.ws.v_blk), kpad, bp.npairs, S, (uint64_t)kpad * 2, (uint64_t)vplane * 2, BK,
                        kEmuTile) ||
-            !make_tmap(&tm_t, at<char>(ws, p.ws.t_slices), nv2, no2, S, (uint64_t)kpad * 2, (uint64_t)no2 * kpad * 2,
+            !make_tmap(&tm_t, at<char>(ws, p.ws.t_slices), kpad, no2, S, (uint64_t)kpad * 2, (uint64_t)no2 * kpad * 2,
                        BK, BN))
             return cudaErrorInvalidValue;
     }
     la.n_mt = (la.M + kEmuTile - 1) / kEmuTile;
     la.n_nt = (la.N + BN - 1) / BN;
-    la.nkb = (int)((nv2 + BK - 1) / BK);
+    la.nkb = (kpad + BK - 1) / BK;
     la.kb_per_chunk = kEmuChunkK / BK;
     la.n_ch = (la.nkb + la.kb_per_chunk - 1) / la.kb_per_chunk;
     la.units = (long long)la.n_mt * la.n_nt * la.n_ch;

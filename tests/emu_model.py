@@ -9,7 +9,9 @@ the plain FP64 definition in ``oracle/``.
 Scheme (FP64 emulated by BF16 digit slices, Ozaki-style splitting):
 
 * Row groups of G consecutive rows share one exponent e with
-  max|x| < 2^(e-1), so u = x 2^-e lies in (-1/2, 1/2).
+  max|x| < 2^(e-1), so u = x 2^-e lies in (-1/2, 1/2).  The rows of L^T are
+  (a, c) with c padded to vp = nv rounded up to 8 (zero pad rows), so the
+  groups are 64 consecutive padded rows, as in the kernels.
 * N = round_half_even(x 2^(7S - e)) (|N| <= 2^(7S-1)) is written in
   balanced base 128: N = sum_s d_s 128^(S-s), |d_s| <= 64.  Slice plane s
   holds d_s 2^(-7s) (exact in BF16: 7 significant bits).
@@ -116,8 +118,12 @@ def emulated_ladder(L: np.ndarray, t2: np.ndarray, S: int = 6, group: int = GROU
     """R = ladder(L, t2) through the emulation scheme (all pairs, no a <= b packing)."""
     nchol, nv, _ = L.shape
     no = t2.shape[0]
-    Lt = np.ascontiguousarray(L.reshape(nchol, nv * nv).T)     # rows (a, c), K = P
-    dL, eL = to_digits(Lt, S, group)
+    vp = (nv + 7) // 8 * 8
+    Ltp = np.zeros((nv, vp, nchol))
+    Ltp[:, :nv, :] = L.transpose(1, 2, 0)                        # rows (a, c padded), K = P
+    dLp, eLp = to_digits(Ltp.reshape(nv * vp, nchol), S, group)
+    valid = (np.arange(nv)[:, None] * vp + np.arange(nv)[None, :]).ravel()
+    dL, eL = dLp[:, valid, :], eLp[valid]
     I = np.zeros((nv * nv, nv * nv), dtype=np.int64)
     for k0 in range(0, nchol, chunk):
         sl = slice(k0, min(nchol, k0 + chunk))
