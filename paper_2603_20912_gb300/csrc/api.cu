@@ -57,11 +57,11 @@ Geometry geometry_for(const ladder_plan_s& p) {
         // BF16 tcgen05: ~1.5 PFLOP/s sustained; S(S+1)/2 slice products per element.
         const double pairs = 0.5 * p.nslices * (p.nslices + 1);
         const double sm_rate = 1.5e15 / std::max(1, p.num_sms);
-        const int nnt = (p.no * p.no + ladder::kEmuTileN - 1) / ladder::kEmuTileN;
-        const int ltn = ((p.no * p.no + nnt - 1) / nnt + 15) / 16 * 16;
-        g = {256, ladder::kEmuTileN, 1, 128, ltn, 1, 0, 0, 25e-6};
+        // ladder tiles: 96 pairs x (i,j) rows of 128 (one SM) or 256 (CTA pair)
+        const int lrows = p.no * p.no <= 128 ? 128 : 256;
+        g = {256, ladder::kEmuTileN, 1, ladder::kEmuTileN, lrows, 1, 0, 0, 25e-6};
         g.eri_tile_s = 2.0 * 128 * ladder::kEmuTileN * X * pairs / sm_rate + 3e-6;  // per SM of the pair
-        g.lad_tile_s = 2.0 * 128 * ltn * v2 * pairs / sm_rate + 3e-6;
+        g.lad_tile_s = 2.0 * ladder::kEmuTileN * lrows * v2 * pairs / sm_rate / (lrows / 128) + 3e-6;
     }
     return g;
 }

@@ -90,6 +90,39 @@ __device__ __forceinline__ void digits_of(long long N, __nv_bfloat16 (&out)[S]) 
     out[0] = __float2bfloat16_rn(small_int_to_float((int)N) * pow2f(-7));
 }
 
+// Balanced base-128 digits of N (|N| <= 2^(7S-1)) as floats d_s (unscaled), taking the low 21
+// bits (three digits) in 32-bit arithmetic and the carry into the high part, also 32-bit for
+// S <= 7.  Same digits as digits_of.
+template <int S>
+__device__ __forceinline__ void digits_f32(long long N, float (&out)[S]) {
+    if constexpr (S <= 7) {
+        int lo = (int)(N & 0x1FFFFF);
+        int hi = (int)(N >> 21);
+#pragma unroll
+        for (int s = S - 1; s >= S - 3; --s) {
+            const int low = ((lo + 64) & 127) - 64;
+            lo = (lo - low) >> 7;
+            out[s] = small_int_to_float(low);
+        }
+        hi += lo;
+#pragma unroll
+        for (int s = S - 4; s >= 1; --s) {
+            const int low = ((hi + 64) & 127) - 64;
+            hi = (hi - low) >> 7;
+            out[s] = small_int_to_float(low);
+        }
+        out[0] = small_int_to_float(hi);
+    } else {
+#pragma unroll
+        for (int s = S - 1; s >= 1; --s) {
+            const int low = (int)(((N + 64) & 127)) - 64;
+            N = (N - low) >> 7;
+            out[s] = small_int_to_float(low);
+        }
+        out[0] = small_int_to_float((int)N);
+    }
+}
+
 // round(I / 2^sh) with halves rounded up (sh <= 0 multiplies); values beyond
 // +-lim cannot occur for a valid exponent bound and are clamped and flagged.
 __device__ __forceinline__ long long rescale(long long I, int sh, long long lim, unsigned* status) {
@@ -476,29 +509,37 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
             const int rs = p.row_start[a - p.a0];
             // Two runs of 8 columns per 16-column chunk; with vp % 8 == 0 each run lies in one b and
             // starts at d % 8 == 0, so it is one 16-byte store per plane (pad columns come out zero).
+            int sh_run[6];
+            size_t off_run[6];
+            bool ok_run[6];
 #pragma unroll
-            for (int cc = 0; cc < 3; ++cc) {
+            for (int rr = 0; rr < 6; ++rr) {  // issue every table load of the tile's runs first
+                const int col = qt * kEmuTileN + 48 * h + 8 * rr;
+                const int b = p.b0 + col / p.vp, d = col % p.vp;
+                ok_run[rr] = col < Ncols && a <= b;
+                const int bb = ok_run[rr] ? b : a;
+                sh_run[rr] = p.f_tab[a * p.nv + bb] - e_ac - p.lt_exp[(p.b0 * p.vp + (ok_run[rr] ? col : 0)) / kG] +
+                             49 - 7 * S;
+                off_run[rr] = (size_t)(rs + (bb - max(a, p.b0))) * p.kpad + (size_t)c * p.vp + d;
+            }
 #pragma unroll
-                for (int half = 0; half < 2; ++half) {
-                    const int col = qt * kEmuTileN + 48 * h + 16 * cc + 8 * half;
-                    const int b = p.b0 + col / p.vp, d = col % p.vp;
-                    if (col >= Ncols || a > b) continue;
-                    const int e_bd = p.lt_exp[(p.b0 * p.vp + col) / kG];
-                    const int sh = p.f_tab[a * p.nv + b] - e_ac - e_bd + 49 - 7 * S;
-                    __align__(16) __nv_bfloat16 out[S][8];
+            for (int rr = 0; rr < 6; ++rr) {
+                if (!ok_run[rr]) continue;
+                __align__(16) __nv_bfloat162 out[S][4];
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) {
-                        __nv_bfloat16 dg[S];
-                        digits_of<S>(rescale(run[cc][8 * half + k], sh, 1LL << (7 * S - 1), p.status), dg);
-#pragma unroll
-                        for (int s2 = 0; s2 < S; ++s2) out[s2][k] = dg[s2];
-                    }
-                    const size_t off = (size_t)(rs + (b - max(a, p.b0))) * p.kpad + (size_t)c * p.vp + d;
+                for (int k = 0; k < 8; k += 2) {
+                    float d0[S], d1[S];
+                    digits_f32<S>(rescale(run[rr >> 1][8 * (rr & 1) + k], sh_run[rr], 1LL << (7 * S - 1), p.status), d0);
+                    digits_f32<S>(rescale(run[rr >> 1][8 * (rr & 1) + k + 1], sh_run[rr], 1LL << (7 * S - 1), p.status),
+                                  d1);
 #pragma unroll
                     for (int s2 = 0; s2 < S; ++s2)
-                        *reinterpret_cast<uint4*>(p.vplanes + s2 * p.plane_stride + off) =
-                            *reinterpret_cast<const uint4*>(out[s2]);
+                        out[s2][k >> 1] = __floats2bfloat162_rn(d0[s2] * pow2f(-7 * (s2 + 1)), d1[s2] * pow2f(-7 * (s2 + 1)));
                 }
+#pragma unroll
+                for (int s2 = 0; s2 < S; ++s2)
+                    *reinterpret_cast<uint4*>(p.vplanes + s2 * p.plane_stride + off_run[rr]) =
+                        *reinterpret_cast<const uint4*>(out[s2]);
             }
         }
         failed = !ok;
@@ -670,6 +711,147 @@ __global__ void __launch_bounds__(kThreadsTC, 1) ladder_emu_kernel(const __grid_
     }
 }
 
+// Ladder on CTA pairs, for o^2 > 128: rows = (i,j) in 256-row tiles (128 per CTA), columns =
+// 96 pairs (48 per CTA), 2-SM MMAs; V streams from HBM ceil(o^2 / 256) times.  Work units are
+// (row tile, column tile, K chunk) with the chunk fastest; cluster c takes a contiguous range of
+// units and each CTA flushes its int64 sums with atomics whenever the tile changes.
+template <int S>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
+    ladder_pair_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ CUtensorMap tm_b, LadArgs p) {
+    constexpr int BK = bk_for(S), STAGES = eri_stages_for(S);
+    constexpr uint32_t APLANE = kEmuTile * BK * 2, BPLANE = (kEmuTileN / 2) * BK * 2;
+    constexpr uint32_t ABYTES = S * APLANE;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    __shared__ uint64_t full[STAGES], empty[STAGES], acc_full, acc_empty, done;
+    __shared__ uint32_t tmem_base;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_ctarank();
+    const long long cluster = blockIdx.x >> 1, nclusters = gridDim.x >> 1;
+    const long long u0 = p.units * cluster / nclusters, u1 = p.units * (cluster + 1) / nclusters;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < STAGES; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        mbar_init(&acc_full, 1);
+        mbar_init(&acc_empty, 2 * kEpiWarps);
+        mbar_init(&done, 1);
+        fence_barrier_init();
+        tma_prefetch_desc(&tm_a);
+        tma_prefetch_desc(&tm_b);
+    }
+    if (warp == 1) tmem_alloc_pair(&tmem_base, kTmemCols);
+    tc_fence_before();
+    cluster_sync();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    bool failed = false;
+
+    if (warp == 0 && lane == 0) {
+        Ring ring;
+        bool ok = true;
+        for (long long u = u0; u < u1 && ok; ++u) {
+            const int ch = (int)(u % p.n_ch);
+            const long long tile = u / p.n_ch;
+            const int nt = (int)(tile % p.n_nt), mt = (int)(tile / p.n_nt);
+            const int arow = mt * 2 * kEmuTile + kEmuTile * (int)rank;
+            const int brow = nt * kEmuTileN + (kEmuTileN / 2) * (int)rank;
+            const int kb1 = min((ch + 1) * p.kb_per_chunk, p.nkb);
+            for (int kb = ch * p.kb_per_chunk; kb < kb1 && ok; ++kb) {
+                if (!(ok = mbar_wait(&empty[ring.stage], ring.phase ^ 1u, p.status, kStatusTimeout))) break;
+                unsigned char* st = smem + ring.stage * eri_stage_bytes(S);
+                if (rank == 0) mbar_arrive_expect_tx(&full[ring.stage], 2 * eri_stage_bytes(S));
+                const uint32_t fb = mapa_rank(smem_u32(&full[ring.stage]), 0);
+                tma_load_3d_2sm(st, &tm_a, fb, kb * BK, arow, 0);
+                tma_load_3d_2sm(st + ABYTES, &tm_b, fb, kb * BK, brow, 0);
+                ring.next(STAGES);
+            }
+        }
+        failed = !ok;
+    } else if (warp == 1 && lane == 0 && rank == 0) {
+        Ring ring;
+        const uint32_t idesc = idesc_bf16_f32(2 * kEmuTile, kEmuTileN);
+        bool ok = true;
+        int it = 0;
+        for (long long u = u0; u < u1 && ok; ++u, ++it) {
+            const int ch = (int)(u % p.n_ch);
+            if (!(ok = mbar_wait(&acc_empty, (uint32_t)(it & 1) ^ 1u, p.status, kStatusTimeout))) break;
+            tc_fence_after();
+            bool first[kNumAcc] = {true, true, true, true, true};
+            const int kb1 = min((ch + 1) * p.kb_per_chunk, p.nkb);
+            for (int kb = ch * p.kb_per_chunk; kb < kb1 && ok; ++kb) {
+                if (!(ok = mbar_wait(&full[ring.stage], ring.phase, p.status, kStatusTimeout))) break;
+                tc_fence_after();
+                const uint32_t st = smem_u32(smem + ring.stage * eri_stage_bytes(S));
+                issue_pairs<S, true>(tmem, st, st + ABYTES, APLANE, BPLANE, idesc, first);
+                mma_commit_pair_mc(&empty[ring.stage], (uint16_t)0x3);
+                ring.next(STAGES);
+            }
+            if (ok) mma_commit_pair_mc(&acc_full, (uint16_t)0x3);
+        }
+        mma_commit_pair_mc(&done, (uint16_t)0x3);
+        failed = !ok;
+    } else if (warp >= 2) {
+        const int q = warp & 3, h = (warp - 2) >> 2;
+        const uint32_t acc_empty_leader = mapa_rank(smem_u32(&acc_empty), 0);
+        long long run[3][16];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int k = 0; k < 16; ++k) run[i][k] = 0;
+        int it = 0;
+        bool ok = true;
+        for (long long u = u0; u < u1; ++u, ++it) {
+            if (!(ok = mbar_wait(&acc_full, (uint32_t)(it & 1), p.status, kStatusTimeout))) break;
+            tc_fence_after();
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) {
+                const uint32_t base = tmem + ((uint32_t)(32 * q) << 16) + 48 * h + 16 * cc;
+                uint32_t v[3][16];
+                tmem_ld16(base, v[0]);
+                tmem_ld16(base + kAccStride, v[1]);
+                tmem_ld16(base + 2 * kAccStride, v[2]);
+                tmem_ld_wait();
+#pragma unroll
+                for (int k = 0; k < 16; ++k)
+                    run[cc][k] += acc_fixed<6>(0, v[0][k]) + acc_fixed<6>(1, v[1][k]) + acc_fixed<6>(2, v[2][k]);
+                tmem_ld16(base + 3 * kAccStride, v[0]);
+                tmem_ld16(base + 4 * kAccStride, v[1]);
+                tmem_ld_wait();
+#pragma unroll
+                for (int k = 0; k < 16; ++k) run[cc][k] += acc_fixed<6>(3, v[0][k]) + acc_fixed<6>(4, v[1][k]);
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive_remote(acc_empty_leader);
+            const long long tile = u / p.n_ch;
+            if (u + 1 == u1 || (u + 1) / p.n_ch != tile) {
+                const int nt = (int)(tile % p.n_nt), mt = (int)(tile / p.n_nt);
+                const int m = mt * 2 * kEmuTile + kEmuTile * (int)rank + 32 * q + lane;  // (i,j)
+#pragma unroll
+                for (int cc = 0; cc < 3; ++cc)
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) {
+                        const int n = nt * kEmuTileN + 48 * h + 16 * cc + k;                  // pair
+                        if (m < p.M && n < p.N && run[cc][k] != 0)
+                            atomicAdd(p.rp + (size_t)n * p.no2 + m, (unsigned long long)run[cc][k]);
+                        run[cc][k] = 0;
+                    }
+            }
+        }
+        failed = !ok;
+    }
+    if (threadIdx.x == 64) mbar_wait(&done, 0, p.status, kStatusTimeout);
+    if (failed) grace_delay(2000000);
+    tc_fence_before();
+    cluster_sync();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc_pair(tmem, kTmemCols);
+    }
+}
+
 // R[i,j,a,b] += 2^(f_ab + g_ij - 42) J[(a,b), (i,j)] and the mirror R[j,i,b,a] for a < b.
 __global__ void finalize_kernel(const unsigned long long* __restrict__ rp, int npairs, int no, int nv,
                                 const int2* __restrict__ pairs, const int* __restrict__ f_tab,
@@ -724,11 +906,6 @@ T* at(void* ws, size_t off) {
     return reinterpret_cast<T*>(static_cast<char*>(ws) + off);
 }
 
-int ladder_bn(int no2) {
-    const int nt = (no2 + kEmuTileN - 1) / kEmuTileN;
-    const int per = (no2 + nt - 1) / nt;
-    return std::max(16, (per + 15) / 16 * 16);
-}
 
 // Padded (c, d) layout of the emulated path: vp = nv rounded up to 8, K = nv * vp.
 inline int padded_vp(int nv) { return (nv + 7) / 8 * 8; }
@@ -794,30 +971,22 @@ cudaError_t block_impl(const ladder_plan_s& p, const BlockPair& bp, double* R, v
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
 
-    // Small o^2: rows (i,j) in one 128-row tile, columns = 96 pairs, so the V planes stream
-    // from HBM exactly once.  Larger o^2: rows = pairs, columns = (i,j) tiles of <= 96.
-    const bool swap = no2 <= kEmuTile;
-    const int BN = swap ? kEmuTileN : ladder_bn(no2);
+    // Rows = (i,j), columns = 96 pairs, so the V planes stream from HBM once per row tile:
+    // o^2 <= 128 in one 128-row tile (one SM per tile); larger o^2 in 256-row tiles on CTA pairs.
+    const bool pair = no2 > kEmuTile;
+    const int BN = kEmuTileN;
     LadArgs la{};
-    la.swap = swap ? 1 : 0;
+    la.swap = 1;
     la.no2 = no2;
-    la.M = swap ? no2 : bp.npairs;
-    la.N = swap ? bp.npairs : no2;
+    la.M = no2;
+    la.N = bp.npairs;
     la.BN = BN;
-    if (swap) {
-        if (!make_tmap(&tm_t, at<char>(ws, p.ws.t_slices), kpad, no2, S, (uint64_t)kpad * 2, (uint64_t)no2 * kpad * 2,
-                       BK, kEmuTile) ||
-            !make_tmap(&tm_v, at<char>(ws, p.ws.v_blk), kpad, bp.npairs, S, (uint64_t)kpad * 2, (uint64_t)vplane * 2, BK,
-                       BN))
-            return cudaErrorInvalidValue;
-    } else {
-        if (!make_tmap(&tm_v, at<char>(ws, p.ws.v_blk), kpad, bp.npairs, S, (uint64_t)kpad * 2, (uint64_t)vplane * 2, BK,
-                       kEmuTile) ||
-            !make_tmap(&tm_t, at<char>(ws, p.ws.t_slices), kpad, no2, S, (uint64_t)kpad * 2, (uint64_t)no2 * kpad * 2,
-                       BK, BN))
-            return cudaErrorInvalidValue;
-    }
-    la.n_mt = (la.M + kEmuTile - 1) / kEmuTile;
+    if (!make_tmap(&tm_t, at<char>(ws, p.ws.t_slices), kpad, no2, S, (uint64_t)kpad * 2, (uint64_t)no2 * kpad * 2, BK,
+                   kEmuTile) ||
+        !make_tmap(&tm_v, at<char>(ws, p.ws.v_blk), kpad, bp.npairs, S, (uint64_t)kpad * 2, (uint64_t)vplane * 2, BK,
+                   pair ? BN / 2 : BN))
+        return cudaErrorInvalidValue;
+    la.n_mt = (la.M + (pair ? 2 : 1) * kEmuTile - 1) / ((pair ? 2 : 1) * kEmuTile);
     la.n_nt = (la.N + BN - 1) / BN;
     la.nkb = (kpad + BK - 1) / BK;
     la.kb_per_chunk = kEmuChunkK / BK;
@@ -827,8 +996,13 @@ cudaError_t block_impl(const ladder_plan_s& p, const BlockPair& bp, double* R, v
     la.status = p.d_status;
     {
         LaunchTimer tm(p, s, LADDER_KERNEL_LADDER);
-        ladder_emu_kernel<S><<<(unsigned)std::max<long long>(1, std::min<long long>(la.units, p.num_sms)),
-                               kThreadsTC, smem, s>>>(swap ? tm_t : tm_v, swap ? tm_v : tm_t, la);
+        if (pair) {
+            const long long clusters = std::max<long long>(1, std::min<long long>(la.units, p.num_sms / 2));
+            ladder_pair_kernel<S><<<(unsigned)(2 * clusters), kThreadsTC, eri_smem_bytes_for(S), s>>>(tm_t, tm_v, la);
+        } else {
+            ladder_emu_kernel<S><<<(unsigned)std::max<long long>(1, std::min<long long>(la.units, p.num_sms)),
+                                   kThreadsTC, smem, s>>>(tm_t, tm_v, la);
+        }
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     {
@@ -849,6 +1023,9 @@ cudaError_t set_attributes() {
                                          eri_smem_bytes_for(S));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(ladder_emu_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes_for(S));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(ladder_pair_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 eri_smem_bytes_for(S));
     return e;
 }
 
