@@ -21,7 +21,7 @@ from conftest import rel_fro
 
 sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
 from emu_model import emulated_ladder  # noqa: E402
-from test_gpu_fp64 import check_sampled, dev, gpu_ladder, assert_pair_symmetry, _golden_energy  # noqa: E402
+from test_gpu_fp64 import check_sampled, dev, gpu_ladder, assert_pair_symmetry, _golden, _golden_energy  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -145,6 +145,20 @@ def test_full_size_sampled_parity(name):
     assert_pair_symmetry(R, diag_tol=TOL_R)
     E = lad.ladder_energy(plan, dev(t2), dev(R))
     assert E == pytest.approx(oracle.energy(t2, R), rel=1e-12)
-    Eg = _golden_energy(name)
+    Eg, Fg = _golden_energy(name), _golden(name, "R_fro")
     if Eg is not None:
         assert abs(E - Eg) <= TOL_E
+    if Fg is not None:
+        assert abs(float(np.linalg.norm(R.ravel())) - Fg) <= TOL_R * Fg
+
+
+def test_c3_planner_split_is_bitwise_identical():
+    # A budget far below the one-batch workspace forces asymmetric a/b blocks at full size.
+    s = CONFIGS["c3"]
+    L, t2, _, _ = make_inputs(s.no, s.nv, s.nchol, s.seed)
+    R1, plan1 = gpu_ladder(L, t2, EMU)
+    budget = plan1.workspace_bytes() // 5
+    Rb, planb = gpu_ladder(L, t2, EMU, budget=budget)
+    d = planb.describe()
+    assert d["n_block_pairs"] > 1 and planb.workspace_bytes() <= budget
+    assert np.array_equal(Rb, R1)
