@@ -122,6 +122,7 @@ ladder::WsLayout layout_for(const ladder_plan_s& p, long long max_pairs) {
         w.t_exp = take(((no2 + ladder::kExpGroupRows - 1) / ladder::kExpGroupRows) * 4);
         w.v_exp = take(nv2 * 4);
         w.lnorm = take((size_t)p.nv * 8);
+        w.lsq = take(nv2 * 8);
     }
     w.total = std::max<size_t>(off, kAlign);
     return w;

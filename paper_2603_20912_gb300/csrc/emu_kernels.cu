@@ -23,7 +23,9 @@
 // registers; V = 2^(e_ac + e_bd - 49) I.  V is re-sliced for the ladder with
 // one exponent per (a,b) row taken from the Cauchy-Schwarz bound
 // |(ac|bd)| <= max_c ||L_ac|| max_d ||L_bd|| (the ERI is a Gram matrix), so no
-// pass over a whole V row is needed before slicing.
+// pass over a whole V row is needed before slicing.  The O(nv) entries per pair row
+// where a row of L^T meets itself (V_ab,ba and V_aa,cc) are rewritten from FP64 squared
+// norms: the level cut drops squares there, a one-signed error (eri_self_kernel).
 //
 // Ladder (C-split step 1, 'acbd,ecfd->efab'): rows (a,b), columns (i,j),
 // K = (c,d) = nv^2 in chunks of 1024.  Per chunk J = acc2 2^28 + acc3 2^21 +
@@ -182,11 +184,13 @@ __device__ __forceinline__ int exponent_above(double m) {
 
 // ------------------------------------------------------------------ prep kernels
 // One block of 64 threads per group of 64 L^T rows r = (a,c): the group's exponent and,
-// per row, ||L[:, a, c]|| folded into max_c by an atomic max on the IEEE bits.
+// per row, ||L[:, a, c]||^2 (kept for the self-product entries of the ERI) and ||L[:, a, c]||
+// folded into max_c by an atomic max on the IEEE bits.
 // Rows are padded: r = a*vp + c, c < vp, the pad rows (c >= nv) are zero.
 __global__ void __launch_bounds__(64) lt_rowstats_kernel(const double* __restrict__ L, int nchol, int nv, int vp,
                                                          int* __restrict__ lt_exp,
-                                                         unsigned long long* __restrict__ lnorm_bits) {
+                                                         unsigned long long* __restrict__ lnorm_bits,
+                                                         double* __restrict__ lsq) {
     const long long nv2 = (long long)nv * nv, rows = (long long)nv * vp;
     const long long r = (long long)blockIdx.x * kG + threadIdx.x;
     const int a = (int)(r / vp), c = (int)(r % vp);
@@ -203,7 +207,10 @@ __global__ void __launch_bounds__(64) lt_rowstats_kernel(const double* __restric
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
     __syncthreads();
     if (threadIdx.x == 0) lt_exp[blockIdx.x] = exponent_above(fmax(red[0], red[1]));
-    if (valid) atomicMax(lnorm_bits + a, (unsigned long long)__double_as_longlong(sqrt(ss)));
+    if (valid) {
+        lsq[(size_t)a * nv + c] = ss;
+        atomicMax(lnorm_bits + a, (unsigned long long)__double_as_longlong(sqrt(ss)));
+    }
 }
 
 // f[a][b]: smallest f with max_c||L_ac|| max_d||L_bd|| (1 + 2^-20) < 2^(f-1).
@@ -553,6 +560,61 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
         tc_fence_after();
         tmem_dealloc_pair(tmem, kTmemCols);
     }
+}
+
+// ------------------------------------------------------------------ self-product entries
+// In the Gram matrix V = L^T L^T^T two rows meet themselves where (a,c) and (b,d) name the
+// same values of the symmetric L: (c,d) = (b,a) in every pair row (a,b), V_ab,ba = ||L_ab||^2,
+// and (c,c) in the a = b rows, V_aa,cc = ||L_ac||^2.  There the slice products that the level
+// cut drops include the squares d_s d_s, which are never negative, so the cut biases exactly
+// these entries low, and E_L sums that bias coherently over all (i,j,a,b).  After the ERI of a
+// block this kernel rewrites them from the FP64 squared norms: one thread per pair row for
+// (b,a) (a < b), and one per (a, c) for the diagonal rows of the block.
+struct SelfArgs {
+    int nv, vp, kpad, a0, a1, b0, b1, npairs;
+    size_t plane_stride;
+    const int2* pairs;      // pair (a, b) of each V row of the block
+    const int* row_start;   // first V row of each a of the block
+    const int* f_tab;
+    const double* lsq;      // ||L[:, a, c]||^2 [nv][nv]
+    __nv_bfloat16* vplanes;
+    unsigned* status;
+};
+
+template <int S>
+__global__ void __launch_bounds__(256) eri_self_kernel(SelfArgs p) {
+    const long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int a, b, c, d;
+    long long row;
+    if (u < p.npairs) {
+        const int2 ab = p.pairs[u];
+        a = ab.x;
+        b = ab.y;
+        if (a == b) return;  // the diagonal rows are handled below, (b,a) = (a,a) included
+        c = b;
+        d = a;
+        row = u;
+    } else {
+        const int lo = max(p.a0, p.b0), hi = min(p.a1, p.b1);
+        const long long v = u - p.npairs;
+        if (hi <= lo || v >= (long long)(hi - lo) * p.nv) return;
+        a = lo + (int)(v / p.nv);
+        b = a;
+        c = (int)(v % p.nv);
+        d = c;
+        row = p.row_start[a - p.a0];  // the first row of a is (a, max(a, b0)) = (a, a)
+    }
+    long long N = scaled_rint(p.lsq[(size_t)a * p.nv + c], 7 * S - p.f_tab[a * p.nv + b]);
+    const long long lim = 1LL << (7 * S - 1);
+    if (N > lim) {  // cannot happen under the Cauchy-Schwarz exponent bound
+        atomicOr(p.status, kStatusNumeric);
+        N = lim;
+    }
+    __nv_bfloat16 dg[S];
+    digits_of<S>(N, dg);
+    const size_t off = (size_t)row * p.kpad + (size_t)c * p.vp + d;
+#pragma unroll
+    for (int s = 0; s < S; ++s) p.vplanes[s * p.plane_stride + off] = dg[s];
 }
 
 // ------------------------------------------------------------------ ladder kernel
@@ -924,7 +986,8 @@ cudaError_t prep_impl(const ladder_plan_s& p, const double* L, const double* t2,
     if ((e = cudaMemsetAsync(at<char>(ws, p.ws.lnorm), 0, (size_t)p.nv * 8, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(at<char>(ws, p.ws.t_gmax), 0, (size_t)ngt * 8, s)) != cudaSuccess) return e;
     lt_rowstats_kernel<<<(unsigned)((rows + kG - 1) / kG), kG, 0, s>>>(L, p.nchol, p.nv, vp, at<int>(ws, p.ws.lt_exp),
-                                                                        at<unsigned long long>(ws, p.ws.lnorm));
+                                                                        at<unsigned long long>(ws, p.ws.lnorm),
+                                                                        at<double>(ws, p.ws.lsq));
     f_table_kernel<<<(unsigned)((nv2 + 255) / 256), 256, 0, s>>>(at<unsigned long long>(ws, p.ws.lnorm), p.nv,
                                                                    at<int>(ws, p.ws.v_exp));
     lt_slice_kernel<S><<<dim3((p.nchol + 63) / 64, (unsigned)((rows + 63) / 64)), 256, 0, s>>>(
@@ -968,6 +1031,11 @@ cudaError_t block_impl(const ladder_plan_s& p, const BlockPair& bp, double* R, v
         LaunchTimer tm(p, s, LADDER_KERNEL_ERI);
         const int clusters = std::max(1, std::min(bp.ntiles, p.num_sms / 2));
         eri_emu_kernel<S><<<2 * clusters, kThreadsTC, eri_smem_bytes_for(S), s>>>(tm_la, tm_lb, ea);
+        const int ndiag = std::max(0, std::min(bp.a1, bp.b1) - std::max(bp.a0, bp.b0));
+        const long long nself = (long long)bp.npairs + (long long)ndiag * p.nv;
+        SelfArgs sa{p.nv, vp, kpad, bp.a0, bp.a1, bp.b0, bp.b1, bp.npairs, vplane, table + bp.pairs_off, row_start,
+                    at<int>(ws, p.ws.v_exp), at<double>(ws, p.ws.lsq), at<__nv_bfloat16>(ws, p.ws.v_blk), p.d_status};
+        eri_self_kernel<S><<<(unsigned)((nself + 255) / 256), 256, 0, s>>>(sa);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
 

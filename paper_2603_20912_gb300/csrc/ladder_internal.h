@@ -48,6 +48,7 @@ struct WsLayout {
     size_t t_exp = 0;      // EMU: exponent per group of T rows (int)
     size_t v_exp = 0;      // EMU: exponent bound per (a, b) pair [nv][nv] (int)
     size_t lnorm = 0;      // EMU: max_c ||L[:, a, c]||_2 per a (IEEE bits, u64)
+    size_t lsq = 0;        // EMU: ||L[:, a, c]||_2^2 per (a, c) [nv][nv] (f64)
     size_t total = 0;
 };
 

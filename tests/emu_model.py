@@ -23,6 +23,10 @@ Scheme (FP64 emulated by BF16 digit slices, Ozaki-style splitting):
   + acc5 2^14 + round(A6 2^49), V = 2^(e_ac + e_bd - 49) I.  V is re-sliced
   per pair row (a, b) with the exponent f_ab of the Cauchy-Schwarz bound
   |(ac|bd)| <= max_c ||L_ac|| max_d ||L_bd||.
+* Entries where a row of L^T meets itself, V_ab,ba = ||L_ab||^2 and
+  V_aa,cc = ||L_ac||^2, are taken from the FP64 squared norms instead: the
+  level cut drops the squares d_s d_s there, an error of one sign that would
+  add up coherently in E_L.
 * Ladder (K = nv^2, chunks of 1024): per chunk J = acc2 2^28 + acc3 2^21
   + acc4 2^14 + acc5 2^7 + round(A6 2^42), summed exactly over chunks in
   int64; R_ij^ab = 2^(f_ab + g_ij - 42) sum J.
@@ -114,8 +118,12 @@ def pair_exponent_bound(L: np.ndarray) -> np.ndarray:
     return f
 
 
-def emulated_ladder(L: np.ndarray, t2: np.ndarray, S: int = 6, group: int = GROUP, chunk: int = CHUNK):
-    """R = ladder(L, t2) through the emulation scheme (all pairs, no a <= b packing)."""
+def emulated_ladder(L: np.ndarray, t2: np.ndarray, S: int = 6, group: int = GROUP, chunk: int = CHUNK,
+                    exact_self: bool = True):
+    """R = ladder(L, t2) through the emulation scheme (all pairs, no a <= b packing).
+
+    exact_self=False keeps the truncated level sums on the self-product entries too
+    (the uncorrected scheme, for comparison)."""
     nchol, nv, _ = L.shape
     no = t2.shape[0]
     vp = (nv + 7) // 8 * 8
@@ -135,6 +143,11 @@ def emulated_ladder(L: np.ndarray, t2: np.ndarray, S: int = 6, group: int = GROU
     e4 = eL.reshape(nv, nv)                                      # e_ac
     sh = f[:, :, None, None] - e4[:, None, :, None] - e4[None, :, None, :] + 49 - DIGIT_BITS * S
     Np = _round_shift(I4, sh).reshape(nv * nv, nv * nv)          # rows (a, b), K = (c, d)
+    if exact_self:
+        sq = np.sum(L * L, axis=0)                               # [a, c] = ||L[:, a, c]||^2
+        a_, b_ = np.meshgrid(np.arange(nv), np.arange(nv), indexing="ij")
+        Np[a_ * nv + b_, b_ * nv + a_] = np.rint(np.ldexp(sq[a_, b_], DIGIT_BITS * S - f[a_, b_])).astype(np.int64)
+        Np[a_ * nv + a_, b_ * nv + b_] = np.rint(np.ldexp(sq[a_, b_], DIGIT_BITS * S - f[a_, a_])).astype(np.int64)
     assert np.all(np.abs(Np) <= (1 << (DIGIT_BITS * S - 1)))
     dV = np.zeros((S,) + Np.shape, dtype=np.int64)
     M = Np.copy()
