@@ -30,12 +30,15 @@ def _built():
     build.build()
 
 
-def assert_pair_symmetry(R, diag_tol=1e-14):
+def assert_pair_symmetry(R, diag_tol=None):
     """R_ij^ab = R_ji^ba: exact for a != b (both written from one value); for a == b
-    R_ij^aa and R_ji^aa are separate evaluations (FP64: the same products summed in
-    another order; emulated: digits taken in different exponent groups), equal to diag_tol."""
+    R_ij^aa and R_ji^aa are separate evaluations (FP64: the same nv^2 products summed in
+    another order, a rounding difference growing like sqrt(nv^2) u, so the default is
+    nv 2^-50; emulated: digits taken in different exponent groups), equal to diag_tol."""
     Rt = R.transpose(1, 0, 3, 2)
     nv = R.shape[2]
+    if diag_tol is None:
+        diag_tol = nv * 2.0 ** -50
     off = ~np.eye(nv, dtype=bool)
     assert np.array_equal(R[:, :, off], Rt[:, :, off])
     d = np.arange(nv)
