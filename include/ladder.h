@@ -185,9 +185,9 @@ int ladder_tune_batched(ladder_plan_t plan, const double* const* L, const double
 /*
  * Per-kernel timing for benchmarks.  ladder_plan_set_timing(plan, 1) creates a
  * pool of CUDA events; while enabled, ladder_apply records an event pair on
- * its stream around every kernel it launches, tagged with the kernel class
+ * its stream around the launches of each kernel class, tagged with the class
  * (LADDER_KERNEL_*).  ladder_plan_timing waits for the recorded events and
- * returns, for one class, the summed elapsed milliseconds and the launch count
+ * returns, for one class, the summed elapsed milliseconds and the number of kernels launched
  * since the last reset; reset != 0 clears all records afterwards.  Timing is
  * off by default and costs nothing then.
  */

@@ -280,6 +280,7 @@ void free_events(ladder_plan_s* p) {
     for (auto e : p->ev_pool) cudaEventDestroy(e);
     p->ev_pool.clear();
     p->ev_kind.clear();
+    p->ev_kernels.clear();
     p->ev_used = 0;
     p->timing = false;
 }
@@ -612,6 +613,7 @@ int ladder_plan_set_timing(ladder_plan_t plan, int enable) {
         const size_t slots = 64 * (q->bps.size() + 8);
         q->ev_pool.resize(2 * slots);
         q->ev_kind.assign(slots, -1);
+        q->ev_kernels.assign(slots, 0);
         for (auto& e : q->ev_pool)
             if (cudaEventCreate(&e) != cudaSuccess) {
                 free_events(q);
@@ -637,7 +639,7 @@ int ladder_plan_timing(ladder_plan_t plan, int kernel_class, float* total_ms, in
             if (cudaEventElapsedTime(&ms, q->ev_pool[2 * k], q->ev_pool[2 * k + 1]) != cudaSuccess)
                 return LADDER_ERR_CUDA;
             sum += ms;
-            ++n;
+            n += q->ev_kernels[k];
         }
         if (reset) q->ev_used = 0;
     }

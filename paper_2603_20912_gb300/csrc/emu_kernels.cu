@@ -357,17 +357,22 @@ __device__ __forceinline__ void issue_pairs(uint32_t tmem, uint32_t sA, uint32_t
     }
 }
 
-// Integer value of one accumulator in the fixed-point unit 2^(-7 unit_level):
-// accumulator j holds level j+2 (exact, value = integer * 2^(-7(j+2))) for j < 4,
-// and the levels >= 6 (rounded) for j = 4.
-template <int UNIT_LEVEL>
-__device__ __forceinline__ long long acc_fixed(int j, uint32_t bits) {
-    const float x = __uint_as_float(bits);
-    if (j < 4) {
-        const int lvl = j + 2;
-        return (long long)__float2int_rn(x * pow2f(7 * lvl)) << (7 * (UNIT_LEVEL - lvl));
-    }
-    return __float2ll_rn(x * pow2f(7 * UNIT_LEVEL));
+// Accumulator j holds level j+2 (exact, value = integer * 2^(-7(j+2))) for j < 4 and the levels
+// >= 6 (rounded) for j = 4.  The exact levels are integers of magnitude <= K (l-1) 2^12 <= 2^24
+// (K <= 1024), so the pairs acc2 2^7 + acc3 and acc4 2^7 + acc5 stay below 2^30 and
+// 3 2^29 + 2^24 < 2^31: they are formed in 32-bit arithmetic and only the two pair sums and the
+// rounded tail are widened, in the fixed-point unit 2^(-7 U).
+__device__ __forceinline__ int acc_int(uint32_t bits, int lvl) {
+    return __float2int_rn(__uint_as_float(bits) * pow2f(7 * lvl));
+}
+template <int U>
+__device__ __forceinline__ long long acc_head(uint32_t b2, uint32_t b3) {
+    return (long long)(acc_int(b2, 2) * 128 + acc_int(b3, 3)) << (7 * (U - 3));
+}
+template <int U>
+__device__ __forceinline__ long long acc_tail(int i4, uint32_t b5, uint32_t b6) {
+    return ((long long)(i4 * 128 + acc_int(b5, 5)) << (7 * (U - 5))) +
+           __float2ll_rn(__uint_as_float(b6) * pow2f(7 * U));
 }
 
 struct EriArgs {
@@ -494,14 +499,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
                     tmem_ld16(base + kAccStride, v[1]);
                     tmem_ld16(base + 2 * kAccStride, v[2]);
                     tmem_ld_wait();
+                    int i4[16];
 #pragma unroll
-                    for (int k = 0; k < 16; ++k)
-                        run[cc][k] += acc_fixed<7>(0, v[0][k]) + acc_fixed<7>(1, v[1][k]) + acc_fixed<7>(2, v[2][k]);
+                    for (int k = 0; k < 16; ++k) {
+                        run[cc][k] += acc_head<7>(v[0][k], v[1][k]);
+                        i4[k] = acc_int(v[2][k], 4);
+                    }
                     tmem_ld16(base + 3 * kAccStride, v[0]);
                     tmem_ld16(base + 4 * kAccStride, v[1]);
                     tmem_ld_wait();
 #pragma unroll
-                    for (int k = 0; k < 16; ++k) run[cc][k] += acc_fixed<7>(3, v[0][k]) + acc_fixed<7>(4, v[1][k]);
+                    for (int k = 0; k < 16; ++k) run[cc][k] += acc_tail<7>(i4[k], v[0][k], v[1][k]);
                 }
                 tc_fence_before();
                 __syncwarp();
@@ -516,37 +524,31 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
             const int rs = p.row_start[a - p.a0];
             // Two runs of 8 columns per 16-column chunk; with vp % 8 == 0 each run lies in one b and
             // starts at d % 8 == 0, so it is one 16-byte store per plane (pad columns come out zero).
-            int sh_run[6];
-            size_t off_run[6];
-            bool ok_run[6];
 #pragma unroll
-            for (int rr = 0; rr < 6; ++rr) {  // issue every table load of the tile's runs first
-                const int col = qt * kEmuTileN + 48 * h + 8 * rr;
-                const int b = p.b0 + col / p.vp, d = col % p.vp;
-                ok_run[rr] = col < Ncols && a <= b;
-                const int bb = ok_run[rr] ? b : a;
-                sh_run[rr] = p.f_tab[a * p.nv + bb] - e_ac - p.lt_exp[(p.b0 * p.vp + (ok_run[rr] ? col : 0)) / kG] +
-                             49 - 7 * S;
-                off_run[rr] = (size_t)(rs + (bb - max(a, p.b0))) * p.kpad + (size_t)c * p.vp + d;
-            }
+            for (int cc = 0; cc < 3; ++cc) {
 #pragma unroll
-            for (int rr = 0; rr < 6; ++rr) {
-                if (!ok_run[rr]) continue;
-                __align__(16) __nv_bfloat162 out[S][4];
+                for (int half = 0; half < 2; ++half) {
+                    const int col = qt * kEmuTileN + 48 * h + 16 * cc + 8 * half;
+                    const int b = p.b0 + col / p.vp, d = col % p.vp;
+                    if (col >= Ncols || a > b) continue;
+                    const int e_bd = p.lt_exp[(p.b0 * p.vp + col) / kG];
+                    const int sh = p.f_tab[a * p.nv + b] - e_ac - e_bd + 49 - 7 * S;
+                    __align__(16) __nv_bfloat162 out[S][4];
 #pragma unroll
-                for (int k = 0; k < 8; k += 2) {
-                    float d0[S], d1[S];
-                    digits_f32<S>(rescale(run[rr >> 1][8 * (rr & 1) + k], sh_run[rr], 1LL << (7 * S - 1), p.status), d0);
-                    digits_f32<S>(rescale(run[rr >> 1][8 * (rr & 1) + k + 1], sh_run[rr], 1LL << (7 * S - 1), p.status),
-                                  d1);
+                    for (int k = 0; k < 8; k += 2) {
+                        float d0[S], d1[S];
+                        digits_f32<S>(rescale(run[cc][8 * half + k], sh, 1LL << (7 * S - 1), p.status), d0);
+                        digits_f32<S>(rescale(run[cc][8 * half + k + 1], sh, 1LL << (7 * S - 1), p.status), d1);
+#pragma unroll
+                        for (int s2 = 0; s2 < S; ++s2)
+                            out[s2][k >> 1] = __floats2bfloat162_rn(d0[s2] * pow2f(-7 * (s2 + 1)), d1[s2] * pow2f(-7 * (s2 + 1)));
+                    }
+                    const size_t off = (size_t)(rs + (b - max(a, p.b0))) * p.kpad + (size_t)c * p.vp + d;
 #pragma unroll
                     for (int s2 = 0; s2 < S; ++s2)
-                        out[s2][k >> 1] = __floats2bfloat162_rn(d0[s2] * pow2f(-7 * (s2 + 1)), d1[s2] * pow2f(-7 * (s2 + 1)));
+                        *reinterpret_cast<uint4*>(p.vplanes + s2 * p.plane_stride + off) =
+                            *reinterpret_cast<const uint4*>(out[s2]);
                 }
-#pragma unroll
-                for (int s2 = 0; s2 < S; ++s2)
-                    *reinterpret_cast<uint4*>(p.vplanes + s2 * p.plane_stride + off_run[rr]) =
-                        *reinterpret_cast<const uint4*>(out[s2]);
             }
         }
         failed = !ok;
@@ -730,13 +732,17 @@ __global__ void __launch_bounds__(kThreadsTC, 1) ladder_emu_kernel(const __grid_
                     tmem_ld16(base + 2 * kAccStride, v[2]);
                     tmem_ld_wait();
 #pragma unroll
-                    for (int k = 0; k < 16; ++k)
-                        run[i][k] += acc_fixed<6>(0, v[0][k]) + acc_fixed<6>(1, v[1][k]) + acc_fixed<6>(2, v[2][k]);
+                    int i4[16];
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) {
+                        run[i][k] += acc_head<6>(v[0][k], v[1][k]);
+                        i4[k] = acc_int(v[2][k], 4);
+                    }
                     tmem_ld16(base + 3 * kAccStride, v[0]);
                     tmem_ld16(base + 4 * kAccStride, v[1]);
                     tmem_ld_wait();
 #pragma unroll
-                    for (int k = 0; k < 16; ++k) run[i][k] += acc_fixed<6>(3, v[0][k]) + acc_fixed<6>(4, v[1][k]);
+                    for (int k = 0; k < 16; ++k) run[i][k] += acc_tail<6>(i4[k], v[0][k], v[1][k]);
                 }
             }
             tc_fence_before();
@@ -876,13 +882,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
                 tmem_ld16(base + 2 * kAccStride, v[2]);
                 tmem_ld_wait();
 #pragma unroll
-                for (int k = 0; k < 16; ++k)
-                    run[cc][k] += acc_fixed<6>(0, v[0][k]) + acc_fixed<6>(1, v[1][k]) + acc_fixed<6>(2, v[2][k]);
+                int i4[16];
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    run[cc][k] += acc_head<6>(v[0][k], v[1][k]);
+                    i4[k] = acc_int(v[2][k], 4);
+                }
                 tmem_ld16(base + 3 * kAccStride, v[0]);
                 tmem_ld16(base + 4 * kAccStride, v[1]);
                 tmem_ld_wait();
 #pragma unroll
-                for (int k = 0; k < 16; ++k) run[cc][k] += acc_fixed<6>(3, v[0][k]) + acc_fixed<6>(4, v[1][k]);
+                for (int k = 0; k < 16; ++k) run[cc][k] += acc_tail<6>(i4[k], v[0][k], v[1][k]);
             }
             tc_fence_before();
             __syncwarp();
@@ -981,7 +991,7 @@ cudaError_t prep_impl(const ladder_plan_s& p, const double* L, const double* t2,
     const int xpad = (int)align_up((size_t)p.nchol, 8);
     const int kpad = (int)rows;
     const int ngt = (no2 + kG - 1) / kG;
-    LaunchTimer tm(p, s, LADDER_KERNEL_PREP);
+    LaunchTimer tm(p, s, LADDER_KERNEL_PREP, 6);
     cudaError_t e;
     if ((e = cudaMemsetAsync(at<char>(ws, p.ws.lnorm), 0, (size_t)p.nv * 8, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(at<char>(ws, p.ws.t_gmax), 0, (size_t)ngt * 8, s)) != cudaSuccess) return e;
@@ -1028,7 +1038,7 @@ cudaError_t block_impl(const ladder_plan_s& p, const BlockPair& bp, double* R, v
                reinterpret_cast<const int4*>(table + bp.tiles_off), row_start, at<int>(ws, p.ws.lt_exp),
                at<int>(ws, p.ws.v_exp), at<__nv_bfloat16>(ws, p.ws.v_blk), p.d_status};
     {
-        LaunchTimer tm(p, s, LADDER_KERNEL_ERI);
+        LaunchTimer tm(p, s, LADDER_KERNEL_ERI, 2);
         const int clusters = std::max(1, std::min(bp.ntiles, p.num_sms / 2));
         eri_emu_kernel<S><<<2 * clusters, kThreadsTC, eri_smem_bytes_for(S), s>>>(tm_la, tm_lb, ea);
         const int ndiag = std::max(0, std::min(bp.a1, bp.b1) - std::max(bp.a0, bp.b0));

@@ -77,6 +77,7 @@ struct ladder_plan_s {
     bool timing = false;
     std::vector<cudaEvent_t> ev_pool;
     std::vector<int> ev_kind;
+    std::vector<int> ev_kernels;  // kernels launched between the two events of a slot
     size_t ev_used = 0;
     // Batched plans: sub-plans per instance, executed on worker streams forked from the
     // caller's stream (instance k runs on stream `stream_of[k]` with workspace slice
@@ -95,17 +96,19 @@ struct ladder_plan_s {
 
 namespace ladder {
 
-// Records an event pair around one launch when the plan has timing enabled.
+// Records an event pair around the `kernels` launches of one scope when the plan has
+// timing enabled.
 struct LaunchTimer {
     ladder_plan_s& p;
     cudaStream_t s;
     int kind;
     long slot = -1;
-    LaunchTimer(const ladder_plan_s& plan, cudaStream_t stream, int k)
+    LaunchTimer(const ladder_plan_s& plan, cudaStream_t stream, int k, int kernels = 1)
         : p(const_cast<ladder_plan_s&>(plan)), s(stream), kind(k) {
         if (p.timing && 2 * (p.ev_used + 1) <= p.ev_pool.size()) {
             slot = (long)p.ev_used++;
             p.ev_kind[slot] = kind;
+            p.ev_kernels[slot] = kernels;
             cudaEventRecord(p.ev_pool[2 * slot], s);
         }
     }
