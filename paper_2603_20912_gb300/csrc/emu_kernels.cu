@@ -51,8 +51,11 @@ namespace {
 using namespace tc;
 
 constexpr int kG = kExpGroupRows;  // rows per exponent group
-constexpr int kEpiWarps = 8;       // epilogue warps (2 per TMEM lane quadrant)
+constexpr int kEpiWarps = 8;       // ladder epilogue warps (2 per TMEM lane quadrant)
 constexpr int kThreadsTC = 32 * (2 + kEpiWarps);
+constexpr int kEriEpiWarps = 8;    // ERI epilogue warps (4 per TMEM lane quadrant)
+constexpr int kThreadsEri = 32 * (2 + kEriEpiWarps);
+constexpr int kEriRuns = kEmuTileN / (kEriEpiWarps / 4) / 8;  // runs of 8 columns per epilogue warp
 constexpr int kNumAcc = 5;         // exact levels 2, 3, 4, 5 and the shared levels >= 6
 constexpr int kTmemCols = 512;     // 5 accumulators x 96 columns, rounded up to a power of two
 constexpr int kAccStride = kEmuTileN;  // TMEM columns between accumulators
@@ -180,6 +183,59 @@ __device__ __forceinline__ int exponent_above(double m) {
     int E;
     frexp(m, &E);
     return E + 1;
+}
+
+// Balanced digits through a biased integer: with B = 64 (1 + 128 + ... + 128^(S-2)),
+// N + B = sum_{s>=1} (d_s + 64) 128^(S-1-s) + d_0 128^(S-1) holds the digits d_s + 64 in
+// [0, 127] as plain 7-bit fields, so each lower digit is a shift, a mask and one FFMA that
+// turns the field u into the float (u - 64) 2^(-7(s+1)) (exponent-bias trick: the float with
+// bits 0x4B400000 | u equals 1.5 2^23 + u).  d_0 is the arithmetic top of N + B.
+template <int S>
+__host__ __device__ constexpr long long digit_bias() {
+    long long b = 0;
+    for (int s = 1; s < S; ++s) b = b * 128 + 64;
+    return b;
+}
+
+// Re-slices one run of 8 int64 values I (unit 2^(-sh) of the plane grid) into S planes of
+// paired BF16 digits: N = round(I 2^-sh) (halves up), then the digits of N.  The fast path
+// covers 1 <= sh <= 63 - 7S, where I + 2^(sh-1) + B 2^sh cannot overflow (|I| < 2^(sh+7S-1));
+// other shifts take the general rescale.  A top digit beyond +-64 (an exponent bound that
+// does not hold) is flagged.
+template <int S>
+__device__ __forceinline__ void slice_run(const long long (&I)[8], int sh, __nv_bfloat162 (&out)[S][4],
+                                          unsigned* status) {
+    constexpr long long B = digit_bias<S>();
+    long long Nb[8];
+    if (sh >= 1 && sh <= 63 - 7 * S) {
+        const long long add = (1LL << (sh - 1)) + (B << sh);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) Nb[k] = (I[k] + add) >> sh;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) Nb[k] = rescale(I[k], sh, 1LL << (7 * S - 1), status) + B;
+    }
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < 8; k += 2) {
+        float f0[S], f1[S];
+#pragma unroll
+        for (int s = 1; s < S; ++s) {
+            const int sft = 7 * (S - 1 - s);
+            const float sc = pow2f(-7 * (s + 1)), off = -12582976.0f * sc;  // (1.5 2^23 + 64) 2^(-7(s+1))
+            const uint32_t u0 = (uint32_t)((unsigned long long)Nb[k] >> sft) & 127u;
+            const uint32_t u1 = (uint32_t)((unsigned long long)Nb[k + 1] >> sft) & 127u;
+            f0[s] = fmaf(__uint_as_float(0x4B400000u | u0), sc, off);
+            f1[s] = fmaf(__uint_as_float(0x4B400000u | u1), sc, off);
+        }
+        const int t0 = (int)(Nb[k] >> (7 * (S - 1))), t1 = (int)(Nb[k + 1] >> (7 * (S - 1)));
+        bad |= (unsigned)(t0 + 64) > 128u || (unsigned)(t1 + 64) > 128u;
+        f0[0] = fmaf(__int_as_float(0x4B400000 + t0), 0x1p-7f, -12582912.0f * 0x1p-7f);
+        f1[0] = fmaf(__int_as_float(0x4B400000 + t1), 0x1p-7f, -12582912.0f * 0x1p-7f);
+#pragma unroll
+        for (int s = 0; s < S; ++s) out[s][k >> 1] = __floats2bfloat162_rn(f0[s], f1[s]);
+    }
+    if (bad) atomicOr(status, kStatusNumeric);
 }
 
 // ------------------------------------------------------------------ prep kernels
@@ -395,7 +451,7 @@ struct EriArgs {
 // the epilogue warps of both CTAs release the accumulators to the leader.
 // K = nchol runs in exact chunks of kEmuChunkK.
 template <int S>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsEri, 1)
     eri_emu_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ CUtensorMap tm_b, EriArgs p) {
     constexpr int BK = bk_for(S), STAGES = eri_stages_for(S);
     constexpr uint32_t APLANE = kEmuTile * BK * 2, BPLANE = (kEmuTileN / 2) * BK * 2;
@@ -413,7 +469,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
             mbar_init(&empty[i], 1);  // the leader's multicast commit
         }
         mbar_init(&acc_full, 1);
-        mbar_init(&acc_empty, 2 * kEpiWarps);
+        mbar_init(&acc_empty, 2 * kEriEpiWarps);
         mbar_init(&done, 1);
         fence_barrier_init();
         tma_prefetch_desc(&tm_a);
@@ -430,9 +486,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
     bool failed = false;
 
     if (warp == 0 && lane == 0) {
-        // ---------------- TMA producer (both CTAs)
+        // ---------------- TMA producer (both CTAs).  The L^T slices are re-read by many tiles:
+        // they are kept in L2 ahead of the V planes, which are written once and streamed.
         Ring ring;
         bool ok = true;
+        const uint64_t keep = policy_evict_last();
         for (int e = cluster; e < p.nentries && ok; e += nclusters) {
             const int4 en = p.entries[e];
             const int arow = p.a0 * p.vp + en.x * (2 * kEmuTile) + kEmuTile * (int)rank;
@@ -442,8 +500,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
                 unsigned char* st = smem + ring.stage * eri_stage_bytes(S);
                 if (rank == 0) mbar_arrive_expect_tx(&full[ring.stage], 2 * eri_stage_bytes(S));
                 const uint32_t fb = mapa_rank(smem_u32(&full[ring.stage]), 0);
-                tma_load_3d_2sm(st, &tm_a, fb, kb * BK, arow, 0);
-                tma_load_3d_2sm(st + ABYTES, &tm_b, fb, kb * BK, brow, 0);
+                tma_load_3d_2sm_hint(st, &tm_a, fb, kb * BK, arow, 0, keep);
+                tma_load_3d_2sm_hint(st + ABYTES, &tm_b, fb, kb * BK, brow, 0, keep);
                 ring.next(STAGES);
             }
         }
@@ -475,41 +533,34 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
         failed = !ok;
     } else if (warp >= 2) {
         // ---------------- epilogue: exact int64 recombination, then re-slicing into the V planes.
-        // Warp: TMEM lane quadrant q (this CTA's tile rows 32q..32q+31), columns 48h..48h+47.
+        // Warp: TMEM lane quadrant q (this CTA's tile rows 32q..32q+31) and kEriRuns runs of 8
+        // columns.  Several warps per quadrant keep enough independent work in flight to re-slice
+        // a tile while the MMAs of the next one run.
         const int q = warp & 3, h = (warp - 2) >> 2;
         const int Mrows = p.na * p.vp, Ncols = p.nb * p.vp;
         const uint32_t acc_empty_leader = mapa_rank(smem_u32(&acc_empty), 0);
-        long long run[3][16];
+        long long run[kEriRuns][8];
         int it = 0;
         bool ok = true;
         for (int e = cluster; e < p.nentries && ok; e += nclusters) {
             const int4 en = p.entries[e];
 #pragma unroll
-            for (int cc = 0; cc < 3; ++cc)
+            for (int g = 0; g < kEriRuns; ++g)
 #pragma unroll
-                for (int k = 0; k < 16; ++k) run[cc][k] = 0;
+                for (int k = 0; k < 8; ++k) run[g][k] = 0;
             for (int ch = 0; ch < nch; ++ch, ++it) {
                 if (!(ok = mbar_wait(&acc_full, (uint32_t)(it & 1), p.status, kStatusTimeout))) break;
                 tc_fence_after();
 #pragma unroll
-                for (int cc = 0; cc < 3; ++cc) {
-                    const uint32_t base = tmem + ((uint32_t)(32 * q) << 16) + 48 * h + 16 * cc;
-                    uint32_t v[3][16];
-                    tmem_ld16(base, v[0]);
-                    tmem_ld16(base + kAccStride, v[1]);
-                    tmem_ld16(base + 2 * kAccStride, v[2]);
-                    tmem_ld_wait();
-                    int i4[16];
+                for (int g = 0; g < kEriRuns; ++g) {
+                    const uint32_t base = tmem + ((uint32_t)(32 * q) << 16) + 8 * (kEriRuns * h + g);
+                    uint32_t v[kNumAcc][8];
 #pragma unroll
-                    for (int k = 0; k < 16; ++k) {
-                        run[cc][k] += acc_head<7>(v[0][k], v[1][k]);
-                        i4[k] = acc_int(v[2][k], 4);
-                    }
-                    tmem_ld16(base + 3 * kAccStride, v[0]);
-                    tmem_ld16(base + 4 * kAccStride, v[1]);
+                    for (int j = 0; j < kNumAcc; ++j) tmem_ld8(base + j * kAccStride, v[j]);
                     tmem_ld_wait();
 #pragma unroll
-                    for (int k = 0; k < 16; ++k) run[cc][k] += acc_tail<7>(i4[k], v[0][k], v[1][k]);
+                    for (int k = 0; k < 8; ++k)
+                        run[g][k] += acc_head<7>(v[0][k], v[1][k]) + acc_tail<7>(acc_int(v[2][k], 4), v[3][k], v[4][k]);
                 }
                 tc_fence_before();
                 __syncwarp();
@@ -522,33 +573,22 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
             if (r_local >= Mrows || c >= p.nv) continue;   // past the block or a pad row
             const int e_ac = p.lt_exp[(p.a0 * p.vp + r_local) / kG];
             const int rs = p.row_start[a - p.a0];
-            // Two runs of 8 columns per 16-column chunk; with vp % 8 == 0 each run lies in one b and
-            // starts at d % 8 == 0, so it is one 16-byte store per plane (pad columns come out zero).
+            // With vp % 8 == 0 each run of 8 columns lies in one b and starts at d % 8 == 0, so it is
+            // one 16-byte store per plane (pad columns come out zero).
 #pragma unroll
-            for (int cc = 0; cc < 3; ++cc) {
+            for (int g = 0; g < kEriRuns; ++g) {
+                const int col = qt * kEmuTileN + 8 * (kEriRuns * h + g);
+                const int b = p.b0 + col / p.vp, d = col % p.vp;
+                if (col >= Ncols || a > b) continue;
+                const int e_bd = p.lt_exp[(p.b0 * p.vp + col) / kG];
+                const int sh = p.f_tab[a * p.nv + b] - e_ac - e_bd + 49 - 7 * S;
+                __align__(16) __nv_bfloat162 out[S][4];
+                slice_run<S>(run[g], sh, out, p.status);
+                const size_t off = (size_t)(rs + (b - max(a, p.b0))) * p.kpad + (size_t)c * p.vp + d;
 #pragma unroll
-                for (int half = 0; half < 2; ++half) {
-                    const int col = qt * kEmuTileN + 48 * h + 16 * cc + 8 * half;
-                    const int b = p.b0 + col / p.vp, d = col % p.vp;
-                    if (col >= Ncols || a > b) continue;
-                    const int e_bd = p.lt_exp[(p.b0 * p.vp + col) / kG];
-                    const int sh = p.f_tab[a * p.nv + b] - e_ac - e_bd + 49 - 7 * S;
-                    __align__(16) __nv_bfloat162 out[S][4];
-#pragma unroll
-                    for (int k = 0; k < 8; k += 2) {
-                        float d0[S], d1[S];
-                        digits_f32<S>(rescale(run[cc][8 * half + k], sh, 1LL << (7 * S - 1), p.status), d0);
-                        digits_f32<S>(rescale(run[cc][8 * half + k + 1], sh, 1LL << (7 * S - 1), p.status), d1);
-#pragma unroll
-                        for (int s2 = 0; s2 < S; ++s2)
-                            out[s2][k >> 1] = __floats2bfloat162_rn(d0[s2] * pow2f(-7 * (s2 + 1)), d1[s2] * pow2f(-7 * (s2 + 1)));
-                    }
-                    const size_t off = (size_t)(rs + (b - max(a, p.b0))) * p.kpad + (size_t)c * p.vp + d;
-#pragma unroll
-                    for (int s2 = 0; s2 < S; ++s2)
-                        *reinterpret_cast<uint4*>(p.vplanes + s2 * p.plane_stride + off) =
-                            *reinterpret_cast<const uint4*>(out[s2]);
-                }
+                for (int s2 = 0; s2 < S; ++s2)  // streaming stores: V is read back only by the ladder
+                    __stcs(reinterpret_cast<uint4*>(p.vplanes + s2 * p.plane_stride + off),
+                           *reinterpret_cast<const uint4*>(out[s2]));
             }
         }
         failed = !ok;
@@ -664,8 +704,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1) ladder_emu_kernel(const __grid_
     const long long u0 = p.units * blockIdx.x / gridDim.x, u1 = p.units * (blockIdx.x + 1) / gridDim.x;
 
     if (warp == 0 && lane == 0) {
+        // T slices (A) are re-read for every pair tile and stay in L2; the V planes (B) stream.
         Ring ring;
         int issued[STAGES] = {};
+        const uint64_t keep = policy_evict_last(), stream = policy_evict_first();
         bool ok = true;
         const uint32_t bytes = (uint32_t)S * (kEmuTile + p.BN) * BK * 2;
         for (long long u = u0; u < u1 && ok; ++u) {
@@ -677,8 +719,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1) ladder_emu_kernel(const __grid_
                 if (!(ok = mbar_wait(&empty[ring.stage], ring.phase ^ 1u, p.status, kStatusTimeout))) break;
                 unsigned char* st = smem + ring.stage * stage_bytes(S);
                 mbar_arrive_expect_tx(&full[ring.stage], bytes);
-                tma_load_3d(st, &tm_a, &full[ring.stage], kb * BK, mt * kEmuTile, 0);
-                tma_load_3d(st + S * APLANE, &tm_b, &full[ring.stage], kb * BK, nt * p.BN, 0);
+                tma_load_3d_hint(st, &tm_a, &full[ring.stage], kb * BK, mt * kEmuTile, 0, keep);
+                tma_load_3d_hint(st + S * APLANE, &tm_b, &full[ring.stage], kb * BK, nt * p.BN, 0, stream);
                 ++issued[ring.stage];
                 ring.next(STAGES);
             }
@@ -731,7 +773,6 @@ __global__ void __launch_bounds__(kThreadsTC, 1) ladder_emu_kernel(const __grid_
                     tmem_ld16(base + kAccStride, v[1]);
                     tmem_ld16(base + 2 * kAccStride, v[2]);
                     tmem_ld_wait();
-#pragma unroll
                     int i4[16];
 #pragma unroll
                     for (int k = 0; k < 16; ++k) {
@@ -817,8 +858,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
     bool failed = false;
 
     if (warp == 0 && lane == 0) {
+        // T slices (A) are re-read for every pair tile and stay in L2; the V planes (B) stream.
         Ring ring;
         bool ok = true;
+        const uint64_t keep = policy_evict_last(), stream = policy_evict_first();
         for (long long u = u0; u < u1 && ok; ++u) {
             const int ch = (int)(u % p.n_ch);
             const long long tile = u / p.n_ch;
@@ -831,8 +874,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
                 unsigned char* st = smem + ring.stage * eri_stage_bytes(S);
                 if (rank == 0) mbar_arrive_expect_tx(&full[ring.stage], 2 * eri_stage_bytes(S));
                 const uint32_t fb = mapa_rank(smem_u32(&full[ring.stage]), 0);
-                tma_load_3d_2sm(st, &tm_a, fb, kb * BK, arow, 0);
-                tma_load_3d_2sm(st + ABYTES, &tm_b, fb, kb * BK, brow, 0);
+                tma_load_3d_2sm_hint(st, &tm_a, fb, kb * BK, arow, 0, keep);
+                tma_load_3d_2sm_hint(st + ABYTES, &tm_b, fb, kb * BK, brow, 0, stream);
                 ring.next(STAGES);
             }
         }
@@ -881,7 +924,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
                 tmem_ld16(base + kAccStride, v[1]);
                 tmem_ld16(base + 2 * kAccStride, v[2]);
                 tmem_ld_wait();
-#pragma unroll
                 int i4[16];
 #pragma unroll
                 for (int k = 0; k < 16; ++k) {
@@ -1040,7 +1082,7 @@ cudaError_t block_impl(const ladder_plan_s& p, const BlockPair& bp, double* R, v
     {
         LaunchTimer tm(p, s, LADDER_KERNEL_ERI, 2);
         const int clusters = std::max(1, std::min(bp.ntiles, p.num_sms / 2));
-        eri_emu_kernel<S><<<2 * clusters, kThreadsTC, eri_smem_bytes_for(S), s>>>(tm_la, tm_lb, ea);
+        eri_emu_kernel<S><<<2 * clusters, kThreadsEri, eri_smem_bytes_for(S), s>>>(tm_la, tm_lb, ea);
         const int ndiag = std::max(0, std::min(bp.a1, bp.b1) - std::max(bp.a0, bp.b0));
         const long long nself = (long long)bp.npairs + (long long)ndiag * p.nv;
         SelfArgs sa{p.nv, vp, kpad, bp.a0, bp.a1, bp.b0, bp.b1, bp.npairs, vplane, table + bp.pairs_off, row_start,
