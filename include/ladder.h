@@ -97,6 +97,33 @@ int ladder_plan(ladder_plan_t* out, int no, int nv, int nchol, int precision, in
 int ladder_plan_set_blocks(ladder_plan_t plan, int n_a, int n_b);
 
 /*
+ * Data-parallel sharding over several GPUs (the multi-GPU direction named in
+ * Sec. "Conclusions and outlook"; the sharding itself is this library's).
+ * The (A,B) block pairs of one contraction are independent: each writes the
+ * entries R_ij^ab of its own pairs a <= b and their mirrors R_ji^ba, which no
+ * other block pair touches, so ranks that each run a share of the block pairs
+ * on their own GPU produce disjoint parts of R with no exchange, and E_L (linear
+ * in R) is the sum of the ranks' ladder_energy values (one scalar all-reduce).
+ *
+ * ladder_shard_blocks -- host only: owner[k] in [0, world) for each of n_blocks
+ *   block pairs with pair counts npairs[k]: largest first (ties by position),
+ *   each to the least-loaded rank (ties: lower rank).  LADDER_ERR_ARG for
+ *   world < 1, n_blocks < 0 or NULL arrays.
+ *
+ * ladder_plan_shard -- restrict `plan` to the block pairs that rank `rank` of
+ *   `world` owns.  If the plan has fewer than 2*world block pairs (and the
+ *   shape allows more) the planner first re-selects the blocking under the same
+ *   budget with at least that many.  All ranks must build their plans with the
+ *   same shape, precision, slices and an explicit equal ws_budget_bytes, so that
+ *   they see the same blocking.  The workspace size may shrink (query it again).
+ *   A rank may own no block pair; its ladder_apply then leaves R unchanged.
+ *   Call once per plan (a second call, or ladder_plan_set_blocks afterwards,
+ *   returns LADDER_ERR_ARG); world == 1 is a no-op.  Not for batched plans.
+ */
+int ladder_shard_blocks(int n_blocks, const long long* npairs, int world, int* owner);
+int ladder_plan_shard(ladder_plan_t plan, int rank, int world);
+
+/*
  * ladder_plan_dry -- run the planner on the host only (no CUDA call), for
  * inspection and tests.  Same meaning of no, nv, nchol, precision, nslices as
  * ladder_plan; ws_budget_bytes must be > 0 and num_sms >= 1 (the SM count the

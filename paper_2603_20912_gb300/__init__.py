@@ -59,6 +59,10 @@ def _load():
     pint = ctypes.POINTER(ci)
     lib.ladder_plan.argtypes = [ctypes.POINTER(vp), ci, ci, ci, ci, ci, sz, ci]
     lib.ladder_plan.restype = ci
+    lib.ladder_plan_shard.argtypes = [vp, ci, ci]
+    lib.ladder_plan_shard.restype = ci
+    lib.ladder_shard_blocks.argtypes = [ci, ctypes.POINTER(ctypes.c_longlong), ci, pint]
+    lib.ladder_shard_blocks.restype = ci
     lib.ladder_plan_set_blocks.argtypes = [vp, ci, ci]
     lib.ladder_plan_set_blocks.restype = ci
     lib.ladder_workspace_bytes.argtypes = [vp]
@@ -162,6 +166,10 @@ class Plan:
     def set_blocks(self, n_a: int, n_b: int):
         _check(_load().ladder_plan_set_blocks(self._h, int(n_a), int(n_b)), "ladder_plan_set_blocks")
 
+    def shard(self, rank: int, world: int):
+        """Keep only the block pairs rank `rank` of `world` owns (see ladder_plan_shard)."""
+        _check(_load().ladder_plan_shard(self._h, int(rank), int(world)), "ladder_plan_shard")
+
     def set_timing(self, enable: bool):
         _check(_load().ladder_plan_set_timing(self._h, int(bool(enable))), "ladder_plan_set_timing")
 
@@ -234,6 +242,20 @@ def ladder_plan_dry(no, nv, nchol, precision=LADDER_FP64, nslices=0, ws_budget_b
     return {"n_a": na.value, "n_b": nb.value, "ws_bytes": ws.value, "n_block_pairs": nbp.value, "blocks": blocks}
 
 
+def ladder_shard_blocks(npairs, world: int):
+    """Owner rank of each block pair (pair counts `npairs`) when spread over `world` ranks."""
+    n = len(npairs)
+    arr = (ctypes.c_longlong * max(n, 1))(*map(int, npairs))
+    owner = (ctypes.c_int * max(n, 1))()
+    _check(_load().ladder_shard_blocks(n, arr, int(world), owner), "ladder_shard_blocks")
+    return list(owner[:n])
+
+
+def ladder_plan_shard(plan: Plan, rank: int, world: int) -> Plan:
+    plan.shard(rank, world)
+    return plan
+
+
 def ladder_plan_batched(no, nv, nchol, precision=LADDER_EMU_BF16, nslices=0, ws_budget_bytes=0, device=0) -> Plan:
     n = len(no)
     arr = ctypes.c_int * n
@@ -299,5 +321,5 @@ EXPORTED_SYMBOLS = [
     "ladder_plan", "ladder_plan_set_blocks", "ladder_workspace_bytes", "ladder_plan_describe", "ladder_apply",
     "ladder_energy", "ladder_plan_batched", "ladder_apply_batched", "ladder_last_status", "ladder_plan_destroy",
     "ladder_strerror", "ladder_flops", "ladder_plan_dry", "ladder_plan_set_timing", "ladder_plan_timing",
-    "ladder_energy_noalloc", "ladder_tune_batched",
+    "ladder_energy_noalloc", "ladder_tune_batched", "ladder_plan_shard", "ladder_shard_blocks",
 ]

@@ -235,7 +235,24 @@ int apply_blocking(ladder_plan_s& p, int na, int nb) {
     return build_tables(p);
 }
 
-int select_blocking(const ladder_plan_s& p, int* out_na, int* out_nb) {
+// Owner of each block pair when the pairs are spread over `world` ranks: largest pair
+// count first (ties by position), each to the least-loaded rank (ties: the lower rank).
+// Pure host arithmetic, so every rank computes the same partition.
+std::vector<int> shard_owner(const std::vector<long long>& npairs, int world) {
+    const int n = (int)npairs.size();
+    std::vector<int> order(n), owner(n, 0);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return npairs[x] > npairs[y]; });
+    std::vector<long long> load(world, 0);
+    for (int i : order) {
+        const int r = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        owner[i] = r;
+        load[r] += npairs[i];
+    }
+    return owner;
+}
+
+int select_blocking(const ladder_plan_s& p, int* out_na, int* out_nb, int min_block_pairs = 1) {
     std::vector<int> cand;
     for (int k = 1; k <= p.nv; ++k) {
         const int n = (p.nv + k - 1) / k;
@@ -252,6 +269,7 @@ int select_blocking(const ladder_plan_s& p, int* out_na, int* out_nb) {
     int bna = 0, bnb = 0, evaluated = 0;
     for (const Combo& c : combos) {
         std::vector<BlockPair> bps = enumerate_blocks(p.nv, c.na, c.nb);
+        if ((int)bps.size() < min_block_pairs) continue;
         if (layout_for(p, max_pairs_of(bps)).total > p.budget) continue;
         const double t = model_time(p, bps);
         if (t < best * (1 - 1e-9)) {
@@ -406,7 +424,7 @@ int ladder_plan(ladder_plan_t* out, int no, int nv, int nchol, int precision, in
 }
 
 int ladder_plan_set_blocks(ladder_plan_t plan, int n_a, int n_b) {
-    if (!plan || plan->batched) return LADDER_ERR_ARG;
+    if (!plan || plan->batched || plan->shard_world > 1) return LADDER_ERR_ARG;
     if (n_a < 1 || n_b < 1 || n_a > plan->nv || n_b > plan->nv) return LADDER_ERR_ARG;
     DeviceGuard guard(plan->device);
     if (!guard.ok) return LADDER_ERR_CUDA;
@@ -414,6 +432,45 @@ int ladder_plan_set_blocks(ladder_plan_t plan, int n_a, int n_b) {
     std::vector<BlockPair> bps = enumerate_blocks(plan->nv, n_a, n_b);
     if (layout_for(*plan, max_pairs_of(bps)).total > plan->budget) return LADDER_ERR_BUDGET;
     return apply_blocking(*plan, n_a, n_b);
+}
+
+int ladder_shard_blocks(int n_blocks, const long long* npairs, int world, int* owner) {
+    if (n_blocks < 0 || world < 1 || (n_blocks > 0 && (!npairs || !owner))) return LADDER_ERR_ARG;
+    const std::vector<int> o = shard_owner(std::vector<long long>(npairs, npairs + n_blocks), world);
+    for (int i = 0; i < n_blocks; ++i) owner[i] = o[i];
+    return LADDER_OK;
+}
+
+int ladder_plan_shard(ladder_plan_t plan, int rank, int world) {
+    if (!plan || plan->batched || world < 1 || rank < 0 || rank >= world) return LADDER_ERR_ARG;
+    if (plan->shard_world > 1) return LADDER_ERR_ARG;  // already a shard
+    if (world == 1) return LADDER_OK;
+    DeviceGuard guard(plan->device);
+    if (!guard.ok) return LADDER_ERR_CUDA;
+    // Enough block pairs to balance: at least two per rank where the shape allows it.
+    const long long most = (long long)plan->nv * (plan->nv + 1) / 2;
+    const int want = (int)std::min<long long>(2LL * world, most);
+    std::vector<BlockPair> bps = plan->bps;
+    int na = plan->n_a, nb = plan->n_b;
+    if ((int)bps.size() < want) {
+        const int rc = select_blocking(*plan, &na, &nb, want);
+        if (rc != LADDER_OK) return rc;
+        bps = enumerate_blocks(plan->nv, na, nb);
+    }
+    std::vector<long long> np;
+    for (auto& b : bps) np.push_back(b.npairs);
+    const std::vector<int> owner = shard_owner(np, world);
+    std::vector<BlockPair> mine;
+    for (size_t i = 0; i < bps.size(); ++i)
+        if (owner[i] == rank) mine.push_back(bps[i]);
+    plan->n_a = na;
+    plan->n_b = nb;
+    plan->bps = std::move(mine);
+    plan->max_pairs = (int)max_pairs_of(plan->bps);
+    plan->ws = layout_for(*plan, plan->max_pairs);
+    plan->shard_rank = rank;
+    plan->shard_world = world;
+    return build_tables(*plan);
 }
 
 size_t ladder_workspace_bytes(ladder_plan_t plan) {

@@ -64,6 +64,7 @@ struct ladder_plan_s {
     int num_sms = 0;
     size_t budget = 0;
     int n_a = 0, n_b = 0;
+    int shard_rank = 0, shard_world = 1;  // this plan holds shard `shard_rank` of `shard_world`
     std::vector<ladder::BlockPair> bps;
     int max_pairs = 0;
     ladder::WsLayout ws;
