@@ -56,6 +56,7 @@ constexpr int kThreadsTC = 32 * (2 + kEpiWarps);
 constexpr int kEriEpiWarps = 8;    // ERI epilogue warps (4 per TMEM lane quadrant)
 constexpr int kThreadsEri = 32 * (2 + kEriEpiWarps);
 constexpr int kEriRuns = kEmuTileN / (kEriEpiWarps / 4) / 8;  // runs of 8 columns per epilogue warp
+static_assert(kEriRuns % 2 == 0, "runs are stored in sector pairs");
 constexpr int kNumAcc = 5;         // exact levels 2, 3, 4, 5 and the shared levels >= 6
 constexpr int kTmemCols = 512;     // 5 accumulators x 96 columns, rounded up to a power of two
 constexpr int kAccStride = kEmuTileN;  // TMEM columns between accumulators
@@ -236,6 +237,13 @@ __device__ __forceinline__ void slice_run(const long long (&I)[8], int sh, __nv_
         for (int s = 0; s < S; ++s) out[s][k >> 1] = __floats2bfloat162_rn(f0[s], f1[s]);
     }
     if (bad) atomicOr(status, kStatusNumeric);
+}
+
+// One 32-byte streaming store (a whole L2 sector), 32-byte aligned address.
+__device__ __forceinline__ void st_cs_32B(void* ptr, const uint4& lo, const uint4& hi) {
+    asm volatile("st.global.cs.v8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(ptr), "r"(lo.x), "r"(lo.y), "r"(lo.z),
+                 "r"(lo.w), "r"(hi.x), "r"(hi.y), "r"(hi.z), "r"(hi.w)
+                 : "memory");
 }
 
 // ------------------------------------------------------------------ prep kernels
@@ -574,7 +582,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsEri, 1)
             const int e_ac = p.lt_exp[(p.a0 * p.vp + r_local) / kG];
             const int rs = p.row_start[a - p.a0];
             // With vp % 8 == 0 each run of 8 columns lies in one b and starts at d % 8 == 0, so it is
-            // one 16-byte store per plane (pad columns come out zero).
+            // one 16-byte store per plane (pad columns come out zero).  With vp % 16 == 0 the runs
+            // 2k, 2k+1 fill one 32-byte sector and go out as one store: partial sectors written
+            // back before their other half arrives cost DRAM read-modify-writes.
+            const bool sector_pairs = (p.vp & 15) == 0;
+            uint4 prev[S];
 #pragma unroll
             for (int g = 0; g < kEriRuns; ++g) {
                 const int col = qt * kEmuTileN + 8 * (kEriRuns * h + g);
@@ -585,10 +597,21 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsEri, 1)
                 __align__(16) __nv_bfloat162 out[S][4];
                 slice_run<S>(run[g], sh, out, p.status);
                 const size_t off = (size_t)(rs + (b - max(a, p.b0))) * p.kpad + (size_t)c * p.vp + d;
+                // streaming stores: V is read back only by the ladder
+                if (!sector_pairs) {
 #pragma unroll
-                for (int s2 = 0; s2 < S; ++s2)  // streaming stores: V is read back only by the ladder
-                    __stcs(reinterpret_cast<uint4*>(p.vplanes + s2 * p.plane_stride + off),
-                           *reinterpret_cast<const uint4*>(out[s2]));
+                    for (int s2 = 0; s2 < S; ++s2)
+                        __stcs(reinterpret_cast<uint4*>(p.vplanes + s2 * p.plane_stride + off),
+                               *reinterpret_cast<const uint4*>(out[s2]));
+                } else if ((g & 1) == 0) {  // runs 2k, 2k+1: same b, both valid or both skipped
+#pragma unroll
+                    for (int s2 = 0; s2 < S; ++s2) prev[s2] = *reinterpret_cast<const uint4*>(out[s2]);
+                } else {
+#pragma unroll
+                    for (int s2 = 0; s2 < S; ++s2)
+                        st_cs_32B(p.vplanes + s2 * p.plane_stride + off - 8, prev[s2],
+                                  *reinterpret_cast<const uint4*>(out[s2]));
+                }
             }
         }
         failed = !ok;

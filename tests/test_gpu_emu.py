@@ -61,6 +61,22 @@ def test_c1_matches_cpu_model_of_the_scheme():
     assert rel_fro(R[:, :, iu[0], iu[1]], model[:, :, iu[0], iu[1]]) <= 1e-13
 
 
+@pytest.mark.parametrize("no,nv,nchol", [(3, 32, 50), (2, 47, 40), (4, 80, 33)])
+def test_sector_paired_layouts_match_the_model(no, nv, nchol):
+    # nv rounded up to 8 is a multiple of 16 here: the ERI epilogue stores V in whole
+    # 32-byte sectors.  Same digits as the model, and blocking-independent bit for bit.
+    # With K = nv^2 near a full 1024 chunk the FP32 accumulator of the levels >= 6 is no
+    # longer exact (the model keeps it in FP64); modelling it as FP32 with truncation moves
+    # the result by ~2e-13 here, so the bound is 2e-12 (a wrong digit plane gives >= 1e-9).
+    L, t2, _, _ = make_inputs(no, nv, nchol, seed=nv)
+    R, _ = gpu_ladder(L, t2, EMU)
+    model = emulated_ladder(L, t2, S=6)
+    iu = np.triu_indices(nv)
+    assert rel_fro(R[:, :, iu[0], iu[1]], model[:, :, iu[0], iu[1]]) <= 2e-12
+    Rb, _ = gpu_ladder(L, t2, EMU, blocks=(5, 3))
+    assert np.array_equal(Rb, R)
+
+
 @pytest.mark.parametrize("S,tol", [(5, 1e-8), (6, 1e-10), (7, 1e-11), (8, 5e-12)])
 def test_slice_count_controls_the_error(S, tol):
     s = CONFIGS["c1"]
