@@ -550,8 +550,30 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsEri, 1)
         long long run[kEriRuns][8];
         int it = 0;
         bool ok = true;
+        // With vp >= 48 the warp's 48 columns touch at most two b and two exponent groups, so
+        // the exponent tables of a tile come down to six loads per thread, issued before the
+        // accumulators are waited for so that their latency hides behind the MMAs.
+        const bool few_tables = p.vp >= 8 * kEriRuns;
         for (int e = cluster; e < p.nentries && ok; e += nclusters) {
             const int4 en = p.entries[e];
+            const int qt = en.y;
+            const int r_local = en.x * (2 * kEmuTile) + kEmuTile * (int)rank + 32 * q + lane;
+            const int a = p.a0 + r_local / p.vp, c = r_local % p.vp;
+            const bool row_ok = r_local < Mrows && c < p.nv;
+            const int col0 = qt * kEmuTileN + 8 * kEriRuns * h;            // first column of the warp
+            const int colz = min(col0 + 8 * (kEriRuns - 1), Ncols - 1);   // last valid run start
+            const int bq0 = col0 / p.vp, gq0 = (p.b0 * p.vp + col0) / kG;
+            int e_ac = 0, rs = 0, f0 = 0, f1 = 0, x0 = 0, x1 = 0;
+            if (row_ok) {
+                e_ac = p.lt_exp[(p.a0 * p.vp + r_local) / kG];
+                rs = p.row_start[a - p.a0];
+                if (few_tables && col0 < Ncols) {
+                    f0 = p.f_tab[a * p.nv + p.b0 + bq0];
+                    f1 = p.f_tab[a * p.nv + p.b0 + colz / p.vp];
+                    x0 = p.lt_exp[gq0];
+                    x1 = p.lt_exp[(p.b0 * p.vp + colz) / kG];
+                }
+            }
 #pragma unroll
             for (int g = 0; g < kEriRuns; ++g)
 #pragma unroll
@@ -575,12 +597,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsEri, 1)
                 if (lane == 0) mbar_arrive_remote(acc_empty_leader);
             }
             if (!ok) break;
-            const int qt = en.y;
-            const int r_local = en.x * (2 * kEmuTile) + kEmuTile * (int)rank + 32 * q + lane;
-            const int a = p.a0 + r_local / p.vp, c = r_local % p.vp;
-            if (r_local >= Mrows || c >= p.nv) continue;   // past the block or a pad row
-            const int e_ac = p.lt_exp[(p.a0 * p.vp + r_local) / kG];
-            const int rs = p.row_start[a - p.a0];
+            if (!row_ok) continue;   // past the block or a pad row
             // With vp % 8 == 0 each run of 8 columns lies in one b and starts at d % 8 == 0, so it is
             // one 16-byte store per plane (pad columns come out zero).  With vp % 16 == 0 the runs
             // 2k, 2k+1 fill one 32-byte sector and go out as one store: partial sectors written
@@ -589,11 +606,18 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsEri, 1)
             uint4 prev[S];
 #pragma unroll
             for (int g = 0; g < kEriRuns; ++g) {
-                const int col = qt * kEmuTileN + 8 * (kEriRuns * h + g);
-                const int b = p.b0 + col / p.vp, d = col % p.vp;
+                const int col = col0 + 8 * g;
+                const int bq = col / p.vp, b = p.b0 + bq, d = col - bq * p.vp;
                 if (col >= Ncols || a > b) continue;
-                const int e_bd = p.lt_exp[(p.b0 * p.vp + col) / kG];
-                const int sh = p.f_tab[a * p.nv + b] - e_ac - e_bd + 49 - 7 * S;
+                int f_ab, e_bd;
+                if (few_tables) {
+                    f_ab = bq == bq0 ? f0 : f1;
+                    e_bd = (p.b0 * p.vp + col) / kG == gq0 ? x0 : x1;
+                } else {
+                    f_ab = p.f_tab[a * p.nv + b];
+                    e_bd = p.lt_exp[(p.b0 * p.vp + col) / kG];
+                }
+                const int sh = f_ab - e_ac - e_bd + 49 - 7 * S;
                 __align__(16) __nv_bfloat162 out[S][4];
                 slice_run<S>(run[g], sh, out, p.status);
                 const size_t off = (size_t)(rs + (b - max(a, p.b0))) * p.kpad + (size_t)c * p.vp + d;
