@@ -371,9 +371,13 @@ int make_plan(ladder_plan_s** out, int no, int nv, int nchol, int precision, int
         budget = (size_t)((double)free_b * 0.98 * 0.9);
     }
     p->budget = budget;
-    if (precision != LADDER_FP64 && ladder::emu_set_attributes(nslices) != cudaSuccess) {
-        destroy_plan(p);
-        return LADDER_ERR_CUDA;
+    if (precision != LADDER_FP64) {
+        if (ladder::emu_set_attributes(nslices) != cudaSuccess) {
+            destroy_plan(p);
+            return LADDER_ERR_CUDA;
+        }
+        p->eri_clusters = ladder::emu_max_clusters(nslices, 0);
+        p->pair_clusters = ladder::emu_max_clusters(nslices, 1);
     }
     int rc = choose_blocking(*p);
     if (rc == LADDER_OK) {

@@ -1128,7 +1128,10 @@ cudaError_t block_impl(const ladder_plan_s& p, const BlockPair& bp, double* R, v
                at<int>(ws, p.ws.v_exp), at<__nv_bfloat16>(ws, p.ws.v_blk), p.d_status};
     {
         LaunchTimer tm(p, s, LADDER_KERNEL_ERI, 2);
-        const int clusters = std::max(1, std::min(bp.ntiles, p.num_sms / 2));
+        // persistent: no more clusters than fit at once (a cluster that waits for a free slot
+        // would process its share of the tiles after all the others)
+        const int fit = p.eri_clusters > 0 ? p.eri_clusters : p.num_sms / 2;
+        const int clusters = std::max(1, std::min(bp.ntiles, fit));
         eri_emu_kernel<S><<<2 * clusters, kThreadsEri, eri_smem_bytes_for(S), s>>>(tm_la, tm_lb, ea);
         const int ndiag = std::max(0, std::min(bp.a1, bp.b1) - std::max(bp.a0, bp.b0));
         const long long nself = (long long)bp.npairs + (long long)ndiag * p.nv;
@@ -1164,7 +1167,8 @@ cudaError_t block_impl(const ladder_plan_s& p, const BlockPair& bp, double* R, v
     {
         LaunchTimer tm(p, s, LADDER_KERNEL_LADDER);
         if (pair) {
-            const long long clusters = std::max<long long>(1, std::min<long long>(la.units, p.num_sms / 2));
+            const int fit = p.pair_clusters > 0 ? p.pair_clusters : p.num_sms / 2;
+            const long long clusters = std::max<long long>(1, std::min<long long>(la.units, fit));
             ladder_pair_kernel<S><<<(unsigned)(2 * clusters), kThreadsTC, eri_smem_bytes_for(S), s>>>(tm_t, tm_v, la);
         } else {
             ladder_emu_kernel<S><<<(unsigned)std::max<long long>(1, std::min<long long>(la.units, p.num_sms)),
@@ -1194,6 +1198,32 @@ cudaError_t set_attributes() {
         e = cudaFuncSetAttribute(ladder_pair_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  eri_smem_bytes_for(S));
     return e;
+}
+
+template <int S>
+int max_clusters_impl(int kind) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2, 1, 1);
+    cfg.blockDim = dim3(kind == 0 ? kThreadsEri : kThreadsTC, 1, 1);
+    cfg.dynamicSmemBytes = eri_smem_bytes_for(S);
+    int n = 0;
+    const cudaError_t e = kind == 0 ? cudaOccupancyMaxActiveClusters(&n, (void*)eri_emu_kernel<S>, &cfg)
+                                    : cudaOccupancyMaxActiveClusters(&n, (void*)ladder_pair_kernel<S>, &cfg);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+int emu_max_clusters(int nslices, int kind) {
+    switch (nslices) {
+        case 5: return max_clusters_impl<5>(kind);
+        case 6: return max_clusters_impl<6>(kind);
+        case 7: return max_clusters_impl<7>(kind);
+        case 8: return max_clusters_impl<8>(kind);
+        default: return 0;
+    }
 }
 
 bool emu_supported(int no, int nv, int nchol, int nslices) {

@@ -62,6 +62,8 @@ struct ladder_plan_s {
     int nslices = ladder::kDefaultSlices;
     int device = 0;
     int num_sms = 0;
+    int eri_clusters = 0;   // emulated ERI: CTA pairs that fit on the device at once
+    int pair_clusters = 0;  // emulated ladder on CTA pairs: CTA pairs that fit at once
     size_t budget = 0;
     int n_a = 0, n_b = 0;
     int shard_rank = 0, shard_world = 1;  // this plan holds shard `shard_rank` of `shard_world`
@@ -131,5 +133,8 @@ cudaError_t launch_emu_block(const ladder_plan_s& p, const BlockPair& bp, double
                              cudaStream_t s);
 bool emu_supported(int no, int nv, int nchol, int nslices);
 cudaError_t emu_set_attributes(int nslices);  // per device, before the first launch
+// Co-resident clusters of the emulated CTA-pair kernels on the current device: kind 0 = ERI,
+// kind 1 = ladder on CTA pairs.  0 if the query fails.
+int emu_max_clusters(int nslices, int kind);
 
 }  // namespace ladder
