@@ -63,14 +63,24 @@ constexpr int kAccStride = kEmuTileN;  // TMEM columns between accumulators
 constexpr int kSmemBudget = 210 * 1024;
 
 __host__ __device__ constexpr int bk_for(int S) { return S <= 6 ? 32 : 16; }
+// ERI stage width (K columns per pipeline stage) and the most stages it keeps in flight.
+constexpr int kEriBK = 32;
+constexpr int kEriMaxStages = 4;
+__host__ __device__ constexpr int eri_bk_for(int S) { return S <= 6 ? kEriBK : 16; }
 // One stage: S planes of a 128-row tile (A) and S planes of a <= 96-row tile (B), BK columns.
 __host__ __device__ constexpr int stage_bytes(int S) { return S * (kEmuTile + kEmuTileN) * bk_for(S) * 2; }
 // ERI stage on a CTA pair: 128 rows of A and half (48 rows) of the 96-row B tile per CTA.
-__host__ __device__ constexpr int eri_stage_bytes(int S) { return S * (kEmuTile + kEmuTileN / 2) * bk_for(S) * 2; }
+__host__ __device__ constexpr int eri_stage_bytes(int S) { return S * (kEmuTile + kEmuTileN / 2) * eri_bk_for(S) * 2; }
 __host__ __device__ constexpr int eri_stages_for(int S) {
-    return kSmemBudget / eri_stage_bytes(S) < 4 ? kSmemBudget / eri_stage_bytes(S) : 4;
+    return kSmemBudget / eri_stage_bytes(S) < kEriMaxStages ? kSmemBudget / eri_stage_bytes(S) : kEriMaxStages;
 }
 __host__ __device__ constexpr int eri_smem_bytes_for(int S) { return eri_stages_for(S) * eri_stage_bytes(S) + 1024; }
+// Ladder on CTA pairs: the same per-CTA stage shape with the ladder's stage width.
+__host__ __device__ constexpr int pair_stage_bytes(int S) { return S * (kEmuTile + kEmuTileN / 2) * bk_for(S) * 2; }
+__host__ __device__ constexpr int pair_stages_for(int S) {
+    return kSmemBudget / pair_stage_bytes(S) < 4 ? kSmemBudget / pair_stage_bytes(S) : 4;
+}
+__host__ __device__ constexpr int pair_smem_bytes_for(int S) { return pair_stages_for(S) * pair_stage_bytes(S) + 1024; }
 __host__ __device__ constexpr int stages_for(int S) {
     return kSmemBudget / stage_bytes(S) < 4 ? kSmemBudget / stage_bytes(S) : 4;
 }
@@ -396,10 +406,9 @@ struct Ring {
 // Issue the S(S+1)/2 slice-pair MMAs of one stage (BK / 16 K-steps) into the 5 accumulators.
 // The shared-memory descriptors are built once per stage; each MMA only adds the plane
 // and K-step offset (in 16-byte units) to the start-address field.
-template <int S, bool PAIR = false>
+template <int S, bool PAIR = false, int BK = bk_for(S)>
 __device__ __forceinline__ void issue_pairs(uint32_t tmem, uint32_t sA, uint32_t sB, uint32_t a_plane_bytes,
                                             uint32_t b_plane_bytes, uint32_t idesc, bool (&first)[kNumAcc]) {
-    constexpr int BK = bk_for(S);
     const uint64_t da = smem_desc_kmajor(sA, BK * 2), db = smem_desc_kmajor(sB, BK * 2);
     const uint32_t ap = a_plane_bytes >> 4, bp = b_plane_bytes >> 4;
 #pragma unroll
@@ -461,7 +470,7 @@ struct EriArgs {
 template <int S>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsEri, 1)
     eri_emu_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ CUtensorMap tm_b, EriArgs p) {
-    constexpr int BK = bk_for(S), STAGES = eri_stages_for(S);
+    constexpr int BK = eri_bk_for(S), STAGES = eri_stages_for(S);
     constexpr uint32_t APLANE = kEmuTile * BK * 2, BPLANE = (kEmuTileN / 2) * BK * 2;
     constexpr uint32_t ABYTES = S * APLANE;
     extern __shared__ unsigned char smem_raw[];
@@ -530,7 +539,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsEri, 1)
                     if (!(ok = mbar_wait(&full[ring.stage], ring.phase, p.status, kStatusTimeout))) break;
                     tc_fence_after();
                     const uint32_t st = smem_u32(smem + ring.stage * eri_stage_bytes(S));
-                    issue_pairs<S, true>(tmem, st, st + ABYTES, APLANE, BPLANE, idesc, first);
+                    issue_pairs<S, true, BK>(tmem, st, st + ABYTES, APLANE, BPLANE, idesc, first);
                     mma_commit_pair_mc(&empty[ring.stage], (uint16_t)0x3);
                     ring.next(STAGES);
                 }
@@ -874,7 +883,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) ladder_emu_kernel(const __grid_
 template <int S>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
     ladder_pair_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ CUtensorMap tm_b, LadArgs p) {
-    constexpr int BK = bk_for(S), STAGES = eri_stages_for(S);
+    constexpr int BK = bk_for(S), STAGES = pair_stages_for(S);
     constexpr uint32_t APLANE = kEmuTile * BK * 2, BPLANE = (kEmuTileN / 2) * BK * 2;
     constexpr uint32_t ABYTES = S * APLANE;
     extern __shared__ unsigned char smem_raw[];
@@ -918,8 +927,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
             const int kb1 = min((ch + 1) * p.kb_per_chunk, p.nkb);
             for (int kb = ch * p.kb_per_chunk; kb < kb1 && ok; ++kb) {
                 if (!(ok = mbar_wait(&empty[ring.stage], ring.phase ^ 1u, p.status, kStatusTimeout))) break;
-                unsigned char* st = smem + ring.stage * eri_stage_bytes(S);
-                if (rank == 0) mbar_arrive_expect_tx(&full[ring.stage], 2 * eri_stage_bytes(S));
+                unsigned char* st = smem + ring.stage * pair_stage_bytes(S);
+                if (rank == 0) mbar_arrive_expect_tx(&full[ring.stage], 2 * pair_stage_bytes(S));
                 const uint32_t fb = mapa_rank(smem_u32(&full[ring.stage]), 0);
                 tma_load_3d_2sm_hint(st, &tm_a, fb, kb * BK, arow, 0, keep);
                 tma_load_3d_2sm_hint(st + ABYTES, &tm_b, fb, kb * BK, brow, 0, stream);
@@ -941,7 +950,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
             for (int kb = ch * p.kb_per_chunk; kb < kb1 && ok; ++kb) {
                 if (!(ok = mbar_wait(&full[ring.stage], ring.phase, p.status, kStatusTimeout))) break;
                 tc_fence_after();
-                const uint32_t st = smem_u32(smem + ring.stage * eri_stage_bytes(S));
+                const uint32_t st = smem_u32(smem + ring.stage * pair_stage_bytes(S));
                 issue_pairs<S, true>(tmem, st, st + ABYTES, APLANE, BPLANE, idesc, first);
                 mma_commit_pair_mc(&empty[ring.stage], (uint16_t)0x3);
                 ring.next(STAGES);
@@ -1118,10 +1127,11 @@ cudaError_t block_impl(const ladder_plan_s& p, const BlockPair& bp, double* R, v
     const int2* table = reinterpret_cast<const int2*>(p.d_tables);
     const int* row_start = reinterpret_cast<const int*>(p.d_tables) + bp.rows_off;
     CUtensorMap tm_la, tm_lb, tm_v, tm_t;
+    constexpr int EBK = eri_bk_for(S);
     if (!make_tmap(&tm_la, at<char>(ws, p.ws.lt_slices), p.nchol, rows, S, (uint64_t)xpad * 2,
-                   (uint64_t)rows * xpad * 2, BK, kEmuTile) ||
+                   (uint64_t)rows * xpad * 2, EBK, kEmuTile) ||
         !make_tmap(&tm_lb, at<char>(ws, p.ws.lt_slices), p.nchol, rows, S, (uint64_t)xpad * 2,
-                   (uint64_t)rows * xpad * 2, BK, kEmuTileN / 2))
+                   (uint64_t)rows * xpad * 2, EBK, kEmuTileN / 2))
         return cudaErrorInvalidValue;
     EriArgs ea{p.nv, vp, p.nchol, bp.a0, bp.a1 - bp.a0, bp.b0, bp.b1 - bp.b0, kpad, bp.ntiles, vplane,
                reinterpret_cast<const int4*>(table + bp.tiles_off), row_start, at<int>(ws, p.ws.lt_exp),
@@ -1169,7 +1179,7 @@ cudaError_t block_impl(const ladder_plan_s& p, const BlockPair& bp, double* R, v
         if (pair) {
             const int fit = p.pair_clusters > 0 ? p.pair_clusters : p.num_sms / 2;
             const long long clusters = std::max<long long>(1, std::min<long long>(la.units, fit));
-            ladder_pair_kernel<S><<<(unsigned)(2 * clusters), kThreadsTC, eri_smem_bytes_for(S), s>>>(tm_t, tm_v, la);
+            ladder_pair_kernel<S><<<(unsigned)(2 * clusters), kThreadsTC, pair_smem_bytes_for(S), s>>>(tm_t, tm_v, la);
         } else {
             ladder_emu_kernel<S><<<(unsigned)std::max<long long>(1, std::min<long long>(la.units, p.num_sms)),
                                    kThreadsTC, smem, s>>>(tm_t, tm_v, la);
@@ -1196,7 +1206,7 @@ cudaError_t set_attributes() {
         e = cudaFuncSetAttribute(ladder_emu_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes_for(S));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(ladder_pair_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 eri_smem_bytes_for(S));
+                                 pair_smem_bytes_for(S));
     return e;
 }
 
@@ -1205,7 +1215,7 @@ int max_clusters_impl(int kind) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(2, 1, 1);
     cfg.blockDim = dim3(kind == 0 ? kThreadsEri : kThreadsTC, 1, 1);
-    cfg.dynamicSmemBytes = eri_smem_bytes_for(S);
+    cfg.dynamicSmemBytes = kind == 0 ? eri_smem_bytes_for(S) : pair_smem_bytes_for(S);
     int n = 0;
     const cudaError_t e = kind == 0 ? cudaOccupancyMaxActiveClusters(&n, (void*)eri_emu_kernel<S>, &cfg)
                                     : cudaOccupancyMaxActiveClusters(&n, (void*)ladder_pair_kernel<S>, &cfg);
