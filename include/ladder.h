@@ -137,6 +137,21 @@ int ladder_plan_dry(int no, int nv, int nchol, int precision, int nslices, size_
                     int force_n_a, int force_n_b, int* n_a, int* n_b, size_t* ws_bytes, int max_blocks,
                     int* n_block_pairs, int* blocks);
 
+/*
+ * ladder_watchdog_selftest -- check, on the current device, the bounded wait that every
+ * tcgen05 kernel of the library uses for its mbarriers (the watchdog that turns a lost
+ * producer into LADDER_ERR_TIMEOUT instead of a hang).  Launches one CTA on `stream` that
+ * waits on an mbarrier nothing arrives on, with that same wait (limit: 2 s of the GPU's
+ * global timer), then synchronises the stream.  Returns LADDER_ERR_TIMEOUT when the wait
+ * gave up and reported it through its status word -- the expected outcome -- and stores the
+ * time it waited in *waited_ms (may be NULL); LADDER_OK means the wait ended without the
+ * timeout being reported (a broken watchdog); LADDER_ERR_CUDA on a CUDA error.  Allocates and
+ * frees 16 bytes of device memory.  The paper's failure handling is a CUDA availability probe
+ * with a CPU fallback (Sec. "A Generic Interface for a Dynamic Switching Between CuPy,
+ * PyTorch, and CPU-only Libraries"); this library has no fallback and no counterpart there.
+ */
+int ladder_watchdog_selftest(double* waited_ms, cudaStream_t stream);
+
 /* Workspace bytes ladder_apply needs (device memory, 256-byte aligned start). */
 size_t ladder_workspace_bytes(ladder_plan_t plan);
 

@@ -59,6 +59,8 @@ def _load():
     pint = ctypes.POINTER(ci)
     lib.ladder_plan.argtypes = [ctypes.POINTER(vp), ci, ci, ci, ci, ci, sz, ci]
     lib.ladder_plan.restype = ci
+    lib.ladder_watchdog_selftest.argtypes = [ctypes.POINTER(ctypes.c_double), vp]
+    lib.ladder_watchdog_selftest.restype = ci
     lib.ladder_plan_shard.argtypes = [vp, ci, ci]
     lib.ladder_plan_shard.restype = ci
     lib.ladder_shard_blocks.argtypes = [ci, ctypes.POINTER(ctypes.c_longlong), ci, pint]
@@ -309,6 +311,13 @@ def ladder_energy_noalloc(t2, R, E_dev, stream=None):
     return E_dev
 
 
+def ladder_watchdog_selftest(stream=None):
+    """(status, waited_ms): status is LADDER_ERR_TIMEOUT when the bounded wait fired as designed."""
+    ms = ctypes.c_double()
+    rc = _load().ladder_watchdog_selftest(ctypes.byref(ms), _stream_handle(stream))
+    return int(rc), ms.value
+
+
 def ladder_last_status(plan: Plan, stream=None) -> int:
     return plan.last_status(stream)
 
@@ -322,4 +331,5 @@ EXPORTED_SYMBOLS = [
     "ladder_energy", "ladder_plan_batched", "ladder_apply_batched", "ladder_last_status", "ladder_plan_destroy",
     "ladder_strerror", "ladder_flops", "ladder_plan_dry", "ladder_plan_set_timing", "ladder_plan_timing",
     "ladder_energy_noalloc", "ladder_tune_batched", "ladder_plan_shard", "ladder_shard_blocks",
+    "ladder_watchdog_selftest",
 ]

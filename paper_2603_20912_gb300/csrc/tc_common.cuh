@@ -2,9 +2,10 @@
 // waits, TMA tensor loads, TMEM allocation, tcgen05.mma / commit / ld, and
 // the shared-memory and instruction descriptors of tcgen05 (kind::f16).
 //
-// Every wait here is bounded: after `kSpinLimit` polls it gives up, records
-// kStatusTimeout in the caller's status word and returns false, so a kernel
-// whose producer died still terminates and frees its TMEM.
+// Every wait here is bounded: after kWaitLimitNs of polling (read from the
+// global nanosecond timer) it gives up, records the caller's flag in its status
+// word and returns false, so a kernel whose producer died still terminates and
+// frees its TMEM.
 #pragma once
 
 #include <cstdint>
@@ -14,7 +15,13 @@
 namespace ladder {
 namespace tc {
 
-constexpr uint32_t kSpinLimit = 1u << 28;  // ~ seconds of polling before a wait is declared dead
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s of polling before a wait is declared dead
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -54,8 +61,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 
 // Bounded wait for the phase with the given parity to complete.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned* status, unsigned flag) {
-    for (uint32_t i = 0; i < kSpinLimit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t i = 1;; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 1023u) == 0 && global_ns() - t0 > kWaitLimitNs) break;
+    }
     if (status) atomicOr(status, flag);
     return false;
 }
