@@ -370,6 +370,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--device-inputs", action="store_true",
+                    help="draw L and t2 on the GPU (timing-only runs at large shapes)")
+    ap.add_argument("--budget-gb", type=float, default=0.0, help="workspace budget (0: 0.9*0.98*free)")
     ap.add_argument("--fp64-reference", action="store_true",
                     help="c5: also time 24 sequential native-FP64 calls (slow)")
     ap.add_argument("--measure-peaks", action="store_true",
@@ -399,13 +402,22 @@ def main():
     build.build()
     precision = lad.LADDER_EMU_BF16 if args.precision == "emu" else lad.LADDER_FP64
     # Each rank: its own independent instance (seed offset by rank).
-    L, t2, _, _ = make_inputs(cfg.no, cfg.nv, cfg.nchol, cfg.seed + 7919 * rank)
-    Lh = torch.from_numpy(L).pin_memory()
-    th = torch.from_numpy(t2).pin_memory()
-    Ld = Lh.to("cuda", non_blocking=True)
-    td = th.to("cuda", non_blocking=True)
+    if args.device_inputs:
+        # timing-only shapes: inputs drawn on the GPU, no host copies (no e2e, no CPU baseline)
+        from ladder_inputs import make_device_inputs
+        Ld, td = make_device_inputs(cfg.no, cfg.nv, cfg.nchol, cfg.seed + 7919 * rank, device=f"cuda:{local}")
+        args.no_e2e = args.no_cpu_baseline = True
+        L = t2 = Lh = th = None
+    else:
+        L, t2, _, _ = make_inputs(cfg.no, cfg.nv, cfg.nchol, cfg.seed + 7919 * rank)
+        Lh = torch.from_numpy(L).pin_memory()
+        th = torch.from_numpy(t2).pin_memory()
+        Ld = Lh.to("cuda", non_blocking=True)
+        td = th.to("cuda", non_blocking=True)
     R = torch.zeros_like(td)
-    plan = lad.ladder_plan(cfg.no, cfg.nv, cfg.nchol, precision, nslices=args.nslices, device=local)
+    torch.cuda.synchronize()
+    plan = lad.ladder_plan(cfg.no, cfg.nv, cfg.nchol, precision, nslices=args.nslices,
+                           ws_budget_bytes=int(args.budget_gb * 1e9), device=local)
     ws = plan.workspace()
     desc = plan.describe()
     stream = torch.cuda.current_stream()

@@ -106,6 +106,30 @@ def make_inputs(no: int, nv: int, nchol: int, seed: int, symmetric_t2: bool = Tr
     return (np.ascontiguousarray(L), np.ascontiguousarray(t2), eps_occ, eps_vir)
 
 
+def make_device_inputs(no: int, nv: int, nchol: int, seed: int, device="cuda"):
+    """(L, t2) as torch float64 tensors drawn on the GPU with the same distributions and
+    symmetries as ``make_inputs`` (torch's generator, so not the same numbers): for timing runs
+    at shapes whose host-side generation would take minutes.  Not used for parity."""
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    f64 = dict(dtype=torch.float64, device=device)
+    eps_occ = torch.empty(no, **f64).uniform_(-1.5, -0.3, generator=gen)
+    eps_vir = torch.empty(nv, **f64).uniform_(0.2, 3.0, generator=gen)
+    g = torch.randn((nchol, nv, nv), generator=gen, **f64)
+    L = torch.triu(g) + torch.triu(g, 1).transpose(1, 2)
+    del g
+    L *= torch.tensor(decay_factors(nchol), **f64)[:, None, None]
+    x = torch.randn((no, no, nv, nv), generator=gen, **f64)
+    x *= 0.01
+    t2 = (x + x.permute(1, 0, 3, 2)) / 2.0
+    del x
+    eab = eps_vir[:, None] + eps_vir[None, :]
+    eij = eps_occ[:, None] + eps_occ[None, :]
+    t2 /= (2.0 + eab)[None, None, :, :] - eij[:, :, None, None]
+    return L.contiguous(), t2.contiguous()
+
+
 def make_integer_inputs(no: int, nv: int, nchol: int, seed: int, lo: int = -3, hi: int = 3,
                         symmetric_L: bool = True, symmetric_t2: bool = True):
     """Integer-valued operands (entries in [lo, hi]) for exact-arithmetic checks."""
