@@ -106,39 +106,6 @@ __device__ __forceinline__ void digits_of(long long N, __nv_bfloat16 (&out)[S]) 
     out[0] = __float2bfloat16_rn(small_int_to_float((int)N) * pow2f(-7));
 }
 
-// Balanced base-128 digits of N (|N| <= 2^(7S-1)) as floats d_s (unscaled), taking the low 21
-// bits (three digits) in 32-bit arithmetic and the carry into the high part, also 32-bit for
-// S <= 7.  Same digits as digits_of.
-template <int S>
-__device__ __forceinline__ void digits_f32(long long N, float (&out)[S]) {
-    if constexpr (S <= 7) {
-        int lo = (int)(N & 0x1FFFFF);
-        int hi = (int)(N >> 21);
-#pragma unroll
-        for (int s = S - 1; s >= S - 3; --s) {
-            const int low = ((lo + 64) & 127) - 64;
-            lo = (lo - low) >> 7;
-            out[s] = small_int_to_float(low);
-        }
-        hi += lo;
-#pragma unroll
-        for (int s = S - 4; s >= 1; --s) {
-            const int low = ((hi + 64) & 127) - 64;
-            hi = (hi - low) >> 7;
-            out[s] = small_int_to_float(low);
-        }
-        out[0] = small_int_to_float(hi);
-    } else {
-#pragma unroll
-        for (int s = S - 1; s >= 1; --s) {
-            const int low = (int)(((N + 64) & 127)) - 64;
-            N = (N - low) >> 7;
-            out[s] = small_int_to_float(low);
-        }
-        out[0] = small_int_to_float((int)N);
-    }
-}
-
 // round(I / 2^sh) with halves rounded up (sh <= 0 multiplies); values beyond
 // +-lim cannot occur for a valid exponent bound and are clamped and flagged.
 __device__ __forceinline__ long long rescale(long long I, int sh, long long lim, unsigned* status) {
