@@ -415,14 +415,26 @@ __device__ __forceinline__ long long acc_tail(int i4, uint32_t b5, uint32_t b6) 
            __float2ll_rn(__uint_as_float(b6) * pow2f(7 * U));
 }
 
-struct EriArgs {
-    int nv, vp, nchol, a0, na, b0, nb, kpad, nentries;
+// Work of one ERI launch: up to kMaxItems items (an instance's block pair each), every one with
+// its own L^T tensor maps and tables, and one list of tiles over all of them, so a single
+// persistent launch covers several instances.
+constexpr int kMaxItems = 32;
+
+struct EriItem {
+    int nv, vp, nchol, a0, na, b0, nb, kpad;
     size_t plane_stride;  // elements between V planes
-    const int4* entries;  // (rt, qt for CTA rank 0 or -1, qt for CTA rank 1 or -1, 0)
     const int* row_start;
     const int* lt_exp;
     const int* f_tab;
     __nv_bfloat16* vplanes;
+};
+
+struct EriBatch {
+    CUtensorMap ta[kMaxItems];  // L^T slices, 128-row boxes (A)
+    CUtensorMap tb[kMaxItems];  // L^T slices, 48-row boxes (B)
+    EriItem item[kMaxItems];
+    const int4* entries;        // (row tile, column tile, item, 0)
+    int nentries, nitems;
     unsigned* status;
 };
 
@@ -436,7 +448,7 @@ struct EriArgs {
 // K = nchol runs in exact chunks of kEmuChunkK.
 template <int S>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsEri, 1)
-    eri_emu_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ CUtensorMap tm_b, EriArgs p) {
+    eri_emu_kernel(const __grid_constant__ EriBatch B) {
     constexpr int BK = eri_bk_for(S), STAGES = eri_stages_for(S);
     constexpr uint32_t APLANE = kEmuTile * BK * 2, BPLANE = (kEmuTileN / 2) * BK * 2;
     constexpr uint32_t ABYTES = S * APLANE;
@@ -456,17 +468,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsEri, 1)
         mbar_init(&acc_empty, 2 * kEriEpiWarps);
         mbar_init(&done, 1);
         fence_barrier_init();
-        tma_prefetch_desc(&tm_a);
-        tma_prefetch_desc(&tm_b);
+        for (int i = 0; i < B.nitems; ++i) {
+            tma_prefetch_desc(&B.ta[i]);
+            tma_prefetch_desc(&B.tb[i]);
+        }
     }
     if (warp == 1) tmem_alloc_pair(&tmem_base, kTmemCols);
     tc_fence_before();
     cluster_sync();
     tc_fence_after();
     const uint32_t tmem = tmem_base;
-    const int nkb = (p.nchol + BK - 1) / BK;
     const int kb_per_chunk = kEmuChunkK / BK;
-    const int nch = (nkb + kb_per_chunk - 1) / kb_per_chunk;
     bool failed = false;
 
     if (warp == 0 && lane == 0) {
@@ -475,17 +487,19 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsEri, 1)
         Ring ring;
         bool ok = true;
         const uint64_t keep = policy_evict_last();
-        for (int e = cluster; e < p.nentries && ok; e += nclusters) {
-            const int4 en = p.entries[e];
+        for (int e = cluster; e < B.nentries && ok; e += nclusters) {
+            const int4 en = B.entries[e];
+            const EriItem& p = B.item[en.z];
+            const int nkb = (p.nchol + BK - 1) / BK;
             const int arow = p.a0 * p.vp + en.x * (2 * kEmuTile) + kEmuTile * (int)rank;
             const int brow = p.b0 * p.vp + en.y * kEmuTileN + (kEmuTileN / 2) * (int)rank;
             for (int kb = 0; kb < nkb && ok; ++kb) {
-                if (!(ok = mbar_wait(&empty[ring.stage], ring.phase ^ 1u, p.status, kStatusTimeout))) break;
+                if (!(ok = mbar_wait(&empty[ring.stage], ring.phase ^ 1u, B.status, kStatusTimeout))) break;
                 unsigned char* st = smem + ring.stage * eri_stage_bytes(S);
                 if (rank == 0) mbar_arrive_expect_tx(&full[ring.stage], 2 * eri_stage_bytes(S));
                 const uint32_t fb = mapa_rank(smem_u32(&full[ring.stage]), 0);
-                tma_load_3d_2sm_hint(st, &tm_a, fb, kb * BK, arow, 0, keep);
-                tma_load_3d_2sm_hint(st + ABYTES, &tm_b, fb, kb * BK, brow, 0, keep);
+                tma_load_3d_2sm_hint(st, &B.ta[en.z], fb, kb * BK, arow, 0, keep);
+                tma_load_3d_2sm_hint(st + ABYTES, &B.tb[en.z], fb, kb * BK, brow, 0, keep);
                 ring.next(STAGES);
             }
         }
@@ -496,14 +510,16 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsEri, 1)
         const uint32_t idesc = idesc_bf16_f32(2 * kEmuTile, kEmuTileN);
         bool ok = true;
         int it = 0;
-        for (int e = cluster; e < p.nentries && ok; e += nclusters) {
+        for (int e = cluster; e < B.nentries && ok; e += nclusters) {
+            const int nkb = (B.item[B.entries[e].z].nchol + BK - 1) / BK;
+            const int nch = (nkb + kb_per_chunk - 1) / kb_per_chunk;
             for (int ch = 0; ch < nch && ok; ++ch, ++it) {
-                if (!(ok = mbar_wait(&acc_empty, (uint32_t)(it & 1) ^ 1u, p.status, kStatusTimeout))) break;
+                if (!(ok = mbar_wait(&acc_empty, (uint32_t)(it & 1) ^ 1u, B.status, kStatusTimeout))) break;
                 tc_fence_after();
                 bool first[kNumAcc] = {true, true, true, true, true};
                 const int kb1 = min((ch + 1) * kb_per_chunk, nkb);
                 for (int kb = ch * kb_per_chunk; kb < kb1 && ok; ++kb) {
-                    if (!(ok = mbar_wait(&full[ring.stage], ring.phase, p.status, kStatusTimeout))) break;
+                    if (!(ok = mbar_wait(&full[ring.stage], ring.phase, B.status, kStatusTimeout))) break;
                     tc_fence_after();
                     const uint32_t st = smem_u32(smem + ring.stage * eri_stage_bytes(S));
                     issue_pairs<S, true, BK>(tmem, st, st + ABYTES, APLANE, BPLANE, idesc, first);
@@ -521,7 +537,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsEri, 1)
         // columns.  Several warps per quadrant keep enough independent work in flight to re-slice
         // a tile while the MMAs of the next one run.
         const int q = warp & 3, h = (warp - 2) >> 2;
-        const int Mrows = p.na * p.vp, Ncols = p.nb * p.vp;
         const uint32_t acc_empty_leader = mapa_rank(smem_u32(&acc_empty), 0);
         long long run[kEriRuns][8];
         int it = 0;
@@ -529,9 +544,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsEri, 1)
         // With vp >= 48 the warp's 48 columns touch at most two b and two exponent groups, so
         // the exponent tables of a tile come down to six loads per thread, issued before the
         // accumulators are waited for so that their latency hides behind the MMAs.
-        const bool few_tables = p.vp >= 8 * kEriRuns;
-        for (int e = cluster; e < p.nentries && ok; e += nclusters) {
-            const int4 en = p.entries[e];
+        for (int e = cluster; e < B.nentries && ok; e += nclusters) {
+            const int4 en = B.entries[e];
+            const EriItem& p = B.item[en.z];
+            const int Mrows = p.na * p.vp, Ncols = p.nb * p.vp;
+            const bool few_tables = p.vp >= 8 * kEriRuns;
+            const int nkb = (p.nchol + BK - 1) / BK;
+            const int nch = (nkb + kb_per_chunk - 1) / kb_per_chunk;
             const int qt = en.y;
             const int r_local = en.x * (2 * kEmuTile) + kEmuTile * (int)rank + 32 * q + lane;
             const int a = p.a0 + r_local / p.vp, c = r_local % p.vp;
@@ -555,7 +574,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsEri, 1)
 #pragma unroll
                 for (int k = 0; k < 8; ++k) run[g][k] = 0;
             for (int ch = 0; ch < nch; ++ch, ++it) {
-                if (!(ok = mbar_wait(&acc_full, (uint32_t)(it & 1), p.status, kStatusTimeout))) break;
+                if (!(ok = mbar_wait(&acc_full, (uint32_t)(it & 1), B.status, kStatusTimeout))) break;
                 tc_fence_after();
 #pragma unroll
                 for (int g = 0; g < kEriRuns; ++g) {
@@ -595,7 +614,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsEri, 1)
                 }
                 const int sh = f_ab - e_ac - e_bd + 49 - 7 * S;
                 __align__(16) __nv_bfloat162 out[S][4];
-                slice_run<S>(run[g], sh, out, p.status);
+                slice_run<S>(run[g], sh, out, B.status);
                 const size_t off = (size_t)(rs + (b - max(a, p.b0))) * p.kpad + (size_t)c * p.vp + d;
                 // streaming stores: V is read back only by the ladder
                 if (!sector_pairs) {
@@ -617,7 +636,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsEri, 1)
         failed = !ok;
     }
     // Every CTA waits for the leader's last commit (all MMAs that read its shared memory are done).
-    if (threadIdx.x == 64) mbar_wait(&done, 0, p.status, kStatusTimeout);
+    if (threadIdx.x == 64) mbar_wait(&done, 0, B.status, kStatusTimeout);
     if (failed) grace_delay(2000000);  // an aborted pipeline: let copies already in flight land
     tc_fence_before();
     cluster_sync();  // no CTA leaves while its peer may still write into it or signal it
@@ -683,22 +702,47 @@ __global__ void __launch_bounds__(256) eri_self_kernel(SelfArgs p) {
 }
 
 // ------------------------------------------------------------------ ladder kernel
-struct LadArgs {
-    int M, N, BN, n_mt, n_nt, n_ch, kb_per_chunk, nkb;
+// Work of one ladder launch: up to kMaxItems items (an instance's block pair each), each with
+// its T and V tensor maps and its int64 accumulator; their work units are numbered one after
+// the other, so one persistent launch covers several instances.
+struct LadItem {
+    int M, N, n_mt, n_nt, n_ch, kb_per_chunk, nkb;
     int swap;                // 0: rows m = pairs, columns n = (i,j); 1: rows m = (i,j), columns n = pairs
     int no2;
-    long long units;
+    long long ubeg, units;   // first unit of this item in the launch, and its unit count
     unsigned long long* rp;  // int64 fixed-point accumulator [npairs][no2]
+};
+
+struct LadBatch {
+    CUtensorMap ta[kMaxItems];  // A: T slices of the item's instance
+    CUtensorMap tb[kMaxItems];  // B: V planes of the item
+    LadItem item[kMaxItems];
+    long long units;            // all items' units
+    int nitems, BN;
     unsigned* status;
 };
+
+// Item of a unit, for units visited in increasing order.
+struct ItemCursor {
+    int k = 0;
+    __device__ __forceinline__ int seek(const LadBatch& B, long long u) {
+        while (k + 1 < B.nitems && u >= B.item[k + 1].ubeg) ++k;
+        return k;
+    }
+};
+
+// True when unit u + 1 belongs to another (item, row tile, column tile) than unit u of item k.
+__device__ __forceinline__ bool tile_ends(const LadBatch& B, int k, long long u) {
+    const LadItem& it = B.item[k];
+    if (u + 1 >= it.ubeg + it.units) return true;
+    return (u + 1 - it.ubeg) / it.n_ch != (u - it.ubeg) / it.n_ch;
+}
 
 // Work unit = (row tile, column tile, K chunk), chunk fastest; each CTA takes a
 // contiguous range of units (stream-K) and flushes its int64 sums with atomics
 // whenever its (row tile, column tile) changes.
 template <int S>
-__global__ void __launch_bounds__(kThreadsTC, 1) ladder_emu_kernel(const __grid_constant__ CUtensorMap tm_a,
-                                                                   const __grid_constant__ CUtensorMap tm_b,
-                                                                   LadArgs p) {
+__global__ void __launch_bounds__(kThreadsTC, 1) ladder_emu_kernel(const __grid_constant__ LadBatch B) {
     constexpr int BK = bk_for(S), STAGES = stages_for(S);
     constexpr uint32_t APLANE = kEmuTile * BK * 2;
     extern __shared__ unsigned char smem_raw[];
@@ -706,7 +750,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) ladder_emu_kernel(const __grid_
     __shared__ uint64_t full[STAGES], empty[STAGES], acc_full, acc_empty, done;
     __shared__ uint32_t tmem_base;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t BPLANE = (uint32_t)p.BN * BK * 2;
+    const uint32_t BPLANE = (uint32_t)B.BN * BK * 2;
     if (threadIdx.x == 0) {
         for (int i = 0; i < STAGES; ++i) {
             mbar_init(&full[i], 1);
@@ -716,15 +760,17 @@ __global__ void __launch_bounds__(kThreadsTC, 1) ladder_emu_kernel(const __grid_
         mbar_init(&acc_empty, kEpiWarps);
         mbar_init(&done, 1);
         fence_barrier_init();
-        tma_prefetch_desc(&tm_a);
-        tma_prefetch_desc(&tm_b);
+        for (int i = 0; i < B.nitems; ++i) {
+            tma_prefetch_desc(&B.ta[i]);
+            tma_prefetch_desc(&B.tb[i]);
+        }
     }
     if (warp == 1) tmem_alloc(&tmem_base, kTmemCols);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_base;
-    const long long u0 = p.units * blockIdx.x / gridDim.x, u1 = p.units * (blockIdx.x + 1) / gridDim.x;
+    const long long u0 = B.units * blockIdx.x / gridDim.x, u1 = B.units * (blockIdx.x + 1) / gridDim.x;
 
     if (warp == 0 && lane == 0) {
         // T slices (A) are re-read for every pair tile and stay in L2; the V planes (B) stream.
@@ -732,37 +778,43 @@ __global__ void __launch_bounds__(kThreadsTC, 1) ladder_emu_kernel(const __grid_
         int issued[STAGES] = {};
         const uint64_t keep = policy_evict_last(), stream = policy_evict_first();
         bool ok = true;
-        const uint32_t bytes = (uint32_t)S * (kEmuTile + p.BN) * BK * 2;
+        const uint32_t bytes = (uint32_t)S * (kEmuTile + B.BN) * BK * 2;
+        ItemCursor cur;
         for (long long u = u0; u < u1 && ok; ++u) {
-            const int ch = (int)(u % p.n_ch);
-            const long long tile = u / p.n_ch;
+            const int ik = cur.seek(B, u);
+            const LadItem& p = B.item[ik];
+            const long long ul = u - p.ubeg;
+            const int ch = (int)(ul % p.n_ch);
+            const long long tile = ul / p.n_ch;
             const int nt = (int)(tile % p.n_nt), mt = (int)(tile / p.n_nt);
             const int kb1 = min((ch + 1) * p.kb_per_chunk, p.nkb);
             for (int kb = ch * p.kb_per_chunk; kb < kb1 && ok; ++kb) {
-                if (!(ok = mbar_wait(&empty[ring.stage], ring.phase ^ 1u, p.status, kStatusTimeout))) break;
+                if (!(ok = mbar_wait(&empty[ring.stage], ring.phase ^ 1u, B.status, kStatusTimeout))) break;
                 unsigned char* st = smem + ring.stage * stage_bytes(S);
                 mbar_arrive_expect_tx(&full[ring.stage], bytes);
-                tma_load_3d_hint(st, &tm_a, &full[ring.stage], kb * BK, mt * kEmuTile, 0, keep);
-                tma_load_3d_hint(st + S * APLANE, &tm_b, &full[ring.stage], kb * BK, nt * p.BN, 0, stream);
+                tma_load_3d_hint(st, &B.ta[ik], &full[ring.stage], kb * BK, mt * kEmuTile, 0, keep);
+                tma_load_3d_hint(st + S * APLANE, &B.tb[ik], &full[ring.stage], kb * BK, nt * B.BN, 0, stream);
                 ++issued[ring.stage];
                 ring.next(STAGES);
             }
         }
         for (int i = 0; i < STAGES; ++i)
-            if (issued[i]) mbar_wait(&full[i], (uint32_t)((issued[i] - 1) & 1), p.status, kStatusTimeout);
+            if (issued[i]) mbar_wait(&full[i], (uint32_t)((issued[i] - 1) & 1), B.status, kStatusTimeout);
     } else if (warp == 1 && lane == 0) {
         Ring ring;
-        const uint32_t idesc = idesc_bf16_f32(kEmuTile, p.BN);
+        const uint32_t idesc = idesc_bf16_f32(kEmuTile, B.BN);
         bool ok = true;
         int it = 0;
+        ItemCursor cur;
         for (long long u = u0; u < u1 && ok; ++u, ++it) {
-            const int ch = (int)(u % p.n_ch);
-            if (!(ok = mbar_wait(&acc_empty, (uint32_t)(it & 1) ^ 1u, p.status, kStatusTimeout))) break;
+            const LadItem& p = B.item[cur.seek(B, u)];
+            const int ch = (int)((u - p.ubeg) % p.n_ch);
+            if (!(ok = mbar_wait(&acc_empty, (uint32_t)(it & 1) ^ 1u, B.status, kStatusTimeout))) break;
             tc_fence_after();
             bool first[kNumAcc] = {true, true, true, true, true};
             const int kb1 = min((ch + 1) * p.kb_per_chunk, p.nkb);
             for (int kb = ch * p.kb_per_chunk; kb < kb1 && ok; ++kb) {
-                if (!(ok = mbar_wait(&full[ring.stage], ring.phase, p.status, kStatusTimeout))) break;
+                if (!(ok = mbar_wait(&full[ring.stage], ring.phase, B.status, kStatusTimeout))) break;
                 tc_fence_after();
                 const uint32_t st = smem_u32(smem + ring.stage * stage_bytes(S));
                 issue_pairs<S>(tmem, st, st + S * APLANE, APLANE, BPLANE, idesc, first);
@@ -772,19 +824,20 @@ __global__ void __launch_bounds__(kThreadsTC, 1) ladder_emu_kernel(const __grid_
             if (ok) mma_commit(&acc_full);
         }
         mma_commit(&done);
-        mbar_wait(&done, 0, p.status, kStatusTimeout);
+        mbar_wait(&done, 0, B.status, kStatusTimeout);
     } else if (warp >= 2) {
         // Each warp: TMEM lane quadrant q, column chunks ci = h, h+2, h+4 (16 columns each).
         const int q = warp & 3, h = (warp - 2) >> 2;
-        const int nchunks = p.BN / 16;
+        const int nchunks = B.BN / 16;
         long long run[3][16];
 #pragma unroll
         for (int i = 0; i < 3; ++i)
 #pragma unroll
             for (int k = 0; k < 16; ++k) run[i][k] = 0;
         int it = 0;
+        ItemCursor cur;
         for (long long u = u0; u < u1; ++u, ++it) {
-            if (!mbar_wait(&acc_full, (uint32_t)(it & 1), p.status, kStatusTimeout)) break;
+            if (!mbar_wait(&acc_full, (uint32_t)(it & 1), B.status, kStatusTimeout)) break;
             tc_fence_after();
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
@@ -812,9 +865,11 @@ __global__ void __launch_bounds__(kThreadsTC, 1) ladder_emu_kernel(const __grid_
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty);
-            // Flush at the end of a (row tile, column tile) run or of this CTA's range.
-            const long long tile = u / p.n_ch;
-            if (u + 1 == u1 || (u + 1) / p.n_ch != tile) {
+            // Flush at the end of an (item, row tile, column tile) run or of this CTA's range.
+            const int ik = cur.seek(B, u);
+            const LadItem& p = B.item[ik];
+            const long long tile = (u - p.ubeg) / p.n_ch;
+            if (u + 1 == u1 || tile_ends(B, ik, u)) {
                 const int nt = (int)(tile % p.n_nt), mt = (int)(tile / p.n_nt);
                 const int m = mt * kEmuTile + 32 * q + lane;
 #pragma unroll
@@ -823,7 +878,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) ladder_emu_kernel(const __grid_
                     if (ci < nchunks) {
 #pragma unroll
                         for (int k = 0; k < 16; ++k) {
-                            const int n = nt * p.BN + 16 * ci + k;
+                            const int n = nt * B.BN + 16 * ci + k;
                             if (m < p.M && n < p.N && run[i][k] != 0) {
                                 const size_t idx = p.swap ? (size_t)n * p.no2 + m : (size_t)m * p.no2 + n;
                                 atomicAdd(p.rp + idx, (unsigned long long)run[i][k]);
@@ -849,7 +904,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) ladder_emu_kernel(const __grid_
 // units and each CTA flushes its int64 sums with atomics whenever the tile changes.
 template <int S>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
-    ladder_pair_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ CUtensorMap tm_b, LadArgs p) {
+    ladder_pair_kernel(const __grid_constant__ LadBatch B) {
     constexpr int BK = bk_for(S), STAGES = pair_stages_for(S);
     constexpr uint32_t APLANE = kEmuTile * BK * 2, BPLANE = (kEmuTileN / 2) * BK * 2;
     constexpr uint32_t ABYTES = S * APLANE;
@@ -860,7 +915,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t rank = cluster_ctarank();
     const long long cluster = blockIdx.x >> 1, nclusters = gridDim.x >> 1;
-    const long long u0 = p.units * cluster / nclusters, u1 = p.units * (cluster + 1) / nclusters;
+    const long long u0 = B.units * cluster / nclusters, u1 = B.units * (cluster + 1) / nclusters;
     if (threadIdx.x == 0) {
         for (int i = 0; i < STAGES; ++i) {
             mbar_init(&full[i], 1);
@@ -870,8 +925,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
         mbar_init(&acc_empty, 2 * kEpiWarps);
         mbar_init(&done, 1);
         fence_barrier_init();
-        tma_prefetch_desc(&tm_a);
-        tma_prefetch_desc(&tm_b);
+        for (int i = 0; i < B.nitems; ++i) {
+            tma_prefetch_desc(&B.ta[i]);
+            tma_prefetch_desc(&B.tb[i]);
+        }
     }
     if (warp == 1) tmem_alloc_pair(&tmem_base, kTmemCols);
     tc_fence_before();
@@ -885,20 +942,24 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
         Ring ring;
         bool ok = true;
         const uint64_t keep = policy_evict_last(), stream = policy_evict_first();
+        ItemCursor cur;
         for (long long u = u0; u < u1 && ok; ++u) {
-            const int ch = (int)(u % p.n_ch);
-            const long long tile = u / p.n_ch;
+            const int ik = cur.seek(B, u);
+            const LadItem& p = B.item[ik];
+            const long long ul = u - p.ubeg;
+            const int ch = (int)(ul % p.n_ch);
+            const long long tile = ul / p.n_ch;
             const int nt = (int)(tile % p.n_nt), mt = (int)(tile / p.n_nt);
             const int arow = mt * 2 * kEmuTile + kEmuTile * (int)rank;
             const int brow = nt * kEmuTileN + (kEmuTileN / 2) * (int)rank;
             const int kb1 = min((ch + 1) * p.kb_per_chunk, p.nkb);
             for (int kb = ch * p.kb_per_chunk; kb < kb1 && ok; ++kb) {
-                if (!(ok = mbar_wait(&empty[ring.stage], ring.phase ^ 1u, p.status, kStatusTimeout))) break;
+                if (!(ok = mbar_wait(&empty[ring.stage], ring.phase ^ 1u, B.status, kStatusTimeout))) break;
                 unsigned char* st = smem + ring.stage * pair_stage_bytes(S);
                 if (rank == 0) mbar_arrive_expect_tx(&full[ring.stage], 2 * pair_stage_bytes(S));
                 const uint32_t fb = mapa_rank(smem_u32(&full[ring.stage]), 0);
-                tma_load_3d_2sm_hint(st, &tm_a, fb, kb * BK, arow, 0, keep);
-                tma_load_3d_2sm_hint(st + ABYTES, &tm_b, fb, kb * BK, brow, 0, stream);
+                tma_load_3d_2sm_hint(st, &B.ta[ik], fb, kb * BK, arow, 0, keep);
+                tma_load_3d_2sm_hint(st + ABYTES, &B.tb[ik], fb, kb * BK, brow, 0, stream);
                 ring.next(STAGES);
             }
         }
@@ -908,14 +969,16 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
         const uint32_t idesc = idesc_bf16_f32(2 * kEmuTile, kEmuTileN);
         bool ok = true;
         int it = 0;
+        ItemCursor cur;
         for (long long u = u0; u < u1 && ok; ++u, ++it) {
-            const int ch = (int)(u % p.n_ch);
-            if (!(ok = mbar_wait(&acc_empty, (uint32_t)(it & 1) ^ 1u, p.status, kStatusTimeout))) break;
+            const LadItem& p = B.item[cur.seek(B, u)];
+            const int ch = (int)((u - p.ubeg) % p.n_ch);
+            if (!(ok = mbar_wait(&acc_empty, (uint32_t)(it & 1) ^ 1u, B.status, kStatusTimeout))) break;
             tc_fence_after();
             bool first[kNumAcc] = {true, true, true, true, true};
             const int kb1 = min((ch + 1) * p.kb_per_chunk, p.nkb);
             for (int kb = ch * p.kb_per_chunk; kb < kb1 && ok; ++kb) {
-                if (!(ok = mbar_wait(&full[ring.stage], ring.phase, p.status, kStatusTimeout))) break;
+                if (!(ok = mbar_wait(&full[ring.stage], ring.phase, B.status, kStatusTimeout))) break;
                 tc_fence_after();
                 const uint32_t st = smem_u32(smem + ring.stage * pair_stage_bytes(S));
                 issue_pairs<S, true>(tmem, st, st + ABYTES, APLANE, BPLANE, idesc, first);
@@ -936,8 +999,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
             for (int k = 0; k < 16; ++k) run[i][k] = 0;
         int it = 0;
         bool ok = true;
+        ItemCursor cur;
         for (long long u = u0; u < u1; ++u, ++it) {
-            if (!(ok = mbar_wait(&acc_full, (uint32_t)(it & 1), p.status, kStatusTimeout))) break;
+            if (!(ok = mbar_wait(&acc_full, (uint32_t)(it & 1), B.status, kStatusTimeout))) break;
             tc_fence_after();
 #pragma unroll
             for (int cc = 0; cc < 3; ++cc) {
@@ -962,8 +1026,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive_remote(acc_empty_leader);
-            const long long tile = u / p.n_ch;
-            if (u + 1 == u1 || (u + 1) / p.n_ch != tile) {
+            const int ik = cur.seek(B, u);
+            const LadItem& p = B.item[ik];
+            const long long tile = (u - p.ubeg) / p.n_ch;
+            if (u + 1 == u1 || tile_ends(B, ik, u)) {
                 const int nt = (int)(tile % p.n_nt), mt = (int)(tile / p.n_nt);
                 const int m = mt * 2 * kEmuTile + kEmuTile * (int)rank + 32 * q + lane;  // (i,j)
 #pragma unroll
@@ -979,7 +1045,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
         }
         failed = !ok;
     }
-    if (threadIdx.x == 64) mbar_wait(&done, 0, p.status, kStatusTimeout);
+    if (threadIdx.x == 64) mbar_wait(&done, 0, B.status, kStatusTimeout);
     if (failed) grace_delay(2000000);
     tc_fence_before();
     cluster_sync();
@@ -1077,80 +1143,131 @@ cudaError_t prep_impl(const ladder_plan_s& p, const double* L, const double* t2,
     return cudaGetLastError();
 }
 
+// The ERI work item of one block pair of a plan whose workspace starts at ws: its tables and
+// its two L^T tensor maps.
+template <int S>
+bool eri_item(const ladder_plan_s& p, const BlockPair& bp, void* ws, EriItem* it, CUtensorMap* ta, CUtensorMap* tb) {
+    constexpr int EBK = eri_bk_for(S);
+    const int vp = padded_vp(p.nv);
+    const long long rows = (long long)p.nv * vp;
+    const int xpad = (int)align_up((size_t)p.nchol, 8);
+    if (!make_tmap(ta, at<char>(ws, p.ws.lt_slices), p.nchol, rows, S, (uint64_t)xpad * 2, (uint64_t)rows * xpad * 2,
+                   EBK, kEmuTile) ||
+        !make_tmap(tb, at<char>(ws, p.ws.lt_slices), p.nchol, rows, S, (uint64_t)xpad * 2, (uint64_t)rows * xpad * 2,
+                   EBK, kEmuTileN / 2))
+        return false;
+    const int* row_start = reinterpret_cast<const int*>(p.d_tables) + bp.rows_off;
+    *it = EriItem{p.nv, vp, p.nchol, bp.a0, bp.a1 - bp.a0, bp.b0, bp.b1 - bp.b0, (int)rows,
+                  (size_t)p.max_pairs * (size_t)rows, row_start, at<int>(ws, p.ws.lt_exp), at<int>(ws, p.ws.v_exp),
+                  at<__nv_bfloat16>(ws, p.ws.v_blk)};
+    return true;
+}
+
+// One persistent ERI launch over every tile of the batch: no more CTA pairs than fit at once
+// (a cluster that waited for a free slot would process its share of the tiles after all the
+// others).
+template <int S>
+void launch_eri_batch(const EriBatch& eb, int max_clusters, cudaStream_t s) {
+    const int clusters = std::max(1, std::min(eb.nentries, max_clusters));
+    eri_emu_kernel<S><<<2 * clusters, kThreadsEri, eri_smem_bytes_for(S), s>>>(eb);
+}
+
+// The self-product entries of one block pair, after its ERI.
+template <int S>
+void launch_self(const ladder_plan_s& p, const BlockPair& bp, void* ws, cudaStream_t s) {
+    const int vp = padded_vp(p.nv);
+    const int kpad = p.nv * vp;
+    const int2* table = reinterpret_cast<const int2*>(p.d_tables);
+    const int* row_start = reinterpret_cast<const int*>(p.d_tables) + bp.rows_off;
+    const int ndiag = std::max(0, std::min(bp.a1, bp.b1) - std::max(bp.a0, bp.b0));
+    const long long nself = (long long)bp.npairs + (long long)ndiag * p.nv;
+    SelfArgs sa{p.nv, vp, kpad, bp.a0, bp.a1, bp.b0, bp.b1, bp.npairs, (size_t)p.max_pairs * kpad,
+                table + bp.pairs_off, row_start, at<int>(ws, p.ws.v_exp), at<double>(ws, p.ws.lsq),
+                at<__nv_bfloat16>(ws, p.ws.v_blk), p.d_status};
+    eri_self_kernel<S><<<(unsigned)((nself + 255) / 256), 256, 0, s>>>(sa);
+}
+
+// The ladder runs on CTA pairs (256-row (i,j) tiles) when o^2 > 128.
+inline bool ladder_on_pairs(const ladder_plan_s& p) { return p.no * p.no > kEmuTile; }
+
+// The ladder work item of one block pair of a plan whose workspace starts at ws; its units are
+// numbered from ubeg in the launch.
+template <int S>
+bool ladder_item(const ladder_plan_s& p, const BlockPair& bp, void* ws, long long ubeg, LadItem* it, CUtensorMap* ta,
+                 CUtensorMap* tb) {
+    constexpr int BK = bk_for(S);
+    const bool pair = ladder_on_pairs(p);
+    const int vp = padded_vp(p.nv);
+    const int kpad = p.nv * vp, no2 = p.no * p.no;
+    const size_t vplane = (size_t)p.max_pairs * kpad;
+    if (!make_tmap(ta, at<char>(ws, p.ws.t_slices), kpad, no2, S, (uint64_t)kpad * 2, (uint64_t)no2 * kpad * 2, BK,
+                   kEmuTile) ||
+        !make_tmap(tb, at<char>(ws, p.ws.v_blk), kpad, bp.npairs, S, (uint64_t)kpad * 2, (uint64_t)vplane * 2, BK,
+                   pair ? kEmuTileN / 2 : kEmuTileN))
+        return false;
+    LadItem x{};
+    x.swap = 1;
+    x.no2 = no2;
+    x.M = no2;
+    x.N = bp.npairs;
+    x.n_mt = (x.M + (pair ? 2 : 1) * kEmuTile - 1) / ((pair ? 2 : 1) * kEmuTile);
+    x.n_nt = (x.N + kEmuTileN - 1) / kEmuTileN;
+    x.nkb = (kpad + BK - 1) / BK;
+    x.kb_per_chunk = kEmuChunkK / BK;
+    x.n_ch = (x.nkb + x.kb_per_chunk - 1) / x.kb_per_chunk;
+    x.units = (long long)x.n_mt * x.n_nt * x.n_ch;
+    x.ubeg = ubeg;
+    x.rp = at<unsigned long long>(ws, p.ws.rp_int);
+    *it = x;
+    return true;
+}
+
+// One persistent ladder launch over every unit of the batch (all items on CTA pairs, or all on
+// single CTAs).
+template <int S>
+void launch_ladder_batch(const LadBatch& lb, bool on_pairs, int max_pair_clusters, int num_sms, cudaStream_t s) {
+    if (on_pairs) {
+        const long long clusters = std::max<long long>(1, std::min<long long>(lb.units, max_pair_clusters));
+        ladder_pair_kernel<S><<<(unsigned)(2 * clusters), kThreadsTC, pair_smem_bytes_for(S), s>>>(lb);
+    } else {
+        ladder_emu_kernel<S><<<(unsigned)std::max<long long>(1, std::min<long long>(lb.units, num_sms)), kThreadsTC,
+                               smem_bytes_for(S), s>>>(lb);
+    }
+}
+
 template <int S>
 cudaError_t block_impl(const ladder_plan_s& p, const BlockPair& bp, double* R, void* ws, cudaStream_t s) {
-    constexpr int BK = bk_for(S);
-    const int vp = padded_vp(p.nv);
-    const long long rows = (long long)p.nv * vp;   // padded L^T rows = padded K of the ladder
     const int no2 = p.no * p.no;
-    const int xpad = (int)align_up((size_t)p.nchol, 8);
-    const int kpad = (int)rows;
-    const size_t vplane = (size_t)p.max_pairs * kpad;
-    const int smem = smem_bytes_for(S);
     cudaError_t e;
     // int64 ladder accumulator of this block pair starts at zero
     if ((e = cudaMemsetAsync(at<char>(ws, p.ws.rp_int), 0, (size_t)bp.npairs * no2 * 8, s)) != cudaSuccess) return e;
 
     const int2* table = reinterpret_cast<const int2*>(p.d_tables);
-    const int* row_start = reinterpret_cast<const int*>(p.d_tables) + bp.rows_off;
-    CUtensorMap tm_la, tm_lb, tm_v, tm_t;
-    constexpr int EBK = eri_bk_for(S);
-    if (!make_tmap(&tm_la, at<char>(ws, p.ws.lt_slices), p.nchol, rows, S, (uint64_t)xpad * 2,
-                   (uint64_t)rows * xpad * 2, EBK, kEmuTile) ||
-        !make_tmap(&tm_lb, at<char>(ws, p.ws.lt_slices), p.nchol, rows, S, (uint64_t)xpad * 2,
-                   (uint64_t)rows * xpad * 2, EBK, kEmuTileN / 2))
-        return cudaErrorInvalidValue;
-    EriArgs ea{p.nv, vp, p.nchol, bp.a0, bp.a1 - bp.a0, bp.b0, bp.b1 - bp.b0, kpad, bp.ntiles, vplane,
-               reinterpret_cast<const int4*>(table + bp.tiles_off), row_start, at<int>(ws, p.ws.lt_exp),
-               at<int>(ws, p.ws.v_exp), at<__nv_bfloat16>(ws, p.ws.v_blk), p.d_status};
+    EriBatch eb{};
+    eb.nitems = 1;
+    eb.nentries = bp.ntiles;
+    eb.entries = reinterpret_cast<const int4*>(table + bp.tiles_off);
+    eb.status = p.d_status;
+    if (!eri_item<S>(p, bp, ws, &eb.item[0], &eb.ta[0], &eb.tb[0])) return cudaErrorInvalidValue;
     {
         LaunchTimer tm(p, s, LADDER_KERNEL_ERI, 2);
-        // persistent: no more clusters than fit at once (a cluster that waits for a free slot
-        // would process its share of the tiles after all the others)
-        const int fit = p.eri_clusters > 0 ? p.eri_clusters : p.num_sms / 2;
-        const int clusters = std::max(1, std::min(bp.ntiles, fit));
-        eri_emu_kernel<S><<<2 * clusters, kThreadsEri, eri_smem_bytes_for(S), s>>>(tm_la, tm_lb, ea);
-        const int ndiag = std::max(0, std::min(bp.a1, bp.b1) - std::max(bp.a0, bp.b0));
-        const long long nself = (long long)bp.npairs + (long long)ndiag * p.nv;
-        SelfArgs sa{p.nv, vp, kpad, bp.a0, bp.a1, bp.b0, bp.b1, bp.npairs, vplane, table + bp.pairs_off, row_start,
-                    at<int>(ws, p.ws.v_exp), at<double>(ws, p.ws.lsq), at<__nv_bfloat16>(ws, p.ws.v_blk), p.d_status};
-        eri_self_kernel<S><<<(unsigned)((nself + 255) / 256), 256, 0, s>>>(sa);
+        launch_eri_batch<S>(eb, p.eri_clusters > 0 ? p.eri_clusters : p.num_sms / 2, s);
+        launch_self<S>(p, bp, ws, s);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
 
     // Rows = (i,j), columns = 96 pairs, so the V planes stream from HBM once per row tile:
     // o^2 <= 128 in one 128-row tile (one SM per tile); larger o^2 in 256-row tiles on CTA pairs.
-    const bool pair = no2 > kEmuTile;
-    const int BN = kEmuTileN;
-    LadArgs la{};
-    la.swap = 1;
-    la.no2 = no2;
-    la.M = no2;
-    la.N = bp.npairs;
-    la.BN = BN;
-    if (!make_tmap(&tm_t, at<char>(ws, p.ws.t_slices), kpad, no2, S, (uint64_t)kpad * 2, (uint64_t)no2 * kpad * 2, BK,
-                   kEmuTile) ||
-        !make_tmap(&tm_v, at<char>(ws, p.ws.v_blk), kpad, bp.npairs, S, (uint64_t)kpad * 2, (uint64_t)vplane * 2, BK,
-                   pair ? BN / 2 : BN))
-        return cudaErrorInvalidValue;
-    la.n_mt = (la.M + (pair ? 2 : 1) * kEmuTile - 1) / ((pair ? 2 : 1) * kEmuTile);
-    la.n_nt = (la.N + BN - 1) / BN;
-    la.nkb = (kpad + BK - 1) / BK;
-    la.kb_per_chunk = kEmuChunkK / BK;
-    la.n_ch = (la.nkb + la.kb_per_chunk - 1) / la.kb_per_chunk;
-    la.units = (long long)la.n_mt * la.n_nt * la.n_ch;
-    la.rp = at<unsigned long long>(ws, p.ws.rp_int);
-    la.status = p.d_status;
+    LadBatch lb{};
+    lb.nitems = 1;
+    lb.BN = kEmuTileN;
+    lb.status = p.d_status;
+    if (!ladder_item<S>(p, bp, ws, 0, &lb.item[0], &lb.ta[0], &lb.tb[0])) return cudaErrorInvalidValue;
+    lb.units = lb.item[0].units;
     {
         LaunchTimer tm(p, s, LADDER_KERNEL_LADDER);
-        if (pair) {
-            const int fit = p.pair_clusters > 0 ? p.pair_clusters : p.num_sms / 2;
-            const long long clusters = std::max<long long>(1, std::min<long long>(la.units, fit));
-            ladder_pair_kernel<S><<<(unsigned)(2 * clusters), kThreadsTC, pair_smem_bytes_for(S), s>>>(tm_t, tm_v, la);
-        } else {
-            ladder_emu_kernel<S><<<(unsigned)std::max<long long>(1, std::min<long long>(la.units, p.num_sms)),
-                                   kThreadsTC, smem, s>>>(tm_t, tm_v, la);
-        }
+        launch_ladder_batch<S>(lb, ladder_on_pairs(p), p.pair_clusters > 0 ? p.pair_clusters : p.num_sms / 2,
+                               p.num_sms, s);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     {
