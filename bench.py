@@ -351,7 +351,9 @@ def run_batched(args):
             "vs_baseline": None, "dtype": "f64-emulated(bf16 slices)" if precision == lad.LADDER_EMU_BF16 else "f64",
             "data": "synthetic",
             "config": {"workload": "c5: 24 uneven instances, no~U{5..30}, nv~U{60..320}, nchol=3(no+nv), seed 1239",
-                       "instances": len(shapes), "total_flops": flops, "worker_streams": k,
+                       "instances": len(shapes), "total_flops": flops,
+                       "schedule": (f"{-k} instance groups, one ERI and one ladder launch per shape per group"
+                                    if k < 0 else f"{k} worker streams"),
                        "graph": "one CUDA graph replay per step"},
             "roofline": roof, "clocks": clocks, "fp64_sequential": fp64,
         }

@@ -193,21 +193,43 @@ int ladder_energy(ladder_plan_t plan, const double* t2, const double* R, double*
 
 /*
  * ladder_plan_batched -- one plan for n independent ladder instances of
- * uneven shape (no[k], nv[k], nchol[k]), run by ladder_apply_batched.  Each
- * instance gets its own sub-plan (blocking from the cost model within the
- * budget share of one worker stream); the default schedule spreads the
- * instances over enough worker streams that the largest one is the tail
- * (ladder_tune_batched refines it by measurement).  Same precision / nslices /
- * budget / device meaning as ladder_plan; the budget covers all streams.
+ * uneven shape (no[k], nv[k], nchol[k]), run by ladder_apply_batched (the
+ * batching of independent contractions that the paper's engine does one after
+ * another, Sec. "A Generic Batching Recipe").  Each instance gets its own
+ * sub-plan against the whole budget (one block pair whenever its packed ERI
+ * fits).  The plan's workspace (ladder_workspace_bytes) holds as many
+ * instances at once as the budget allows.  Two kinds of schedule:
+ *   grouped (emulated path, the default): the instances are packed, largest
+ *     workspace first, into groups that fit the workspace; each group runs as
+ *     ONE persistent ERI launch over the tiles of all its instances, then ONE
+ *     persistent ladder launch per ladder shape (single CTAs for o^2 <= 128,
+ *     CTA pairs above) over all their units, with the small per-instance
+ *     preparation and finalisation kernels around them;
+ *   worker streams (the FP64 path's default): each instance runs as its own
+ *     ladder_apply on one of k plan-owned streams (longest first).
+ * ladder_batched_schedule selects one explicitly, ladder_tune_batched by
+ * measurement.  Same precision / nslices / budget / device meaning as
+ * ladder_plan.
  */
 int ladder_plan_batched(ladder_plan_t* out, int n, const int* no, const int* nv, const int* nchol,
                         int precision, int nslices, size_t ws_budget_bytes, int device);
 
 /*
+ * ladder_batched_schedule -- set the schedule of a batched plan.  schedule > 0:
+ * that many worker streams (at most the number that fit the workspace, and 8);
+ * schedule < 0: grouped, with at most ws_bytes / |schedule| of workspace per
+ * group (emulated path only).  Returns LADDER_OK, LADDER_ERR_ARG (not a batched
+ * plan, schedule 0, grouped on the FP64 path), LADDER_ERR_BUDGET (an instance
+ * does not fit the group size) or LADDER_ERR_CUDA.  *groups_or_streams (may be
+ * NULL) receives the resulting number of groups (negated) or streams.
+ */
+int ladder_batched_schedule(ladder_plan_t plan, int schedule, int* groups_or_streams);
+
+/*
  * ladder_apply_batched -- R[k] += ladder(L[k], t2[k]) for every instance k.
- * L, t2, R are HOST arrays of n device pointers.  The instances run on the
- * plan's worker streams (longest-first assignment), forked from and joined
- * back into `stream` with events, each stream with its own workspace slice.
+ * L, t2, R are HOST arrays of n device pointers.  Grouped schedule: everything
+ * is enqueued on `stream`.  Worker-stream schedule: the instances run on the
+ * plan's streams, forked from and joined back into `stream` with events.
  * No allocation and no host synchronisation: the whole call can be captured
  * into one CUDA graph from `stream`.
  */
@@ -216,13 +238,15 @@ int ladder_apply_batched(ladder_plan_t plan, const double* const* L, const doubl
 
 /*
  * ladder_tune_batched -- measured tuner of a batched plan: times
- * ladder_apply_batched with 1, 2, 4, 8 worker streams (capped at the number of
- * instances) on the given buffers and keeps the fastest schedule.  R[k] is
- * accumulated into by every trial (pass scratch R).  Synchronises the stream.
- * *best_streams (may be NULL) receives the chosen stream count.
+ * ladder_apply_batched under worker-stream schedules with 1, 2, 4, ... streams
+ * and (emulated path) grouped schedules with the whole workspace, a half and a
+ * quarter of it per group, on the given buffers, and keeps the fastest.  R[k]
+ * is accumulated into by every trial (pass scratch R).  Synchronises the
+ * stream.  *best_schedule (may be NULL) receives the chosen schedule: the
+ * number of streams (> 0) or minus the number of groups (< 0).
  */
 int ladder_tune_batched(ladder_plan_t plan, const double* const* L, const double* const* t2,
-                        double* const* R, void* ws, cudaStream_t stream, int* best_streams);
+                        double* const* R, void* ws, cudaStream_t stream, int* best_schedule);
 
 /*
  * Per-kernel timing for benchmarks.  ladder_plan_set_timing(plan, 1) creates a

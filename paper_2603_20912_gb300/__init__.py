@@ -283,8 +283,17 @@ def ladder_apply_batched(plan: Plan, Ls, t2s, Rs, ws=None, stream=None):
     return Rs
 
 
+def ladder_batched_schedule(plan: Plan, schedule: int) -> int:
+    """schedule > 0: that many worker streams; < 0: grouped, ws / |schedule| bytes per group.
+    Returns the number of streams (> 0) or minus the number of groups."""
+    out = ctypes.c_int()
+    _check(_load().ladder_batched_schedule(plan.handle, int(schedule), ctypes.byref(out)), "ladder_batched_schedule")
+    return out.value
+
+
 def ladder_tune_batched(plan: Plan, Ls, t2s, Rs, ws=None, stream=None) -> int:
-    """Measure 1/2/4/8 worker streams on these buffers (R receives every trial) and keep the fastest."""
+    """Time worker-stream and grouped schedules on these buffers (R receives every trial) and keep
+    the fastest; returns the number of streams (> 0) or minus the number of groups (< 0)."""
     n = len(Ls)
     arr = ctypes.c_void_p * n
     a = arr(*[_dev_ptr(x, "L").value for x in Ls])
@@ -331,5 +340,5 @@ EXPORTED_SYMBOLS = [
     "ladder_energy", "ladder_plan_batched", "ladder_apply_batched", "ladder_last_status", "ladder_plan_destroy",
     "ladder_strerror", "ladder_flops", "ladder_plan_dry", "ladder_plan_set_timing", "ladder_plan_timing",
     "ladder_energy_noalloc", "ladder_tune_batched", "ladder_plan_shard", "ladder_shard_blocks",
-    "ladder_watchdog_selftest",
+    "ladder_watchdog_selftest", "ladder_batched_schedule",
 ]

@@ -315,6 +315,7 @@ void destroy_plan(ladder_plan_s* p) {
     if (p->d_tables) cudaFree(p->d_tables);
     if (p->d_status) cudaFree(p->d_status);
     if (p->d_partials) cudaFree(p->d_partials);
+    if (p->d_group_entries) cudaFree(p->d_group_entries);
     if (cur >= 0 && cur != p->device) cudaSetDevice(cur);
     delete p;
 }
@@ -402,6 +403,7 @@ int make_plan(ladder_plan_s** out, int no, int nv, int nchol, int precision, int
 // Longest-processing-time-first assignment of instances to k worker streams; the
 // workspace of a stream is the largest workspace among its instances.
 void schedule_batched(ladder_plan_s& p, int k) {
+    p.sched_groups = 0;
     const int n = (int)p.sub.size();
     k = std::max(1, std::min(k, std::min(n, p.max_streams)));
     p.nstreams = k;
@@ -415,6 +417,74 @@ void schedule_batched(ladder_plan_s& p, int k) {
         p.stream_of[i] = w;
         load[w] += p.model_s[i];
     }
+}
+
+// An instance can join a group when it runs on the emulated path as a single block pair.
+bool groupable(const ladder_plan_s& s) { return s.precision != LADDER_FP64 && s.bps.size() == 1; }
+
+// Grouped schedule: first-fit decreasing of the instances' workspaces into groups of at most
+// `cap` bytes and emu_max_group() instances (an instance that cannot be grouped runs alone),
+// and the device list of every group's ERI tiles with z = position of the instance in its group.
+int schedule_groups(ladder_plan_s& p, size_t cap) {
+    const int n = (int)p.sub.size();
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return p.sub[x]->ws.total > p.sub[y]->ws.total; });
+    std::vector<std::vector<int>> groups;
+    std::vector<size_t> used;
+    p.inst_off.assign(n, 0);
+    for (int k : order) {
+        const size_t need = ladder::align_up(p.sub[k]->ws.total, ladder::kAlign);
+        if (need > p.ws.total) return LADDER_ERR_BUDGET;
+        int g = -1;
+        if (groupable(*p.sub[k]))
+            for (int j = 0; j < (int)groups.size() && g < 0; ++j)
+                if (groupable(*p.sub[groups[j][0]]) && used[j] + need <= cap &&
+                    (int)groups[j].size() < ladder::emu_max_group())
+                    g = j;
+        if (g < 0) {
+            groups.push_back({});
+            used.push_back(0);
+            g = (int)groups.size() - 1;
+        }
+        p.inst_off[k] = used[g];
+        used[g] += need;
+        groups[g].push_back(k);
+    }
+    std::vector<int> host;
+    p.group_eoff.clear();
+    p.group_ecnt.clear();
+    for (auto& grp : groups) {
+        p.group_eoff.push_back(host.size() / 4);
+        int cnt = 0;
+        if (grp.size() > 1 || groupable(*p.sub[grp[0]]))
+            for (int i = 0; i < (int)grp.size(); ++i) {
+                const ladder_plan_s& q = *p.sub[grp[i]];
+                const std::vector<int> t = eri_entries(q.bps[0], q.nv, 2 * ladder::kEmuTile, ladder::kEmuTileN,
+                                                       (size_t)q.nslices * 2 * ladder::align_up((size_t)q.nchol, 8));
+                for (size_t j = 0; j < t.size(); j += 4) {
+                    host.push_back(t[j]);
+                    host.push_back(t[j + 1]);
+                    host.push_back(i);
+                    host.push_back(0);
+                    ++cnt;
+                }
+            }
+        p.group_ecnt.push_back(cnt);
+    }
+    if (p.d_group_entries) {
+        cudaFree(p.d_group_entries);
+        p.d_group_entries = nullptr;
+    }
+    if (cudaMalloc(&p.d_group_entries, std::max<size_t>(16, host.size() * sizeof(int))) != cudaSuccess)
+        return LADDER_ERR_CUDA;
+    if (!host.empty() &&
+        cudaMemcpy(p.d_group_entries, host.data(), host.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+        return LADDER_ERR_CUDA;
+    p.groups = std::move(groups);
+    p.sched_groups = (int)p.groups.size();
+    return LADDER_OK;
 }
 
 }  // namespace
@@ -545,22 +615,21 @@ int ladder_plan_batched(ladder_plan_t* out, int n, const int* no, const int* nv,
     p->batched = true;
     p->precision = precision;
     p->device = device;
-    // Budget per worker stream: the caller's budget split over the streams the plan can use.
-    const int max_streams = std::min(n, 8);
-    size_t per_stream_budget = ws_budget_bytes;
-    if (per_stream_budget == 0) {
+    size_t budget = ws_budget_bytes;
+    if (budget == 0) {
         DeviceGuard g0(device);
         size_t free_b = 0, total_b = 0;
         if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
             destroy_plan(p);
             return LADDER_ERR_CUDA;
         }
-        per_stream_budget = (size_t)((double)free_b * 0.98 * 0.9);
+        budget = (size_t)((double)free_b * 0.98 * 0.9);
     }
-    per_stream_budget /= (size_t)max_streams;
+    // Every instance is planned against the whole budget (one block pair whenever its packed
+    // ERI fits), and the plan's workspace holds as many instances at once as the budget allows.
     for (int k = 0; k < n; ++k) {
         ladder_plan_s* s = nullptr;
-        const int rc = make_plan(&s, no[k], nv[k], nchol[k], precision, nslices, per_stream_budget, device);
+        const int rc = make_plan(&s, no[k], nv[k], nchol[k], precision, nslices, budget, device);
         if (rc != LADDER_OK) {
             destroy_plan(p);
             return rc;
@@ -570,15 +639,18 @@ int ladder_plan_batched(ladder_plan_t* out, int n, const int* no, const int* nv,
     }
     p->nslices = p->sub[0]->nslices;
     p->num_sms = p->sub[0]->num_sms;
+    p->budget = budget;
+    size_t biggest = ladder::kAlign, sum = 0;
+    for (auto* s : p->sub) {
+        biggest = std::max(biggest, ladder::align_up(s->ws.total, ladder::kAlign));
+        sum += ladder::align_up(s->ws.total, ladder::kAlign);
+    }
+    p->ws.total = std::max(biggest, std::min(sum, ladder::align_up(budget, ladder::kAlign)));
+    const int max_streams = (int)std::max<size_t>(1, std::min<size_t>(std::min(n, 8), p->ws.total / biggest));
     p->max_streams = max_streams;
     DeviceGuard guard(device);
-    // Workspace: every stream slot large enough for any instance it may get.
-    size_t biggest = ladder::kAlign;
-    for (auto* s : p->sub) biggest = std::max(biggest, s->ws.total);
-    biggest = ladder::align_up(biggest, ladder::kAlign);
     p->ws_off.resize(max_streams);
     for (int w = 0; w < max_streams; ++w) p->ws_off[w] = (size_t)w * biggest;
-    p->ws.total = biggest * (size_t)max_streams;
     p->workers.resize(max_streams, nullptr);
     p->fork_join.resize(1 + max_streams, nullptr);
     bool ok = true;
@@ -590,14 +662,39 @@ int ladder_plan_batched(ladder_plan_t* out, int n, const int* no, const int* nv,
         destroy_plan(p);
         return LADDER_ERR_CUDA;
     }
-    // Default schedule from the model: enough streams that the largest instance is the tail.
-    double total = 0.0, largest = 0.0;
-    for (double t : p->model_s) {
-        total += t;
-        largest = std::max(largest, t);
+    int rc = LADDER_OK;
+    if (precision != LADDER_FP64) {
+        // Default: the instances in as few groups as the workspace allows.
+        rc = schedule_groups(*p, p->ws.total);
+    } else {
+        // Default from the model: enough streams that the largest instance is the tail.
+        double total = 0.0, largest = 0.0;
+        for (double t : p->model_s) {
+            total += t;
+            largest = std::max(largest, t);
+        }
+        schedule_batched(*p, (int)std::ceil(total / std::max(largest, 1e-12)));
     }
-    schedule_batched(*p, (int)std::ceil(total / std::max(largest, 1e-12)));
+    if (rc != LADDER_OK) {
+        destroy_plan(p);
+        return rc;
+    }
     *out = p;
+    return LADDER_OK;
+}
+
+int ladder_batched_schedule(ladder_plan_t plan, int schedule, int* groups_or_streams) {
+    if (!plan || !plan->batched || schedule == 0) return LADDER_ERR_ARG;
+    if (schedule < 0 && plan->precision == LADDER_FP64) return LADDER_ERR_ARG;
+    DeviceGuard guard(plan->device);
+    if (!guard.ok) return LADDER_ERR_CUDA;
+    if (schedule > 0) {
+        schedule_batched(*plan, std::min(schedule, plan->max_streams));
+    } else {
+        const int rc = schedule_groups(*plan, plan->ws.total / (size_t)(-(long long)schedule));
+        if (rc != LADDER_OK) return rc;
+    }
+    if (groups_or_streams) *groups_or_streams = plan->sched_groups > 0 ? -plan->sched_groups : plan->nstreams;
     return LADDER_OK;
 }
 
@@ -607,6 +704,38 @@ int ladder_apply_batched(ladder_plan_t plan, const double* const* L, const doubl
     if (!aligned256(ws)) return LADDER_ERR_ARG;
     DeviceGuard guard(plan->device);
     if (!guard.ok) return LADDER_ERR_CUDA;
+    if (plan->sched_groups > 0) {
+        // Grouped schedule: each group is one ERI launch and one ladder launch per shape.
+        char* base = static_cast<char*>(ws);
+        for (size_t g = 0; g < plan->groups.size(); ++g) {
+            const std::vector<int>& grp = plan->groups[g];
+            if (grp.size() == 1 && !groupable(*plan->sub[grp[0]])) {
+                const int k = grp[0];
+                const int rc = ladder_apply(plan->sub[k], L[k], t2[k], R[k], base + plan->inst_off[k], stream);
+                if (rc != LADDER_OK) return rc;
+                continue;
+            }
+            std::vector<const ladder_plan_s*> subs;
+            std::vector<void*> wsv;
+            std::vector<const double*> Lv, tv;
+            std::vector<double*> Rv;
+            for (int k : grp) {
+                if (!L[k] || !t2[k] || !R[k] || !aligned256(L[k]) || !aligned256(t2[k]) || !aligned256(R[k]))
+                    return LADDER_ERR_ARG;
+                subs.push_back(plan->sub[k]);
+                wsv.push_back(base + plan->inst_off[k]);
+                Lv.push_back(L[k]);
+                tv.push_back(t2[k]);
+                Rv.push_back(R[k]);
+            }
+            const int4* entries = static_cast<const int4*>(plan->d_group_entries) + plan->group_eoff[g];
+            const cudaError_t e = ladder::launch_emu_group(*plan, subs.data(), (int)subs.size(), wsv.data(),
+                                                           Lv.data(), tv.data(), Rv.data(), entries,
+                                                           plan->group_ecnt[g], stream);
+            if (e != cudaSuccess) return LADDER_ERR_CUDA;
+        }
+        return LADDER_OK;
+    }
     const int k = plan->nstreams;
     // fork: every worker stream waits for the work already queued on the caller's stream
     if (cudaEventRecord(plan->fork_join[0], stream) != cudaSuccess) return LADDER_ERR_CUDA;
@@ -629,20 +758,36 @@ int ladder_apply_batched(ladder_plan_t plan, const double* const* L, const doubl
 }
 
 int ladder_tune_batched(ladder_plan_t plan, const double* const* L, const double* const* t2, double* const* R,
-                        void* ws, cudaStream_t stream, int* best_streams) {
+                        void* ws, cudaStream_t stream, int* best_schedule) {
     if (!plan || !plan->batched) return LADDER_ERR_ARG;
     DeviceGuard guard(plan->device);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return LADDER_ERR_CUDA;
-    int best_k = plan->nstreams;
+    // Candidates: worker-stream schedules with 1, 2, 4, ... streams, and (emulated path) grouped
+    // schedules with the whole workspace, a half and a quarter of it per group.
+    struct Cand { int streams; size_t cap; };
+    std::vector<Cand> cands;
+    for (int k = 1; k < plan->max_streams; k *= 2) cands.push_back({k, 0});
+    cands.push_back({plan->max_streams, 0});
+    if (plan->precision != LADDER_FP64) {
+        size_t biggest = 0;
+        for (auto* s : plan->sub) biggest = std::max(biggest, ladder::align_up(s->ws.total, ladder::kAlign));
+        for (int d = 1; d <= 4; d *= 2)
+            if (plan->ws.total / d >= biggest) cands.push_back({0, plan->ws.total / d});
+    }
     float best_ms = 1e30f;
+    Cand best = cands[0];
     int rc = LADDER_OK;
-    std::vector<int> cands;
-    for (int k = 1; k < plan->max_streams; k *= 2) cands.push_back(k);
-    cands.push_back(plan->max_streams);
-    for (int k : cands) {
+    auto use = [&](const Cand& c) -> int {
+        if (c.streams > 0) {
+            schedule_batched(*plan, c.streams);
+            return LADDER_OK;
+        }
+        return schedule_groups(*plan, c.cap);
+    };
+    for (const Cand& c : cands) {
         if (rc != LADDER_OK) break;
-        schedule_batched(*plan, k);
+        if ((rc = use(c)) != LADDER_OK) break;
         rc = ladder_apply_batched(plan, L, t2, R, ws, stream);  // warm-up of this schedule
         if (rc != LADDER_OK) break;
         if (cudaEventRecord(e0, stream) != cudaSuccess) rc = LADDER_ERR_CUDA;
@@ -651,15 +796,18 @@ int ladder_tune_batched(ladder_plan_t plan, const double* const* L, const double
             rc = LADDER_ERR_CUDA;
         float ms = 0.0f;
         if (rc == LADDER_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = LADDER_ERR_CUDA;
-        if (rc == LADDER_OK && ms < best_ms) {
-            best_ms = ms;
-            best_k = plan->nstreams;
+        // A grouped schedule (fewer launches) wins ties within 1 %.
+        const float score = c.streams > 0 ? ms : ms * 0.99f;
+        if (rc == LADDER_OK && score < best_ms) {
+            best_ms = score;
+            best = c;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    schedule_batched(*plan, best_k);
-    if (best_streams) *best_streams = plan->nstreams;
+    const int rc2 = use(best);
+    if (rc == LADDER_OK) rc = rc2;
+    if (best_schedule) *best_schedule = plan->sched_groups > 0 ? -plan->sched_groups : plan->nstreams;
     return rc;
 }
 

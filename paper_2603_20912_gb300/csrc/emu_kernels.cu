@@ -1280,6 +1280,77 @@ cudaError_t block_impl(const ladder_plan_s& p, const BlockPair& bp, double* R, v
     return cudaGetLastError();
 }
 
+// A group of instances, each planned as one block pair: every instance's operand preparation,
+// then ONE persistent ERI launch over all their tiles, their self-product entries, ONE
+// persistent ladder launch per ladder shape (single CTAs for o^2 <= 128, CTA pairs above) over
+// all their units, and their finalisation.  The instances' workspaces start at ws[k].  The
+// ERI tile list (z = position of the instance in the group) is built by the caller.
+template <int S>
+cudaError_t group_impl(const ladder_plan_s& parent, const ladder_plan_s* const* subs, int n, void* const* ws,
+                       const double* const* L, const double* const* t2, double* const* R, const int4* entries,
+                       int nentries, cudaStream_t s) {
+    if (n < 1 || n > kMaxItems) return cudaErrorInvalidValue;
+    cudaError_t e;
+    for (int k = 0; k < n; ++k) {
+        const ladder_plan_s& p = *subs[k];
+        if (p.bps.size() != 1) return cudaErrorInvalidValue;
+        if ((e = prep_impl<S>(p, L[k], t2[k], ws[k], s)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(at<char>(ws[k], p.ws.rp_int), 0, (size_t)p.bps[0].npairs * p.no * p.no * 8, s)) !=
+            cudaSuccess)
+            return e;
+    }
+    static thread_local EriBatch eb;   // ~10 KB: kept off the stack
+    eb = EriBatch{};
+    eb.nitems = n;
+    eb.nentries = nentries;
+    eb.entries = entries;
+    eb.status = parent.d_status;
+    for (int k = 0; k < n; ++k)
+        if (!eri_item<S>(*subs[k], subs[k]->bps[0], ws[k], &eb.item[k], &eb.ta[k], &eb.tb[k]))
+            return cudaErrorInvalidValue;
+    const int eri_fit = subs[0]->eri_clusters > 0 ? subs[0]->eri_clusters : subs[0]->num_sms / 2;
+    const int pair_fit = subs[0]->pair_clusters > 0 ? subs[0]->pair_clusters : subs[0]->num_sms / 2;
+    {
+        LaunchTimer tm(parent, s, LADDER_KERNEL_ERI, 1 + n);
+        launch_eri_batch<S>(eb, eri_fit, s);
+        for (int k = 0; k < n; ++k) launch_self<S>(*subs[k], subs[k]->bps[0], ws[k], s);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    for (int shape = 0; shape < 2; ++shape) {   // 0: single CTAs, 1: CTA pairs
+        static thread_local LadBatch lb;
+        lb = LadBatch{};
+        lb.BN = kEmuTileN;
+        lb.status = parent.d_status;
+        long long units = 0;
+        for (int k = 0; k < n; ++k) {
+            if ((int)ladder_on_pairs(*subs[k]) != shape) continue;
+            LadItem* it = &lb.item[lb.nitems];
+            if (!ladder_item<S>(*subs[k], subs[k]->bps[0], ws[k], units, it, &lb.ta[lb.nitems], &lb.tb[lb.nitems]))
+                return cudaErrorInvalidValue;
+            units += it->units;
+            ++lb.nitems;
+        }
+        if (lb.nitems == 0) continue;
+        lb.units = units;
+        LaunchTimer tm(parent, s, LADDER_KERNEL_LADDER);
+        launch_ladder_batch<S>(lb, shape == 1, pair_fit, subs[0]->num_sms, s);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    {
+        LaunchTimer tm(parent, s, LADDER_KERNEL_FINISH, n);
+        for (int k = 0; k < n; ++k) {
+            const ladder_plan_s& p = *subs[k];
+            const BlockPair& bp = p.bps[0];
+            const long long cnt = (long long)bp.npairs * p.no * p.no;
+            finalize_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(
+                at<unsigned long long>(ws[k], p.ws.rp_int), bp.npairs, p.no, p.nv,
+                reinterpret_cast<const int2*>(p.d_tables) + bp.pairs_off, at<int>(ws[k], p.ws.v_exp),
+                at<int>(ws[k], p.ws.t_exp), R[k]);
+        }
+    }
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 template <int S>
@@ -1346,6 +1417,20 @@ cudaError_t launch_emu_prep(const ladder_plan_s& p, const double* L, const doubl
         default: return cudaErrorInvalidValue;
     }
 }
+
+cudaError_t launch_emu_group(const ladder_plan_s& parent, const ladder_plan_s* const* subs, int n, void* const* ws,
+                             const double* const* L, const double* const* t2, double* const* R, const int4* entries,
+                             int nentries, cudaStream_t s) {
+    switch (parent.nslices) {
+        case 5: return group_impl<5>(parent, subs, n, ws, L, t2, R, entries, nentries, s);
+        case 6: return group_impl<6>(parent, subs, n, ws, L, t2, R, entries, nentries, s);
+        case 7: return group_impl<7>(parent, subs, n, ws, L, t2, R, entries, nentries, s);
+        case 8: return group_impl<8>(parent, subs, n, ws, L, t2, R, entries, nentries, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+int emu_max_group() { return kMaxItems; }
 
 cudaError_t launch_emu_block(const ladder_plan_s& p, const BlockPair& bp, double* R, void* ws, cudaStream_t s) {
     switch (p.nslices) {

@@ -95,6 +95,14 @@ struct ladder_plan_s {
     std::vector<cudaStream_t> workers;
     std::vector<cudaEvent_t> fork_join;  // [0] fork, [1 + w] join of worker w
     std::vector<double> model_s;       // modelled seconds per instance
+    // Batched plans, grouped schedule (emulated path): the instances run in groups, each group
+    // with one ERI launch and one ladder launch per ladder shape over all of its instances.
+    int sched_groups = 0;                     // 0: worker-stream schedule; > 0: number of groups
+    std::vector<std::vector<int>> groups;     // instances of each group
+    std::vector<size_t> inst_off;             // workspace offset of each instance in the grouped schedule
+    std::vector<size_t> group_eoff;           // first ERI entry (int4) of each group in d_group_entries
+    std::vector<int> group_ecnt;              // ERI entries of each group
+    void* d_group_entries = nullptr;
 };
 
 namespace ladder {
@@ -131,6 +139,13 @@ cudaError_t launch_emu_prep(const ladder_plan_s& p, const double* L, const doubl
                             cudaStream_t s);
 cudaError_t launch_emu_block(const ladder_plan_s& p, const BlockPair& bp, double* R, void* ws,
                              cudaStream_t s);
+// A group of emulated instances planned as one block pair each, run with one ERI launch and
+// one ladder launch per ladder shape over all of them (ws[k]: instance k's workspace; entries:
+// the group's ERI tiles with z = position of the instance in the group).
+cudaError_t launch_emu_group(const ladder_plan_s& parent, const ladder_plan_s* const* subs, int n, void* const* ws,
+                             const double* const* L, const double* const* t2, double* const* R, const int4* entries,
+                             int nentries, cudaStream_t s);
+int emu_max_group();  // most instances in one group
 bool emu_supported(int no, int nv, int nchol, int nslices);
 cudaError_t emu_set_attributes(int nslices);  // per device, before the first launch
 // Co-resident clusters of the emulated CTA-pair kernels on the current device: kind 0 = ERI,
