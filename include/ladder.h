@@ -55,7 +55,8 @@ enum {
     LADDER_ERR_CUDA = 3,         /* a CUDA runtime / driver call failed                  */
     LADDER_ERR_UNSUPPORTED = 4,  /* valid request this build does not implement          */
     LADDER_ERR_TIMEOUT = 5,      /* a kernel's bounded wait ran out (device status)      */
-    LADDER_ERR_NUMERIC = 6       /* a kernel consistency check failed (device status)    */
+    LADDER_ERR_NUMERIC = 6,      /* a kernel consistency check failed (device status)    */
+    LADDER_ERR_BOUNDS = 7        /* an index check of a LADDER_CHECK build failed         */
 };
 
 /* Arithmetic of the two contractions. */
@@ -267,8 +268,10 @@ enum {
 int ladder_plan_set_timing(ladder_plan_t plan, int enable);
 int ladder_plan_timing(ladder_plan_t plan, int kernel_class, float* total_ms, int* launches, int reset);
 
-/* Read (and clear) the plan's device status word: LADDER_OK, LADDER_ERR_TIMEOUT
- * or LADDER_ERR_NUMERIC.  Synchronises the stream. */
+/* Read (and clear) the plan's device status word: LADDER_OK, LADDER_ERR_BOUNDS
+ * (only in a library built with LADDER_CHECK, whose kernels test the index of
+ * every store into the workspace and into R, record a failure here and skip the
+ * store), LADDER_ERR_TIMEOUT or LADDER_ERR_NUMERIC.  Synchronises the stream. */
 int ladder_last_status(ladder_plan_t plan, cudaStream_t stream);
 
 /*

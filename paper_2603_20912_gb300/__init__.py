@@ -26,6 +26,7 @@ LADDER_ERR_CUDA = 3
 LADDER_ERR_UNSUPPORTED = 4
 LADDER_ERR_TIMEOUT = 5
 LADDER_ERR_NUMERIC = 6
+LADDER_ERR_BOUNDS = 7
 
 LADDER_FP64 = 0
 LADDER_EMU_BF16 = 1
@@ -36,7 +37,8 @@ LADDER_KERNEL_ERI = 1
 LADDER_KERNEL_LADDER = 2
 LADDER_KERNEL_FINISH = 3
 
-LIB_PATH = _build_mod.LIB
+# LADDER_CHECKED_LIBRARY=1 loads the index-checked build (build.build(check=True)) instead.
+LIB_PATH = _build_mod.LIB_CHECK if os.environ.get("LADDER_CHECKED_LIBRARY") == "1" else _build_mod.LIB
 
 _lib = None
 

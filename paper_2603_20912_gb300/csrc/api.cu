@@ -872,6 +872,7 @@ int ladder_last_status(ladder_plan_t plan, cudaStream_t stream) {
             return LADDER_ERR_CUDA;
         word |= w;
     }
+    if (word & ladder::kStatusBounds) return LADDER_ERR_BOUNDS;
     if (word & ladder::kStatusTimeout) return LADDER_ERR_TIMEOUT;
     if (word & ladder::kStatusNumeric) return LADDER_ERR_NUMERIC;
     return LADDER_OK;
@@ -930,6 +931,7 @@ const char* ladder_strerror(int status) {
         case LADDER_ERR_UNSUPPORTED: return "unsupported configuration";
         case LADDER_ERR_TIMEOUT: return "a kernel's bounded wait timed out";
         case LADDER_ERR_NUMERIC: return "a kernel consistency check failed";
+        case LADDER_ERR_BOUNDS: return "an index check of a LADDER_CHECK build failed";
         default: return "unknown status";
     }
 }

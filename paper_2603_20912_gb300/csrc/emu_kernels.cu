@@ -267,7 +267,7 @@ __global__ void f_table_kernel(const unsigned long long* __restrict__ lnorm_bits
 template <int S>
 __global__ void __launch_bounds__(256) lt_slice_kernel(const double* __restrict__ L, int nchol, int nv, int vp,
                                                        int xpad, const int* __restrict__ lt_exp,
-                                                       __nv_bfloat16* __restrict__ planes) {
+                                                       __nv_bfloat16* __restrict__ planes, unsigned* status) {
     __shared__ double tile[64][65];
     const long long nv2 = (long long)nv * nv, rows = (long long)nv * vp;
     const int P0 = blockIdx.x * 64;
@@ -300,6 +300,7 @@ __global__ void __launch_bounds__(256) lt_slice_kernel(const double* __restrict_
         // 16 consecutive P of one row: two 16-byte stores per plane (xpad % 8 == 0, P0t % 16 == 0)
 #pragma unroll
         for (int s2 = 0; s2 < S; ++s2) {
+            if (!LADDER_IN_BOUNDS((size_t)r * xpad + P0t + 16 <= plane, status)) continue;
             uint4* dst = reinterpret_cast<uint4*>(planes + s2 * plane + (size_t)r * xpad + P0t);
             dst[0] = reinterpret_cast<const uint4*>(out[s2])[0];
             dst[1] = reinterpret_cast<const uint4*>(out[s2])[1];
@@ -307,7 +308,9 @@ __global__ void __launch_bounds__(256) lt_slice_kernel(const double* __restrict_
     } else {
         for (int k = 0; k < 16 && P0t + k < xpad; ++k)
 #pragma unroll
-            for (int s2 = 0; s2 < S; ++s2) planes[s2 * plane + (size_t)r * xpad + P0t + k] = out[s2][k];
+            for (int s2 = 0; s2 < S; ++s2)
+                if (LADDER_IN_BOUNDS((size_t)r * xpad + P0t + k < plane, status))
+                    planes[s2 * plane + (size_t)r * xpad + P0t + k] = out[s2][k];
     }
 }
 
@@ -333,7 +336,7 @@ __global__ void exp_from_max_kernel(const unsigned long long* __restrict__ gmax,
 template <int S>
 __global__ void __launch_bounds__(256) t_slice_kernel(const double* __restrict__ t2, int nv, int vp, int rows,
                                                       int kpad, const int* __restrict__ t_exp,
-                                                      __nv_bfloat16* __restrict__ planes) {
+                                                      __nv_bfloat16* __restrict__ planes, unsigned* status) {
     const long long per_row = kpad / 8;
     const long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= per_row * rows) return;
@@ -355,7 +358,8 @@ __global__ void __launch_bounds__(256) t_slice_kernel(const double* __restrict__
     }
 #pragma unroll
     for (int s = 0; s < S; ++s)
-        *reinterpret_cast<uint4*>(planes + s * plane + (size_t)row * kpad + k0) = *reinterpret_cast<uint4*>(out[s]);
+        if (LADDER_IN_BOUNDS((size_t)row * kpad + k0 + 8 <= plane, status))
+            *reinterpret_cast<uint4*>(planes + s * plane + (size_t)row * kpad + k0) = *reinterpret_cast<uint4*>(out[s]);
 }
 
 // ------------------------------------------------------------------ shared tcgen05 pieces
@@ -620,16 +624,18 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsEri, 1)
                 if (!sector_pairs) {
 #pragma unroll
                     for (int s2 = 0; s2 < S; ++s2)
-                        __stcs(reinterpret_cast<uint4*>(p.vplanes + s2 * p.plane_stride + off),
-                               *reinterpret_cast<const uint4*>(out[s2]));
+                        if (LADDER_IN_BOUNDS(off + 8 <= p.plane_stride, B.status))
+                            __stcs(reinterpret_cast<uint4*>(p.vplanes + s2 * p.plane_stride + off),
+                                   *reinterpret_cast<const uint4*>(out[s2]));
                 } else if ((g & 1) == 0) {  // runs 2k, 2k+1: same b, both valid or both skipped
 #pragma unroll
                     for (int s2 = 0; s2 < S; ++s2) prev[s2] = *reinterpret_cast<const uint4*>(out[s2]);
                 } else {
 #pragma unroll
                     for (int s2 = 0; s2 < S; ++s2)
-                        st_cs_32B(p.vplanes + s2 * p.plane_stride + off - 8, prev[s2],
-                                  *reinterpret_cast<const uint4*>(out[s2]));
+                        if (LADDER_IN_BOUNDS(off >= 8 && off + 8 <= p.plane_stride, B.status))
+                            st_cs_32B(p.vplanes + s2 * p.plane_stride + off - 8, prev[s2],
+                                      *reinterpret_cast<const uint4*>(out[s2]));
                 }
             }
         }
@@ -697,6 +703,7 @@ __global__ void __launch_bounds__(256) eri_self_kernel(SelfArgs p) {
     __nv_bfloat16 dg[S];
     digits_of<S>(N, dg);
     const size_t off = (size_t)row * p.kpad + (size_t)c * p.vp + d;
+    if (!LADDER_IN_BOUNDS(off < p.plane_stride, p.status)) return;
 #pragma unroll
     for (int s = 0; s < S; ++s) p.vplanes[s * p.plane_stride + off] = dg[s];
 }
@@ -881,7 +888,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1) ladder_emu_kernel(const __grid_
                             const int n = nt * B.BN + 16 * ci + k;
                             if (m < p.M && n < p.N && run[i][k] != 0) {
                                 const size_t idx = p.swap ? (size_t)n * p.no2 + m : (size_t)m * p.no2 + n;
-                                atomicAdd(p.rp + idx, (unsigned long long)run[i][k]);
+                                if (LADDER_IN_BOUNDS(idx < (size_t)(p.swap ? p.N : p.M) * p.no2, B.status))
+                                    atomicAdd(p.rp + idx, (unsigned long long)run[i][k]);
                             }
                             run[i][k] = 0;
                         }
@@ -1037,7 +1045,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
 #pragma unroll
                     for (int k = 0; k < 16; ++k) {
                         const int n = nt * kEmuTileN + 48 * h + 16 * cc + k;                  // pair
-                        if (m < p.M && n < p.N && run[cc][k] != 0)
+                        if (m < p.M && n < p.N && run[cc][k] != 0 &&
+                            LADDER_IN_BOUNDS((size_t)n * p.no2 + m < (size_t)p.N * p.no2, B.status))
                             atomicAdd(p.rp + (size_t)n * p.no2 + m, (unsigned long long)run[cc][k]);
                         run[cc][k] = 0;
                     }
@@ -1058,7 +1067,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
 // R[i,j,a,b] += 2^(f_ab + g_ij - 42) J[(a,b), (i,j)] and the mirror R[j,i,b,a] for a < b.
 __global__ void finalize_kernel(const unsigned long long* __restrict__ rp, int npairs, int no, int nv,
                                 const int2* __restrict__ pairs, const int* __restrict__ f_tab,
-                                const int* __restrict__ t_exp, double* __restrict__ R) {
+                                const int* __restrict__ t_exp, double* __restrict__ R, unsigned* status) {
     const int no2 = no * no;
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= (long long)npairs * no2) return;
@@ -1067,8 +1076,9 @@ __global__ void finalize_kernel(const unsigned long long* __restrict__ rp, int n
     const long long J = (long long)rp[k];
     const double v = ldexp((double)J, f_tab[ab.x * nv + ab.y] + t_exp[n / kG] - 42);
     const int i = n / no, j = n % no;
-    R[(((size_t)i * no + j) * nv + ab.x) * nv + ab.y] += v;
-    if (ab.x < ab.y) R[(((size_t)j * no + i) * nv + ab.y) * nv + ab.x] += v;
+    const size_t x = (((size_t)i * no + j) * nv + ab.x) * nv + ab.y, y = (((size_t)j * no + i) * nv + ab.y) * nv + ab.x;
+    if (LADDER_IN_BOUNDS(x < (size_t)no2 * nv * nv, status)) R[x] += v;
+    if (ab.x < ab.y && LADDER_IN_BOUNDS(y < (size_t)no2 * nv * nv, status)) R[y] += v;
 }
 
 // ------------------------------------------------------------------ host side
@@ -1132,14 +1142,14 @@ cudaError_t prep_impl(const ladder_plan_s& p, const double* L, const double* t2,
     f_table_kernel<<<(unsigned)((nv2 + 255) / 256), 256, 0, s>>>(at<unsigned long long>(ws, p.ws.lnorm), p.nv,
                                                                    at<int>(ws, p.ws.v_exp));
     lt_slice_kernel<S><<<dim3((p.nchol + 63) / 64, (unsigned)((rows + 63) / 64)), 256, 0, s>>>(
-        L, p.nchol, p.nv, vp, xpad, at<int>(ws, p.ws.lt_exp), at<__nv_bfloat16>(ws, p.ws.lt_slices));
+        L, p.nchol, p.nv, vp, xpad, at<int>(ws, p.ws.lt_exp), at<__nv_bfloat16>(ws, p.ws.lt_slices), p.d_status);
     t_rowmax_kernel<<<dim3((unsigned)((nv2 + 8191) / 8192), no2), 256, 0, s>>>(t2, nv2, no2,
                                                                               at<unsigned long long>(ws, p.ws.t_gmax));
     exp_from_max_kernel<<<(ngt + 255) / 256, 256, 0, s>>>(at<unsigned long long>(ws, p.ws.t_gmax), ngt,
                                                            at<int>(ws, p.ws.t_exp));
     const long long units = (long long)(kpad / 8) * no2;
     t_slice_kernel<S><<<(unsigned)((units + 255) / 256), 256, 0, s>>>(t2, p.nv, vp, no2, kpad, at<int>(ws, p.ws.t_exp),
-                                                                      at<__nv_bfloat16>(ws, p.ws.t_slices));
+                                                                      at<__nv_bfloat16>(ws, p.ws.t_slices), p.d_status);
     return cudaGetLastError();
 }
 
@@ -1275,7 +1285,8 @@ cudaError_t block_impl(const ladder_plan_s& p, const BlockPair& bp, double* R, v
         const long long n = (long long)bp.npairs * no2;
         finalize_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(at<unsigned long long>(ws, p.ws.rp_int),
                                                                     bp.npairs, p.no, p.nv, table + bp.pairs_off,
-                                                                    at<int>(ws, p.ws.v_exp), at<int>(ws, p.ws.t_exp), R);
+                                                                    at<int>(ws, p.ws.v_exp), at<int>(ws, p.ws.t_exp), R,
+                                                                    p.d_status);
     }
     return cudaGetLastError();
 }
@@ -1345,7 +1356,7 @@ cudaError_t group_impl(const ladder_plan_s& parent, const ladder_plan_s* const* 
             finalize_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(
                 at<unsigned long long>(ws[k], p.ws.rp_int), bp.npairs, p.no, p.nv,
                 reinterpret_cast<const int2*>(p.d_tables) + bp.pairs_off, at<int>(ws[k], p.ws.v_exp),
-                at<int>(ws[k], p.ws.t_exp), R[k]);
+                at<int>(ws[k], p.ws.t_exp), R[k], parent.d_status);
         }
     }
     return cudaGetLastError();

@@ -10,6 +10,16 @@
 
 #include "../../include/ladder.h"
 
+// Index checks of a LADDER_CHECK build: a store whose index fails `cond` records
+// kStatusBounds in the status word and is skipped (no trap, no fault).  In a normal build the
+// condition is not evaluated.
+#ifdef LADDER_CHECK
+#define LADDER_IN_BOUNDS(cond, status) \
+    ((cond) ? true : (atomicOr((status), ::ladder::kStatusBounds), false))
+#else
+#define LADDER_IN_BOUNDS(cond, status) true
+#endif
+
 namespace ladder {
 
 constexpr int kAlign = 256;                 // workspace sub-buffer alignment (bytes)
@@ -23,6 +33,7 @@ constexpr int kEmuTileN = 96;               // widest tile N: 5 TMEM accumulator
 // Device status bits (ORed into the plan's status word by kernels).
 constexpr unsigned kStatusTimeout = 1u;
 constexpr unsigned kStatusNumeric = 2u;
+constexpr unsigned kStatusBounds = 4u;
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 

@@ -96,6 +96,12 @@ def test_graph_capture_and_replay_is_deterministic():
         assert rel_fro(R.cpu().numpy(), oracle.ladder(L, t)) <= 1e-10
 
 
+@pytest.fixture(autouse=True)
+def _release_cached_memory():
+    yield
+    torch.cuda.empty_cache()   # batched workspaces are large; later tests plan from free memory
+
+
 def test_uneven_24_instance_batch_sampled_parity():
     shapes = batched_shapes()
     assert len(shapes) == 24

@@ -173,7 +173,8 @@ def test_c3_planner_split_is_bitwise_identical():
     s = CONFIGS["c3"]
     L, t2, _, _ = make_inputs(s.no, s.nv, s.nchol, s.seed)
     R1, plan1 = gpu_ladder(L, t2, EMU)
-    budget = plan1.workspace_bytes() // 5
+    one_block = lad.ladder_plan_dry(s.no, s.nv, s.nchol, EMU, force_n_a=s.nv, force_n_b=s.nv)["ws_bytes"]
+    budget = one_block // 5
     Rb, planb = gpu_ladder(L, t2, EMU, budget=budget)
     d = planb.describe()
     assert d["n_block_pairs"] > 1 and planb.workspace_bytes() <= budget

@@ -52,6 +52,8 @@ def dev(x):
 def gpu_ladder(L, t2, precision=lad.LADDER_FP64, R0=None, blocks=None, budget=0, nslices=0):
     nchol, nv, _ = L.shape
     no = t2.shape[0]
+    # the default budget is a fraction of the free memory: hand torch's cached blocks back first
+    torch.cuda.empty_cache()
     plan = lad.ladder_plan(no, nv, nchol, precision, nslices=nslices, ws_budget_bytes=budget)
     if blocks is not None:
         plan.set_blocks(*blocks)
