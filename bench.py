@@ -47,8 +47,8 @@ NOMINAL_FP64_TFLOPS = 1.25
 # sources hash to the value recorded with the capture; any change to them makes it null.
 TRAFFIC_CAPTURES = {
     # (precision, workload): (sources sha256 prefix, bytes per launch, profiles/ summary)
-    ("emu", "c2"): ("ef2020608cb80f21", 8694602752 + 11763489024, "profiles/dram_traffic_no10_nv200_nchol630.md"),
-    ("fp64", "c2"): ("ef2020608cb80f21", 49780009216 + 6437039104, "profiles/dram_traffic_no10_nv200_nchol630.md"),
+    ("emu", "c2"): ("20e7275c739538cd", 9759341568 + 12133569024, "profiles/dram_traffic_no10_nv200_nchol630.md"),
+    ("fp64", "c2"): ("20e7275c739538cd", 49997810432 + 6438575104, "profiles/dram_traffic_no10_nv200_nchol630.md"),
 }
 KERNEL_SOURCE_DIR = os.path.join(ROOT, "paper_2603_20912_gb300", "csrc")
 
