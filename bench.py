@@ -369,6 +369,8 @@ def main():
     ap.add_argument("--shape", default=None, help="no,nv,nchol overriding --config (profiling runs)")
     ap.add_argument("--precision", default="emu", choices=["emu", "fp64"])
     ap.add_argument("--nslices", type=int, default=0)
+    ap.add_argument("--form", default="auto", choices=["auto", "plain", "pm"],
+                    help="emulated ladder form: the planner's choice, plain, or the symmetric/antisymmetric split")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -420,6 +422,9 @@ def main():
     torch.cuda.synchronize()
     plan = lad.ladder_plan(cfg.no, cfg.nv, cfg.nchol, precision, nslices=args.nslices,
                            ws_budget_bytes=int(args.budget_gb * 1e9), device=local)
+    if args.form != "auto":
+        plan.set_form(1 if args.form == "pm" else 0)
+    form_used = "pm" if plan.form() == 1 else "plain"
     ws = plan.workspace()
     desc = plan.describe()
     stream = torch.cuda.current_stream()
@@ -532,7 +537,8 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
             "config": {"workload": f"{cfg.name}: no={cfg.no} nv={cfg.nv} nchol={cfg.nchol} seed={cfg.seed}",
-                       "precision": args.precision, "nslices": desc["nslices"], "n_a": desc["n_a"],
+                       "precision": args.precision, "form": form_used, "nslices": desc["nslices"],
+                       "n_a": desc["n_a"],
                        "n_b": desc["n_b"], "block_pairs": desc["n_block_pairs"],
                        "l2": "inputs+workspace > L2 (V block written and re-read every step)",
                        "parallelism": f"independent instance per GPU x{world}"},

@@ -98,6 +98,28 @@ int ladder_plan(ladder_plan_t* out, int no, int nv, int nchol, int precision, in
 int ladder_plan_set_blocks(ladder_plan_t plan, int n_a, int n_b);
 
 /*
+ * ladder_plan_set_form -- arithmetic form of the emulated ladder GEMM of a plan.
+ *   0 (default): K = (c,d) over all c, d and rows = all (i,j), as in Eq. vfunction-chol.
+ *   1: symmetric/antisymmetric split.  With t_ij^cd = t_ji^dc the sum is taken over
+ *      c <= d only, as X_ij^ab = sum_{c<=d} V'_ab,cd T'_ij,cd (i <= j) and
+ *      Y_ij^ab = sum_{c<d} V''_ab,cd T''_ij,cd (i < j), with V' = V_cd + V_dc (V_cc on the
+ *      diagonal), V'' = V_cd - V_dc, T' = (T_ij,cd + T_ji,cd)/2 (T_ij,cc), T'' = (T_ij,cd -
+ *      T_ji,cd)/2, and R_ij^ab += X + Y, R_ji^ab += X - Y: half the multiply-adds of the
+ *      ladder GEMM, for one extra pass over the V digit planes of each block pair and V', V''
+ *      workspace about as large as the V planes (V' and V'' are re-sliced with the pair's
+ *      exponent bound plus one, one rounding of half a unit).  This split is not in the paper.
+ * The blocking is kept if its workspace still fits the plan's budget, else chosen again.
+ * Call before querying the workspace.  Returns LADDER_OK, LADDER_ERR_ARG (batched plan or a
+ * form other than 0, 1), LADDER_ERR_UNSUPPORTED (form 1 on the FP64 path), LADDER_ERR_BUDGET
+ * or LADDER_ERR_CUDA.
+ */
+int ladder_plan_set_form(ladder_plan_t plan, int form);
+/* The form a plan uses: ladder_plan picks 1 on the emulated path when a cost model over the
+ * tile-padded ladder rows and the extra pass over V gives it a 5 % lead (large no^2 with
+ * respect to the 128/256-row MMA tiles) and the workspace fits, else 0.  -1 for NULL. */
+int ladder_plan_get_form(ladder_plan_t plan);
+
+/*
  * Data-parallel sharding over several GPUs (the multi-GPU direction named in
  * Sec. "Conclusions and outlook"; the sharding itself is this library's).
  * The (A,B) block pairs of one contraction are independent: each writes the

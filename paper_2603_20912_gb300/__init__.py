@@ -61,6 +61,12 @@ def _load():
     pint = ctypes.POINTER(ci)
     lib.ladder_plan.argtypes = [ctypes.POINTER(vp), ci, ci, ci, ci, ci, sz, ci]
     lib.ladder_plan.restype = ci
+    lib.ladder_plan_set_form.argtypes = [vp, ci]
+    lib.ladder_plan_set_form.restype = ci
+    lib.ladder_plan_get_form.argtypes = [vp]
+    lib.ladder_plan_get_form.restype = ci
+    lib.ladder_batched_schedule.argtypes = [vp, ci, pint]
+    lib.ladder_batched_schedule.restype = ci
     lib.ladder_watchdog_selftest.argtypes = [ctypes.POINTER(ctypes.c_double), vp]
     lib.ladder_watchdog_selftest.restype = ci
     lib.ladder_plan_shard.argtypes = [vp, ci, ci]
@@ -169,6 +175,13 @@ class Plan:
 
     def set_blocks(self, n_a: int, n_b: int):
         _check(_load().ladder_plan_set_blocks(self._h, int(n_a), int(n_b)), "ladder_plan_set_blocks")
+
+    def form(self) -> int:
+        return int(_load().ladder_plan_get_form(self._h))
+
+    def set_form(self, form: int):
+        """Emulated ladder form: 0 plain, 1 symmetric/antisymmetric (see ladder_plan_set_form)."""
+        _check(_load().ladder_plan_set_form(self._h, int(form)), "ladder_plan_set_form")
 
     def shard(self, rank: int, world: int):
         """Keep only the block pairs rank `rank` of `world` owns (see ladder_plan_shard)."""
@@ -342,5 +355,5 @@ EXPORTED_SYMBOLS = [
     "ladder_energy", "ladder_plan_batched", "ladder_apply_batched", "ladder_last_status", "ladder_plan_destroy",
     "ladder_strerror", "ladder_flops", "ladder_plan_dry", "ladder_plan_set_timing", "ladder_plan_timing",
     "ladder_energy_noalloc", "ladder_tune_batched", "ladder_plan_shard", "ladder_shard_blocks",
-    "ladder_watchdog_selftest", "ladder_batched_schedule",
+    "ladder_watchdog_selftest", "ladder_batched_schedule", "ladder_plan_set_form", "ladder_plan_get_form",
 ]

@@ -113,13 +113,28 @@ ladder::WsLayout layout_for(const ladder_plan_s& p, long long max_pairs) {
         const size_t S = p.nslices;
         const size_t vp = align_up((size_t)p.nv, 8), nvp = (size_t)p.nv * vp;
         const size_t kpad = nvp, xpad = align_up((size_t)p.nchol, 8);
+        const size_t G = ladder::kExpGroupRows;
         w.v_blk = take(S * (size_t)max_pairs * kpad * 2);
-        w.rp_int = take((size_t)max_pairs * no2 * 8);
         w.lt_slices = take(S * nvp * xpad * 2);
-        w.lt_exp = take(((nvp + ladder::kExpGroupRows - 1) / ladder::kExpGroupRows) * 4);
-        w.t_slices = take(S * no2 * kpad * 2);
-        w.t_gmax = take(((no2 + ladder::kExpGroupRows - 1) / ladder::kExpGroupRows) * 8);
-        w.t_exp = take(((no2 + ladder::kExpGroupRows - 1) / ladder::kExpGroupRows) * 4);
+        w.lt_exp = take(((nvp + G - 1) / G) * 4);
+        if (p.form == 0) {
+            w.rp_int = take((size_t)max_pairs * no2 * 8);
+            w.t_slices = take(S * no2 * kpad * 2);
+            w.t_gmax = take(((no2 + G - 1) / G) * 8);
+            w.t_exp = take(((no2 + G - 1) / G) * 4);
+        } else {
+            const ladder::PmDims d = ladder::pm_dims(p.no, p.nv);
+            w.vp_blk = take(S * (size_t)max_pairs * d.kp_pad * 2);
+            w.vm_blk = take(S * (size_t)max_pairs * d.km_pad * 2);
+            w.tp_slices = take(S * (size_t)d.np * d.kp_pad * 2);
+            w.tm_slices = take(S * (size_t)d.nm * d.km_pad * 2);
+            w.tp_gmax = take(((d.np + G - 1) / G) * 8);
+            w.tm_gmax = take(((d.nm + G - 1) / G) * 8);
+            w.tp_exp = take(((d.np + G - 1) / G) * 4);
+            w.tm_exp = take(((d.nm + G - 1) / G) * 4);
+            w.rpx = take((size_t)max_pairs * d.np * 8);
+            w.rpy = take((size_t)max_pairs * d.nm * 8);
+        }
         w.v_exp = take(nv2 * 4);
         w.lnorm = take((size_t)p.nv * 8);
         w.lsq = take(nv2 * 8);
@@ -334,6 +349,24 @@ struct DeviceGuard {
     }
 };
 
+// Emulated ladder form from a cost model over all a <= b pairs: the ladder GEMM's MMA rows are
+// padded to its tiles (128 rows on one SM up to 128 (i,j) rows, else 256 on CTA pairs), the
+// symmetric/antisymmetric form halves K and splits the rows into i <= j and i < j, and pays one
+// pass over the V digit planes (read and write, ~2.8 TB/s measured).  The split is chosen when
+// the model gives it a 5 % lead.
+int auto_form(int no, int nv, int nslices) {
+    const double pairs = 0.5 * nv * (nv + 1.0);
+    auto rows_pad = [](double r) { return r <= ladder::kEmuTile ? ladder::kEmuTile : std::ceil(r / 256.0) * 256.0; };
+    const double vp = std::ceil(nv / 8.0) * 8.0;
+    const double per_row_k = pairs * 2.0 * nslices * (nslices + 1) / 2 / 1.3e15;   // s per (row, K element)
+    const double plain = rows_pad((double)no * no) * nv * vp * per_row_k;
+    const ladder::PmDims d = ladder::pm_dims(no, nv);
+    double pm = rows_pad(d.np) * (double)d.kp * per_row_k;
+    if (d.nm > 0) pm += rows_pad(d.nm) * (double)d.km * per_row_k;
+    pm += 2.0 * (nslices * 2.0 * pairs * nv * vp) / 2.8e12;   // read and write the V digit planes
+    return pm < 0.95 * plain ? 1 : 0;
+}
+
 int make_plan(ladder_plan_s** out, int no, int nv, int nchol, int precision, int nslices, size_t budget,
               int device) {
     *out = nullptr;
@@ -380,7 +413,12 @@ int make_plan(ladder_plan_s** out, int no, int nv, int nchol, int precision, int
         p->eri_clusters = ladder::emu_max_clusters(nslices, 0);
         p->pair_clusters = ladder::emu_max_clusters(nslices, 1);
     }
+    p->form = precision == LADDER_FP64 ? 0 : auto_form(no, nv, p->nslices);
     int rc = choose_blocking(*p);
+    if (rc == LADDER_ERR_BUDGET && p->form == 1) {   // the split needs more workspace: fall back
+        p->form = 0;
+        rc = choose_blocking(*p);
+    }
     if (rc == LADDER_OK) {
         if (cudaMalloc(&p->d_status, sizeof(unsigned)) != cudaSuccess ||
             cudaMemset(p->d_status, 0, sizeof(unsigned)) != cudaSuccess)
@@ -420,7 +458,7 @@ void schedule_batched(ladder_plan_s& p, int k) {
 }
 
 // An instance can join a group when it runs on the emulated path as a single block pair.
-bool groupable(const ladder_plan_s& s) { return s.precision != LADDER_FP64 && s.bps.size() == 1; }
+bool groupable(const ladder_plan_s& s) { return s.precision != LADDER_FP64 && s.form == 0 && s.bps.size() == 1; }
 
 // Grouped schedule: first-fit decreasing of the instances' workspaces into groups of at most
 // `cap` bytes and emu_max_group() instances (an instance that cannot be grouped runs alone),
@@ -546,6 +584,26 @@ int ladder_plan_shard(ladder_plan_t plan, int rank, int world) {
     plan->shard_world = world;
     return build_tables(*plan);
 }
+
+int ladder_plan_set_form(ladder_plan_t plan, int form) {
+    if (!plan || plan->batched || (form != 0 && form != 1)) return LADDER_ERR_ARG;
+    if (form == 1 && plan->precision == LADDER_FP64) return LADDER_ERR_UNSUPPORTED;
+    if (form == plan->form) return LADDER_OK;
+    DeviceGuard guard(plan->device);
+    if (!guard.ok) return LADDER_ERR_CUDA;
+    const int old = plan->form;
+    plan->form = form;
+    // keep the blocking when it still fits, else choose again under the same budget
+    int rc = apply_blocking(*plan, plan->n_a, plan->n_b);
+    if (rc == LADDER_ERR_BUDGET) rc = choose_blocking(*plan);
+    if (rc != LADDER_OK) {
+        plan->form = old;
+        apply_blocking(*plan, plan->n_a, plan->n_b);
+    }
+    return rc;
+}
+
+int ladder_plan_get_form(ladder_plan_t plan) { return plan ? plan->form : -1; }
 
 size_t ladder_workspace_bytes(ladder_plan_t plan) {
     if (!plan) return 0;
@@ -896,9 +954,14 @@ int ladder_plan_dry(int no, int nv, int nchol, int precision, int nslices, size_
     p.nslices = precision == LADDER_FP64 ? 0 : nslices;
     p.num_sms = num_sms;
     p.budget = ws_budget_bytes;
+    p.form = precision == LADDER_FP64 ? 0 : auto_form(no, nv, nslices);
     int na = force_n_a, nb = force_n_b;
     if (na <= 0 || nb <= 0) {
-        const int rc = select_blocking(p, &na, &nb);
+        int rc = select_blocking(p, &na, &nb);
+        if (rc == LADDER_ERR_BUDGET && p.form == 1) {
+            p.form = 0;
+            rc = select_blocking(p, &na, &nb);
+        }
         if (rc != LADDER_OK) return rc;
     } else if (na > nv || nb > nv) {
         return LADDER_ERR_ARG;

@@ -362,6 +362,202 @@ __global__ void __launch_bounds__(256) t_slice_kernel(const double* __restrict__
             *reinterpret_cast<uint4*>(planes + s * plane + (size_t)row * kpad + k0) = *reinterpret_cast<uint4*>(out[s]);
 }
 
+// ------------------------------------------------------------------ symmetric/antisymmetric form
+// With t_ij^cd = t_ji^dc the ladder splits into a part symmetric and a part antisymmetric in
+// (i,j), each over c <= d only:
+//   X_ij^ab = sum_{c<=d} V'_ab,cd T'_ij,cd   (i <= j),  V' = V_cd + V_dc (c < d), V_cc (c = d),
+//                                                        T' = (T_ij,cd + T_ji,cd) / 2 (c < d), T_ij,cc
+//   Y_ij^ab = sum_{c<d}  V''_ab,cd T''_ij,cd  (i < j),  V'' = V_cd - V_dc, T'' = (T_ij,cd - T_ji,cd) / 2
+//   R_ij^ab = X + Y,  R_ji^ab = X - Y,
+// half the multiply-adds of the plain ladder.  K' and the rows (i <= j) are packed row-major:
+// k'(c,d) = c nv - c(c-1)/2 + (d - c), r(i,j) = i no - i(i-1)/2 + (j - i); K'' and the rows
+// (i < j) the same without the diagonal.
+
+// (i, j) of packed row r of the upper triangle of an n x n grid (diag: with the diagonal).
+__device__ __forceinline__ void tri_unpack(int r, int n, bool diag, int* i, int* j) {
+    int a = 0, len = diag ? n : n - 1;
+    while (r >= len && len > 0) {
+        r -= len;
+        ++a;
+        --len;
+    }
+    *i = a;
+    *j = a + r + (diag ? 0 : 1);
+}
+
+__device__ __forceinline__ long long tri_off(int c, int n, bool diag) {  // first packed index of row c
+    return diag ? (long long)c * n - (long long)c * (c - 1) / 2 : (long long)c * (n - 1) - (long long)c * (c - 1) / 2;
+}
+
+// One block per packed row of T' (r < np) or T'' (r >= np): max |value| into its 64-row group.
+__global__ void __launch_bounds__(256) tpm_rowmax_kernel(const double* __restrict__ t2, int no, int nv, int np,
+                                                         unsigned long long* __restrict__ gmax_p,
+                                                         unsigned long long* __restrict__ gmax_m) {
+    __shared__ int si, sj;
+    const bool plus = (int)blockIdx.x < np;
+    const int r = plus ? (int)blockIdx.x : (int)blockIdx.x - np;
+    if (threadIdx.x == 0) tri_unpack(r, no, plus, &si, &sj);
+    __syncthreads();
+    const int i = si, j = sj;
+    const long long nv2 = (long long)nv * nv;
+    const double* tij = t2 + ((size_t)i * no + j) * nv2;
+    const double* tji = t2 + ((size_t)j * no + i) * nv2;
+    double m = 0.0;
+    for (long long f = threadIdx.x; f < nv2; f += blockDim.x) {
+        const int c = (int)(f / nv), d = (int)(f % nv);
+        if (c > d || (!plus && c == d)) continue;
+        const double a = __ldg(tij + f), b = __ldg(tji + f);
+        const double v = plus ? (c == d ? a : 0.5 * (a + b)) : 0.5 * (a - b);
+        m = fmax(m, fabs(v));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0.0)
+        atomicMax((plus ? gmax_p : gmax_m) + r / kG, (unsigned long long)__double_as_longlong(m));
+}
+
+// T' and T'' digit planes: one block per packed row, threads over the rows c of its (c,d) triangle.
+template <int S>
+__global__ void __launch_bounds__(128) tpm_slice_kernel(const double* __restrict__ t2, int no, int nv, int np,
+                                                        long long kp_pad, long long km_pad, int nm,
+                                                        const int* __restrict__ e_p, const int* __restrict__ e_m,
+                                                        __nv_bfloat16* __restrict__ tp, __nv_bfloat16* __restrict__ tm,
+                                                        unsigned* status) {
+    __shared__ int si, sj;
+    const bool plus = (int)blockIdx.x < np;
+    const int r = plus ? (int)blockIdx.x : (int)blockIdx.x - np;
+    if (threadIdx.x == 0) tri_unpack(r, no, plus, &si, &sj);
+    __syncthreads();
+    const int i = si, j = sj;
+    const long long nv2 = (long long)nv * nv;
+    const double* tij = t2 + ((size_t)i * no + j) * nv2;
+    const double* tji = t2 + ((size_t)j * no + i) * nv2;
+    const int e = plus ? e_p[r / kG] : e_m[r / kG];
+    const long long kpad = plus ? kp_pad : km_pad;
+    const size_t plane = (size_t)(plus ? np : nm) * kpad;
+    __nv_bfloat16* out = (plus ? tp : tm) + (size_t)r * kpad;
+    for (int c = threadIdx.x; c < nv; c += blockDim.x) {
+        const long long k0 = tri_off(c, nv, plus);
+        for (int d = plus ? c : c + 1; d < nv; ++d) {
+            const double a = __ldg(tij + (size_t)c * nv + d), b = __ldg(tji + (size_t)c * nv + d);
+            const double v = plus ? (c == d ? a : 0.5 * (a + b)) : 0.5 * (a - b);
+            __nv_bfloat16 dg[S];
+            digits_of<S>(scaled_rint(v, 7 * S - e), dg);
+            const long long k = k0 + (d - c - (plus ? 0 : 1));
+            if (!LADDER_IN_BOUNDS((size_t)r * kpad + k < plane, status)) continue;
+#pragma unroll
+            for (int s = 0; s < S; ++s) out[s * plane + k] = dg[s];
+        }
+    }
+}
+
+struct CombineArgs {
+    int nv, vp, npairs, ntile;        // ntile = 32-wide tiles per (c or d) axis
+    size_t vplane, pplane, mplane;    // element strides between planes of V, V', V''
+    long long kpad, kp_pad, km_pad;   // row strides of V, V', V''
+    const __nv_bfloat16* v;
+    __nv_bfloat16* vp_out;
+    __nv_bfloat16* vm_out;
+    unsigned* status;
+};
+
+// V' and V'' of every pair row of a block from its V digit planes, on the grid of exponent
+// f_ab + 1: N' = round((N_cd + N_dc) / 2) (c < d) or round(N_cc / 2), N'' = round((N_cd - N_dc) / 2),
+// halves rounded up, so |N'|, |N''| <= 2^(7S-1) and the digits stay within +-64.  One block per
+// (pair row, 32x32 tile of (c,d) with c-tile <= d-tile); both the tile and its transpose pass
+// through shared memory so that every global access is a row segment.
+template <int S>
+__global__ void __launch_bounds__(256) vpm_combine_kernel(CombineArgs p) {
+    __shared__ __nv_bfloat16 ta[S][32][33], tb[S][32][33];   // ta[s][c][d] = V(c,d), tb[s][d][c] = V(d,c)
+    const long long ntp = (long long)p.ntile * (p.ntile + 1) / 2;
+    const long long blk = blockIdx.x;
+    const int row = (int)(blk / ntp);
+    int tc, td;
+    tri_unpack((int)(blk % ntp), p.ntile, true, &tc, &td);
+    const int c0 = tc * 32, d0 = td * 32;
+    const __nv_bfloat16 zero = __float2bfloat16_rn(0.0f);
+    // 16-byte loads: 8 consecutive columns of one (c or d) row segment per thread and plane
+    // (vp % 8 == 0 keeps every segment aligned; the pad columns up to vp hold zeros).
+    for (int t = threadIdx.x; t < 2 * S * 32 * 4; t += blockDim.x) {
+        const int q = t & 3, u = (t >> 2) & 31, s2 = (t >> 7) % S, which = t / (128 * S);
+        const int rr = (which == 0 ? c0 : d0) + u, col0 = (which == 0 ? d0 : c0) + 8 * q;
+        __nv_bfloat16 (*dst)[33] = which == 0 ? ta[s2] : tb[s2];
+        const __nv_bfloat16* src = p.v + s2 * p.vplane + (size_t)row * p.kpad + (size_t)rr * p.vp + col0;
+        if (rr < p.nv && col0 + 8 <= p.vp) {
+            const uint4 x = *reinterpret_cast<const uint4*>(src);
+            const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(&x);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) dst[u][8 * q + k] = h[k];
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) dst[u][8 * q + k] = (rr < p.nv && col0 + k < p.nv) ? src[k] : zero;
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
+        const int u = t >> 5, w = t & 31;
+        const int c = c0 + u, d = d0 + w;
+        if (c >= p.nv || d >= p.nv || c > d) continue;
+        long long ncd = 0, ndc = 0;
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            const float sc = pow2f(7 * (s + 1));
+            ncd = ncd * 128 + (long long)__float2int_rn(__bfloat162float(ta[s][u][w]) * sc);
+            ndc = ndc * 128 + (long long)__float2int_rn(__bfloat162float(tb[s][w][u]) * sc);
+        }
+        __nv_bfloat16 dg[S];
+        const long long kp = tri_off(c, p.nv, true) + (d - c);
+        const long long np_ = (c < d ? ncd + ndc : ncd) + 1;
+        digits_of<S>(np_ >> 1, dg);
+        if (LADDER_IN_BOUNDS((size_t)row * p.kp_pad + kp < p.pplane, p.status))
+#pragma unroll
+            for (int s = 0; s < S; ++s) p.vp_out[s * p.pplane + (size_t)row * p.kp_pad + kp] = dg[s];
+        if (c < d) {
+            const long long km = tri_off(c, p.nv, false) + (d - c - 1);
+            digits_of<S>((ncd - ndc + 1) >> 1, dg);
+            if (LADDER_IN_BOUNDS((size_t)row * p.km_pad + km < p.mplane, p.status))
+#pragma unroll
+                for (int s = 0; s < S; ++s) p.vm_out[s * p.mplane + (size_t)row * p.km_pad + km] = dg[s];
+        }
+    }
+}
+
+// R from X (rows i <= j) and Y (rows i < j) of one block pair: R_ij^ab += X + Y, R_ji^ab += X - Y,
+// and the mirrors R_ji^ba = R_ij^ab, R_ij^ba = R_ji^ab for a < b.  Grid: x over pairs, y over rows.
+__global__ void __launch_bounds__(256) finalize_pm_kernel(const unsigned long long* __restrict__ rpx,
+                                                          const unsigned long long* __restrict__ rpy, int npairs,
+                                                          int no, int nv, int np, int nm,
+                                                          const int2* __restrict__ pairs,
+                                                          const int* __restrict__ f_tab,
+                                                          const int* __restrict__ e_p, const int* __restrict__ e_m,
+                                                          double* __restrict__ R, unsigned* status) {
+    __shared__ int si, sj;
+    const size_t total = (size_t)no * no * nv * nv;
+    (void)total;
+    for (int r = blockIdx.y; r < np; r += gridDim.y) {
+        __syncthreads();
+        if (threadIdx.x == 0) tri_unpack(r, no, true, &si, &sj);
+        __syncthreads();
+        const int i = si, j = sj;
+        const int r2 = r - (i + 1);   // (i, j) among the rows with i < j
+        for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < npairs; m += gridDim.x * blockDim.x) {
+            const int2 ab = pairs[m];
+            const int f = f_tab[ab.x * nv + ab.y] + 1;
+            const double X = ldexp((double)(long long)rpx[(size_t)m * np + r], f + e_p[r / kG] - 42);
+            const double Y = i < j ? ldexp((double)(long long)rpy[(size_t)m * nm + r2], f + e_m[r2 / kG] - 42) : 0.0;
+            const size_t ij_ab = (((size_t)i * no + j) * nv + ab.x) * nv + ab.y;
+            const size_t ji_ab = (((size_t)j * no + i) * nv + ab.x) * nv + ab.y;
+            const size_t ji_ba = (((size_t)j * no + i) * nv + ab.y) * nv + ab.x;
+            const size_t ij_ba = (((size_t)i * no + j) * nv + ab.y) * nv + ab.x;
+            if (LADDER_IN_BOUNDS(ij_ab < total, status)) R[ij_ab] += X + Y;
+            if (i < j && LADDER_IN_BOUNDS(ji_ab < total, status)) R[ji_ab] += X - Y;
+            if (ab.x < ab.y) {
+                if (LADDER_IN_BOUNDS(ji_ba < total, status)) R[ji_ba] += X + Y;
+                if (i < j && LADDER_IN_BOUNDS(ij_ba < total, status)) R[ij_ba] += X - Y;
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------------------ shared tcgen05 pieces
 struct Ring {
     int stage = 0;
@@ -1135,7 +1331,8 @@ cudaError_t prep_impl(const ladder_plan_s& p, const double* L, const double* t2,
     LaunchTimer tm(p, s, LADDER_KERNEL_PREP, 6);
     cudaError_t e;
     if ((e = cudaMemsetAsync(at<char>(ws, p.ws.lnorm), 0, (size_t)p.nv * 8, s)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(at<char>(ws, p.ws.t_gmax), 0, (size_t)ngt * 8, s)) != cudaSuccess) return e;
+    if (p.form == 0 && (e = cudaMemsetAsync(at<char>(ws, p.ws.t_gmax), 0, (size_t)ngt * 8, s)) != cudaSuccess)
+        return e;
     lt_rowstats_kernel<<<(unsigned)((rows + kG - 1) / kG), kG, 0, s>>>(L, p.nchol, p.nv, vp, at<int>(ws, p.ws.lt_exp),
                                                                         at<unsigned long long>(ws, p.ws.lnorm),
                                                                         at<double>(ws, p.ws.lsq));
@@ -1143,13 +1340,32 @@ cudaError_t prep_impl(const ladder_plan_s& p, const double* L, const double* t2,
                                                                    at<int>(ws, p.ws.v_exp));
     lt_slice_kernel<S><<<dim3((p.nchol + 63) / 64, (unsigned)((rows + 63) / 64)), 256, 0, s>>>(
         L, p.nchol, p.nv, vp, xpad, at<int>(ws, p.ws.lt_exp), at<__nv_bfloat16>(ws, p.ws.lt_slices), p.d_status);
-    t_rowmax_kernel<<<dim3((unsigned)((nv2 + 8191) / 8192), no2), 256, 0, s>>>(t2, nv2, no2,
-                                                                              at<unsigned long long>(ws, p.ws.t_gmax));
-    exp_from_max_kernel<<<(ngt + 255) / 256, 256, 0, s>>>(at<unsigned long long>(ws, p.ws.t_gmax), ngt,
-                                                           at<int>(ws, p.ws.t_exp));
-    const long long units = (long long)(kpad / 8) * no2;
-    t_slice_kernel<S><<<(unsigned)((units + 255) / 256), 256, 0, s>>>(t2, p.nv, vp, no2, kpad, at<int>(ws, p.ws.t_exp),
-                                                                      at<__nv_bfloat16>(ws, p.ws.t_slices), p.d_status);
+    if (p.form == 0) {
+        t_rowmax_kernel<<<dim3((unsigned)((nv2 + 8191) / 8192), no2), 256, 0, s>>>(
+            t2, nv2, no2, at<unsigned long long>(ws, p.ws.t_gmax));
+        exp_from_max_kernel<<<(ngt + 255) / 256, 256, 0, s>>>(at<unsigned long long>(ws, p.ws.t_gmax), ngt,
+                                                               at<int>(ws, p.ws.t_exp));
+        const long long units = (long long)(kpad / 8) * no2;
+        t_slice_kernel<S><<<(unsigned)((units + 255) / 256), 256, 0, s>>>(
+            t2, p.nv, vp, no2, kpad, at<int>(ws, p.ws.t_exp), at<__nv_bfloat16>(ws, p.ws.t_slices), p.d_status);
+        return cudaGetLastError();
+    }
+    // symmetric/antisymmetric form: T' (rows i <= j, c <= d) and T'' (rows i < j, c < d)
+    const PmDims d = pm_dims(p.no, p.nv);
+    const int ngp = (d.np + kG - 1) / kG, ngm = (d.nm + kG - 1) / kG;
+    if ((e = cudaMemsetAsync(at<char>(ws, p.ws.tp_gmax), 0, (size_t)ngp * 8, s)) != cudaSuccess) return e;
+    if (ngm > 0 && (e = cudaMemsetAsync(at<char>(ws, p.ws.tm_gmax), 0, (size_t)ngm * 8, s)) != cudaSuccess) return e;
+    tpm_rowmax_kernel<<<(unsigned)(d.np + d.nm), 256, 0, s>>>(t2, p.no, p.nv, d.np,
+                                                                at<unsigned long long>(ws, p.ws.tp_gmax),
+                                                                at<unsigned long long>(ws, p.ws.tm_gmax));
+    exp_from_max_kernel<<<(ngp + 255) / 256, 256, 0, s>>>(at<unsigned long long>(ws, p.ws.tp_gmax), ngp,
+                                                           at<int>(ws, p.ws.tp_exp));
+    if (ngm > 0)
+        exp_from_max_kernel<<<(ngm + 255) / 256, 256, 0, s>>>(at<unsigned long long>(ws, p.ws.tm_gmax), ngm,
+                                                               at<int>(ws, p.ws.tm_exp));
+    tpm_slice_kernel<S><<<(unsigned)(d.np + d.nm), 128, 0, s>>>(
+        t2, p.no, p.nv, d.np, d.kp_pad, d.km_pad, d.nm, at<int>(ws, p.ws.tp_exp), at<int>(ws, p.ws.tm_exp),
+        at<__nv_bfloat16>(ws, p.ws.tp_slices), at<__nv_bfloat16>(ws, p.ws.tm_slices), p.d_status);
     return cudaGetLastError();
 }
 
@@ -1245,8 +1461,95 @@ void launch_ladder_batch(const LadBatch& lb, bool on_pairs, int max_pair_cluster
     }
 }
 
+// Ladder work item X (plus) or Y (minus) of the symmetric/antisymmetric form of one block pair.
+template <int S>
+bool ladder_item_pm(const ladder_plan_s& p, const BlockPair& bp, void* ws, long long ubeg, bool plus, LadItem* it,
+                    CUtensorMap* ta, CUtensorMap* tb) {
+    constexpr int BK = bk_for(S);
+    const PmDims d = pm_dims(p.no, p.nv);
+    const int rows = plus ? d.np : d.nm;
+    const long long K = plus ? d.kp : d.km, kpad = plus ? d.kp_pad : d.km_pad;
+    const bool pair = rows > kEmuTile;
+    if (!make_tmap(ta, at<char>(ws, plus ? p.ws.tp_slices : p.ws.tm_slices), K, rows, S, (uint64_t)kpad * 2,
+                   (uint64_t)rows * kpad * 2, BK, kEmuTile) ||
+        !make_tmap(tb, at<char>(ws, plus ? p.ws.vp_blk : p.ws.vm_blk), K, bp.npairs, S, (uint64_t)kpad * 2,
+                   (uint64_t)p.max_pairs * kpad * 2, BK, pair ? kEmuTileN / 2 : kEmuTileN))
+        return false;
+    LadItem x{};
+    x.swap = 1;
+    x.no2 = rows;
+    x.M = rows;
+    x.N = bp.npairs;
+    x.n_mt = (rows + (pair ? 2 : 1) * kEmuTile - 1) / ((pair ? 2 : 1) * kEmuTile);
+    x.n_nt = (x.N + kEmuTileN - 1) / kEmuTileN;
+    x.nkb = (int)((K + BK - 1) / BK);
+    x.kb_per_chunk = kEmuChunkK / BK;
+    x.n_ch = (x.nkb + x.kb_per_chunk - 1) / x.kb_per_chunk;
+    x.units = (long long)x.n_mt * x.n_nt * x.n_ch;
+    x.ubeg = ubeg;
+    x.rp = at<unsigned long long>(ws, plus ? p.ws.rpx : p.ws.rpy);
+    *it = x;
+    return true;
+}
+
+// One block pair in the symmetric/antisymmetric form: ERI and self-product entries as in the
+// plain form, V -> V', V'', the X and Y ladders, and the four-way finalisation.
+template <int S>
+cudaError_t block_pm_impl(const ladder_plan_s& p, const BlockPair& bp, double* R, void* ws, cudaStream_t s) {
+    const PmDims d = pm_dims(p.no, p.nv);
+    const bool has_y = d.nm > 0 && d.km > 0;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(at<char>(ws, p.ws.rpx), 0, (size_t)bp.npairs * d.np * 8, s)) != cudaSuccess) return e;
+    if (has_y && (e = cudaMemsetAsync(at<char>(ws, p.ws.rpy), 0, (size_t)bp.npairs * d.nm * 8, s)) != cudaSuccess)
+        return e;
+    const int2* table = reinterpret_cast<const int2*>(p.d_tables);
+    EriBatch eb{};
+    eb.nitems = 1;
+    eb.nentries = bp.ntiles;
+    eb.entries = reinterpret_cast<const int4*>(table + bp.tiles_off);
+    eb.status = p.d_status;
+    if (!eri_item<S>(p, bp, ws, &eb.item[0], &eb.ta[0], &eb.tb[0])) return cudaErrorInvalidValue;
+    const int vp = padded_vp(p.nv);
+    {
+        LaunchTimer tm(p, s, LADDER_KERNEL_ERI, 3);
+        launch_eri_batch<S>(eb, p.eri_clusters > 0 ? p.eri_clusters : p.num_sms / 2, s);
+        launch_self<S>(p, bp, ws, s);
+        CombineArgs ca{p.nv, vp, bp.npairs, (p.nv + 31) / 32, (size_t)p.max_pairs * p.nv * vp,
+                       (size_t)p.max_pairs * d.kp_pad, (size_t)p.max_pairs * d.km_pad, (long long)p.nv * vp,
+                       d.kp_pad, d.km_pad, at<__nv_bfloat16>(ws, p.ws.v_blk), at<__nv_bfloat16>(ws, p.ws.vp_blk),
+                       at<__nv_bfloat16>(ws, p.ws.vm_blk), p.d_status};
+        const long long blocks = (long long)bp.npairs * ca.ntile * (ca.ntile + 1) / 2;
+        vpm_combine_kernel<S><<<(unsigned)blocks, 256, 0, s>>>(ca);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int fit = p.pair_clusters > 0 ? p.pair_clusters : p.num_sms / 2;
+    for (int part = 0; part < (has_y ? 2 : 1); ++part) {
+        LadBatch lb{};
+        lb.nitems = 1;
+        lb.BN = kEmuTileN;
+        lb.status = p.d_status;
+        if (!ladder_item_pm<S>(p, bp, ws, 0, part == 0, &lb.item[0], &lb.ta[0], &lb.tb[0]))
+            return cudaErrorInvalidValue;
+        lb.units = lb.item[0].units;
+        LaunchTimer tm(p, s, LADDER_KERNEL_LADDER);
+        launch_ladder_batch<S>(lb, lb.item[0].M > kEmuTile, fit, p.num_sms, s);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    {
+        LaunchTimer tm(p, s, LADDER_KERNEL_FINISH);
+        const unsigned gx = (unsigned)std::min<long long>((bp.npairs + 255) / 256, 1024);
+        const unsigned gy = (unsigned)std::min(d.np, 65535);
+        finalize_pm_kernel<<<dim3(gx, gy), 256, 0, s>>>(
+            at<unsigned long long>(ws, p.ws.rpx), at<unsigned long long>(ws, p.ws.rpy), bp.npairs, p.no, p.nv, d.np,
+            d.nm, table + bp.pairs_off, at<int>(ws, p.ws.v_exp), at<int>(ws, p.ws.tp_exp), at<int>(ws, p.ws.tm_exp),
+            R, p.d_status);
+    }
+    return cudaGetLastError();
+}
+
 template <int S>
 cudaError_t block_impl(const ladder_plan_s& p, const BlockPair& bp, double* R, void* ws, cudaStream_t s) {
+    if (p.form == 1) return block_pm_impl<S>(p, bp, R, ws, s);
     const int no2 = p.no * p.no;
     cudaError_t e;
     // int64 ladder accumulator of this block pair starts at zero

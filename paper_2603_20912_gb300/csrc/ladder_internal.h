@@ -60,8 +60,33 @@ struct WsLayout {
     size_t v_exp = 0;      // EMU: exponent bound per (a, b) pair [nv][nv] (int)
     size_t lnorm = 0;      // EMU: max_c ||L[:, a, c]||_2 per a (IEEE bits, u64)
     size_t lsq = 0;        // EMU: ||L[:, a, c]||_2^2 per (a, c) [nv][nv] (f64)
+    // EMU, symmetric/antisymmetric ladder form (instead of t_slices, t_gmax, t_exp, rp_int):
+    size_t vp_blk = 0;     // V' planes [S][max_pairs][kp] bf16, K' = (c <= d) packed
+    size_t vm_blk = 0;     // V'' planes [S][max_pairs][km] bf16, K'' = (c < d) packed
+    size_t tp_slices = 0;  // T' planes [S][np][kp] bf16, rows (i <= j)
+    size_t tm_slices = 0;  // T'' planes [S][nm][km] bf16, rows (i < j)
+    size_t tp_gmax = 0, tm_gmax = 0;  // max |T'|, |T''| per group of rows (IEEE bits, u64)
+    size_t tp_exp = 0, tm_exp = 0;    // exponent per group of rows (int)
+    size_t rpx = 0, rpy = 0;          // int64 accumulators [max_pairs][np], [max_pairs][nm]
     size_t total = 0;
 };
+
+// Symmetric/antisymmetric ladder form: packed sizes of its K and row ranges.
+struct PmDims {
+    long long kp, km;      // K' = nv(nv+1)/2, K'' = nv(nv-1)/2
+    long long kp_pad, km_pad;  // rounded up to 8 (16-byte rows)
+    int np, nm;            // rows: o(o+1)/2 (i <= j), o(o-1)/2 (i < j)
+};
+inline PmDims pm_dims(int no, int nv) {
+    PmDims d;
+    d.kp = (long long)nv * (nv + 1) / 2;
+    d.km = (long long)nv * (nv - 1) / 2;
+    d.kp_pad = (d.kp + 7) / 8 * 8;
+    d.km_pad = (d.km + 7) / 8 * 8;
+    d.np = no * (no + 1) / 2;
+    d.nm = no * (no - 1) / 2;
+    return d;
+}
 
 struct TensorMaps;  // TMA descriptors (emulated path), defined in emu_kernels.cu
 
@@ -77,6 +102,7 @@ struct ladder_plan_s {
     int pair_clusters = 0;  // emulated ladder on CTA pairs: CTA pairs that fit at once
     size_t budget = 0;
     int n_a = 0, n_b = 0;
+    int form = 0;  // emulated ladder form: 0 = plain (K = (c,d)), 1 = symmetric/antisymmetric
     int shard_rank = 0, shard_world = 1;  // this plan holds shard `shard_rank` of `shard_world`
     std::vector<ladder::BlockPair> bps;
     int max_pairs = 0;
