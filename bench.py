@@ -456,7 +456,8 @@ def main():
     counts = {}
     kms = {}
     for kind, name in [(lad.LADDER_KERNEL_PREP, "prep"), (lad.LADDER_KERNEL_ERI, "eri"),
-                       (lad.LADDER_KERNEL_LADDER, "ladder"), (lad.LADDER_KERNEL_FINISH, "finish")]:
+                       (lad.LADDER_KERNEL_LADDER, "ladder"), (lad.LADDER_KERNEL_FINISH, "finish"),
+                       (lad.LADDER_KERNEL_COMBINE, "combine")]:
         ms, n = plan.timing(kind)
         kms[name] = ms
         counts[name] = n

@@ -105,18 +105,20 @@ int ladder_plan_set_blocks(ladder_plan_t plan, int n_a, int n_b);
  *      Y_ij^ab = sum_{c<d} V''_ab,cd T''_ij,cd (i < j), with V' = V_cd + V_dc (V_cc on the
  *      diagonal), V'' = V_cd - V_dc, T' = (T_ij,cd + T_ji,cd)/2 (T_ij,cc), T'' = (T_ij,cd -
  *      T_ji,cd)/2, and R_ij^ab += X + Y, R_ji^ab += X - Y: half the multiply-adds of the
- *      ladder GEMM, for one extra pass over the V digit planes of each block pair and V', V''
- *      workspace about as large as the V planes (V' and V'' are re-sliced with the pair's
- *      exponent bound plus one, one rounding of half a unit).  This split is not in the paper.
+ *      ladder GEMM, for one extra pass per block pair that reads V (kept as int64 in this
+ *      form) and writes the V' and V'' digit planes (re-sliced with the pair's exponent bound
+ *      plus one, one rounding of half a unit).  K' and K'' are packed in 4-byte words of two
+ *      (c,d) slots, a few zero slots per row included.  This split is not in the paper.
  * The blocking is kept if its workspace still fits the plan's budget, else chosen again.
  * Call before querying the workspace.  Returns LADDER_OK, LADDER_ERR_ARG (batched plan or a
  * form other than 0, 1), LADDER_ERR_UNSUPPORTED (form 1 on the FP64 path), LADDER_ERR_BUDGET
  * or LADDER_ERR_CUDA.
  */
 int ladder_plan_set_form(ladder_plan_t plan, int form);
-/* The form a plan uses: ladder_plan picks 1 on the emulated path when a cost model over the
- * tile-padded ladder rows and the extra pass over V gives it a 5 % lead (large no^2 with
- * respect to the 128/256-row MMA tiles) and the workspace fits, else 0.  -1 for NULL. */
+/* The form a plan uses: ladder_plan picks 1 on the emulated path when a cost model of the whole
+ * call (ERI, tile-padded ladder rows, the extra pass over V) gives it a 5 % lead (the ladder a
+ * large share of the call: large no^2 with respect to the 128/256-row MMA tiles and to nchol)
+ * and the workspace fits, else 0.  The instances of a batched plan use form 0.  -1 for NULL. */
 int ladder_plan_get_form(ladder_plan_t plan);
 
 /*
@@ -285,7 +287,8 @@ enum {
     LADDER_KERNEL_ERI = 1,      /* Cholesky -> ERI GEMM                               */
     LADDER_KERNEL_LADDER = 2,   /* ladder GEMM                                        */
     LADDER_KERNEL_FINISH = 3,   /* accumulator finalisation / unpack                  */
-    LADDER_KERNEL_CLASSES = 4
+    LADDER_KERNEL_COMBINE = 4,  /* V' and V'' from V (symmetric/antisymmetric form)   */
+    LADDER_KERNEL_CLASSES = 5
 };
 int ladder_plan_set_timing(ladder_plan_t plan, int enable);
 int ladder_plan_timing(ladder_plan_t plan, int kernel_class, float* total_ms, int* launches, int reset);

@@ -36,6 +36,7 @@ LADDER_KERNEL_PREP = 0
 LADDER_KERNEL_ERI = 1
 LADDER_KERNEL_LADDER = 2
 LADDER_KERNEL_FINISH = 3
+LADDER_KERNEL_COMBINE = 4
 
 # LADDER_CHECKED_LIBRARY=1 loads the index-checked build (build.build(check=True)) instead.
 LIB_PATH = _build_mod.LIB_CHECK if os.environ.get("LADDER_CHECKED_LIBRARY") == "1" else _build_mod.LIB

@@ -114,7 +114,8 @@ ladder::WsLayout layout_for(const ladder_plan_s& p, long long max_pairs) {
         const size_t vp = align_up((size_t)p.nv, 8), nvp = (size_t)p.nv * vp;
         const size_t kpad = nvp, xpad = align_up((size_t)p.nchol, 8);
         const size_t G = ladder::kExpGroupRows;
-        w.v_blk = take(S * (size_t)max_pairs * kpad * 2);
+        // V digit planes, or V as int64 for the symmetric/antisymmetric form (combined first)
+        w.v_blk = take((p.form == 0 ? S * 2 : 8) * (size_t)max_pairs * kpad);
         w.lt_slices = take(S * nvp * xpad * 2);
         w.lt_exp = take(((nvp + G - 1) / G) * 4);
         if (p.form == 0) {
@@ -349,26 +350,30 @@ struct DeviceGuard {
     }
 };
 
-// Emulated ladder form from a cost model over all a <= b pairs: the ladder GEMM's MMA rows are
-// padded to its tiles (128 rows on one SM up to 128 (i,j) rows, else 256 on CTA pairs), the
-// symmetric/antisymmetric form halves K and splits the rows into i <= j and i < j, and pays one
-// pass over the V digit planes (read and write, ~2.8 TB/s measured).  The split is chosen when
-// the model gives it a 5 % lead.
-int auto_form(int no, int nv, int nslices) {
+// Emulated ladder form from a cost model of a whole call over all a <= b pairs: the ERI (the same
+// in both forms; K = nchol), the ladder GEMM, whose MMA rows are padded to its tiles (128 rows
+// on one SM up to 128 (i,j) rows, else 256 on CTA pairs) and which the symmetric/antisymmetric
+// form halves in K and splits into rows i <= j and i < j, and the split's one pass that reads V
+// as int64 and writes the V' and V'' digit planes (~3.5 TB/s measured).  The split is chosen
+// when the model gives the call a 5 % lead.
+int auto_form(int no, int nv, int nchol, int nslices) {
     const double pairs = 0.5 * nv * (nv + 1.0);
     auto rows_pad = [](double r) { return r <= ladder::kEmuTile ? ladder::kEmuTile : std::ceil(r / 256.0) * 256.0; };
     const double vp = std::ceil(nv / 8.0) * 8.0;
     const double per_row_k = pairs * 2.0 * nslices * (nslices + 1) / 2 / 1.3e15;   // s per (row, K element)
-    const double plain = rows_pad((double)no * no) * nv * vp * per_row_k;
+    const double eri = (double)nchol * nv * vp * per_row_k;
+    const double plain = eri + rows_pad((double)no * no) * nv * vp * per_row_k;
     const ladder::PmDims d = ladder::pm_dims(no, nv);
-    double pm = rows_pad(d.np) * (double)d.kp * per_row_k;
+    double pm = eri + rows_pad(d.np) * (double)d.kp * per_row_k;
     if (d.nm > 0) pm += rows_pad(d.nm) * (double)d.km * per_row_k;
-    pm += 2.0 * (nslices * 2.0 * pairs * nv * vp) / 2.8e12;   // read and write the V digit planes
+    pm += (8.0 + 2.0 * nslices) * pairs * nv * vp / 3.5e12;   // read int64 V, write V' and V''
     return pm < 0.95 * plain ? 1 : 0;
 }
 
+// split_ok = false keeps the plain form (instances of a batched plan, whose grouped launches
+// run the plain form).
 int make_plan(ladder_plan_s** out, int no, int nv, int nchol, int precision, int nslices, size_t budget,
-              int device) {
+              int device, bool split_ok = true) {
     *out = nullptr;
     if (no < 1 || nv < 1 || nchol < 1) return LADDER_ERR_ARG;
     if ((long long)no * no > (1 << 20) || nv > 4096) return LADDER_ERR_ARG;
@@ -413,7 +418,7 @@ int make_plan(ladder_plan_s** out, int no, int nv, int nchol, int precision, int
         p->eri_clusters = ladder::emu_max_clusters(nslices, 0);
         p->pair_clusters = ladder::emu_max_clusters(nslices, 1);
     }
-    p->form = precision == LADDER_FP64 ? 0 : auto_form(no, nv, p->nslices);
+    p->form = precision == LADDER_FP64 || !split_ok ? 0 : auto_form(no, nv, nchol, p->nslices);
     int rc = choose_blocking(*p);
     if (rc == LADDER_ERR_BUDGET && p->form == 1) {   // the split needs more workspace: fall back
         p->form = 0;
@@ -687,7 +692,7 @@ int ladder_plan_batched(ladder_plan_t* out, int n, const int* no, const int* nv,
     // ERI fits), and the plan's workspace holds as many instances at once as the budget allows.
     for (int k = 0; k < n; ++k) {
         ladder_plan_s* s = nullptr;
-        const int rc = make_plan(&s, no[k], nv[k], nchol[k], precision, nslices, budget, device);
+        const int rc = make_plan(&s, no[k], nv[k], nchol[k], precision, nslices, budget, device, false);
         if (rc != LADDER_OK) {
             destroy_plan(p);
             return rc;
@@ -954,7 +959,7 @@ int ladder_plan_dry(int no, int nv, int nchol, int precision, int nslices, size_
     p.nslices = precision == LADDER_FP64 ? 0 : nslices;
     p.num_sms = num_sms;
     p.budget = ws_budget_bytes;
-    p.form = precision == LADDER_FP64 ? 0 : auto_form(no, nv, nslices);
+    p.form = precision == LADDER_FP64 ? 0 : auto_form(no, nv, nchol, nslices);
     int na = force_n_a, nb = force_n_b;
     if (na <= 0 || nb <= 0) {
         int rc = select_blocking(p, &na, &nb);

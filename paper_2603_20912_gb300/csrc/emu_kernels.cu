@@ -216,6 +216,26 @@ __device__ __forceinline__ void slice_run(const long long (&I)[8], int sh, __nv_
     if (bad) atomicOr(status, kStatusNumeric);
 }
 
+// N = round(I 2^-sh) (halves up) of one run of 8 int64 values, kept as integers (the V of the
+// symmetric/antisymmetric form, which is combined before it is sliced), with the range check of
+// slice_run.
+template <int S>
+__device__ __forceinline__ void round_run(const long long (&I)[8], int sh, long long (&N)[8], unsigned* status) {
+    constexpr long long B = digit_bias<S>();
+    if (sh >= 1 && sh <= 63 - 7 * S) {
+        const long long add = 1LL << (sh - 1);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) N[k] = (I[k] + add) >> sh;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) N[k] = rescale(I[k], sh, 1LL << (7 * S - 1), status);
+    }
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) bad |= (unsigned)((int)((N[k] + B) >> (7 * (S - 1))) + 64) > 128u;
+    if (bad) atomicOr(status, kStatusNumeric);
+}
+
 // One 32-byte streaming store (a whole L2 sector), 32-byte aligned address.
 __device__ __forceinline__ void st_cs_32B(void* ptr, const uint4& lo, const uint4& hi) {
     asm volatile("st.global.cs.v8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(ptr), "r"(lo.x), "r"(lo.y), "r"(lo.z),
@@ -369,9 +389,9 @@ __global__ void __launch_bounds__(256) t_slice_kernel(const double* __restrict__
 //                                                        T' = (T_ij,cd + T_ji,cd) / 2 (c < d), T_ij,cc
 //   Y_ij^ab = sum_{c<d}  V''_ab,cd T''_ij,cd  (i < j),  V'' = V_cd - V_dc, T'' = (T_ij,cd - T_ji,cd) / 2
 //   R_ij^ab = X + Y,  R_ji^ab = X - Y,
-// half the multiply-adds of the plain ladder.  K' and the rows (i <= j) are packed row-major:
-// k'(c,d) = c nv - c(c-1)/2 + (d - c), r(i,j) = i no - i(i-1)/2 + (j - i); K'' and the rows
-// (i < j) the same without the diagonal.
+// half the multiply-adds of the plain ladder.  The rows (i <= j) are packed row-major,
+// r(i,j) = i no - i(i-1)/2 + (j - i), and (i < j) the same without the diagonal; K' and K''
+// are packed in word pairs of slots (pm_base), so that V' and V'' go out in 4-byte stores.
 
 // (i, j) of packed row r of the upper triangle of an n x n grid (diag: with the diagonal).
 __device__ __forceinline__ void tri_unpack(int r, int n, bool diag, int* i, int* j) {
@@ -383,10 +403,6 @@ __device__ __forceinline__ void tri_unpack(int r, int n, bool diag, int* i, int*
     }
     *i = a;
     *j = a + r + (diag ? 0 : 1);
-}
-
-__device__ __forceinline__ long long tri_off(int c, int n, bool diag) {  // first packed index of row c
-    return diag ? (long long)c * n - (long long)c * (c - 1) / 2 : (long long)c * (n - 1) - (long long)c * (c - 1) / 2;
 }
 
 // One block per packed row of T' (r < np) or T'' (r >= np): max |value| into its 64-row group.
@@ -435,14 +451,19 @@ __global__ void __launch_bounds__(128) tpm_slice_kernel(const double* __restrict
     const long long kpad = plus ? kp_pad : km_pad;
     const size_t plane = (size_t)(plus ? np : nm) * kpad;
     __nv_bfloat16* out = (plus ? tp : tm) + (size_t)r * kpad;
-    for (int c = threadIdx.x; c < nv; c += blockDim.x) {
-        const long long k0 = tri_off(c, nv, plus);
-        for (int d = plus ? c : c + 1; d < nv; ++d) {
-            const double a = __ldg(tij + (size_t)c * nv + d), b = __ldg(tji + (size_t)c * nv + d);
-            const double v = plus ? (c == d ? a : 0.5 * (a + b)) : 0.5 * (a - b);
+    const int dend = 2 * ((nv - 1) / 2) + 1;   // last slot of every row's last word
+    for (int c = threadIdx.x; c < (plus ? nv : nv - 1); c += blockDim.x) {
+        const long long k0 = pm_base(c, nv, plus);
+        const int dlo = plus ? c : c + 1;
+        for (int d = dlo & ~1; d <= dend; ++d) {   // whole words: the slots outside the row get zero
+            double v = 0.0;
+            if (d >= dlo && d < nv) {
+                const double a = __ldg(tij + (size_t)c * nv + d), b = __ldg(tji + (size_t)c * nv + d);
+                v = plus ? (c == d ? a : 0.5 * (a + b)) : 0.5 * (a - b);
+            }
             __nv_bfloat16 dg[S];
             digits_of<S>(scaled_rint(v, 7 * S - e), dg);
-            const long long k = k0 + (d - c - (plus ? 0 : 1));
+            const long long k = k0 + d;
             if (!LADDER_IN_BOUNDS((size_t)r * kpad + k < plane, status)) continue;
 #pragma unroll
             for (int s = 0; s < S; ++s) out[s * plane + k] = dg[s];
@@ -452,71 +473,138 @@ __global__ void __launch_bounds__(128) tpm_slice_kernel(const double* __restrict
 
 struct CombineArgs {
     int nv, vp, npairs, ntile;        // ntile = 32-wide tiles per (c or d) axis
-    size_t vplane, pplane, mplane;    // element strides between planes of V, V', V''
-    long long kpad, kp_pad, km_pad;   // row strides of V, V', V''
-    const __nv_bfloat16* v;
+    size_t pplane, mplane;            // element strides between planes of V', V''
+    long long kpad, kp_pad, km_pad;   // row strides of V (int64), V', V''
+    const long long* vi;
     __nv_bfloat16* vp_out;
     __nv_bfloat16* vm_out;
     unsigned* status;
 };
 
-// V' and V'' of every pair row of a block from its V digit planes, on the grid of exponent
-// f_ab + 1: N' = round((N_cd + N_dc) / 2) (c < d) or round(N_cc / 2), N'' = round((N_cd - N_dc) / 2),
-// halves rounded up, so |N'|, |N''| <= 2^(7S-1) and the digits stay within +-64.  One block per
-// (pair row, 32x32 tile of (c,d) with c-tile <= d-tile); both the tile and its transpose pass
-// through shared memory so that every global access is a row segment.
+// Bits [SFT, SFT + W) of two unsigned values, the first in the low and the second in the high
+// 16-bit half.  A field inside one 16-bit window of the same 32-bit word of both values takes
+// one byte permute and a shift; otherwise each value is shifted first.
+template <int SFT, int W>
+__device__ __forceinline__ uint32_t field_pair(unsigned long long b0, unsigned long long b1) {
+    constexpr uint32_t mask = ((1u << W) - 1u) * 0x00010001u;
+    constexpr int k = SFT / 8, r = SFT - 8 * k;
+    uint32_t v;
+    if constexpr (k <= 2) {
+        v = __byte_perm((uint32_t)b0, (uint32_t)b1, k | (k + 1) << 4 | (k + 4) << 8 | (k + 5) << 12) >> r;
+    } else if constexpr (k >= 4 && k <= 6) {
+        v = __byte_perm((uint32_t)(b0 >> 32), (uint32_t)(b1 >> 32), (k - 4) | (k - 3) << 4 | k << 8 | (k + 1) << 12) >> r;
+    } else {
+        v = __byte_perm((uint32_t)(b0 >> SFT), (uint32_t)(b1 >> SFT), 0x5410);
+    }
+    return v & mask;
+}
+
+__device__ __forceinline__ uint32_t bf16x2_fma(uint32_t a, uint32_t b, uint32_t c) {
+    uint32_t d;
+    asm("fma.rn.bf16x2 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+
+// BF16 pairs (x, x) of 2^e and of -192 2^e = -1.5 2^(e+7).
+__host__ __device__ constexpr uint32_t bf16_pair_pow2(int e) { return (uint32_t)((e + 127) << 7) * 0x00010001u; }
+__host__ __device__ constexpr uint32_t bf16_pair_m192(int e) {
+    return (uint32_t)(0x8000 | ((e + 134) << 7) | 0x40) * 0x00010001u;
+}
+
+// Digit planes of two slots as BF16 pairs: word s holds digit s of N0 in its low half and of N1
+// in its high half (the slot order in memory); the digits of digits_of.  With the bias
+// B + 64 128^(S-1), every digit, the top one included, is a plain field u of the biased value
+// (d_s = u - 64; u <= 127 below the top, <= 128 at the top).  The BF16 with bits 0x4300 | u is
+// 128 + u exactly, so one BF16x2 FMA per plane, (128 + u) 2^-k - 192 2^-k, gives the digit
+// values d 2^-k of both slots exactly (k = 7(s+1)).
 template <int S>
-__global__ void __launch_bounds__(256) vpm_combine_kernel(CombineArgs p) {
-    __shared__ __nv_bfloat16 ta[S][32][33], tb[S][32][33];   // ta[s][c][d] = V(c,d), tb[s][d][c] = V(d,c)
+__device__ __forceinline__ void digit_words(long long N0, long long N1, uint32_t (&w)[S]) {
+    constexpr long long Bt = digit_bias<S>() + (64LL << (7 * (S - 1)));
+    const unsigned long long b0 = (unsigned long long)(N0 + Bt), b1 = (unsigned long long)(N1 + Bt);
+    constexpr uint32_t m128 = 0x43004300u;
+    w[0] = bf16x2_fma(field_pair<7 * (S - 1), 8>(b0, b1) | m128, bf16_pair_pow2(-7), bf16_pair_m192(-7));
+#pragma unroll
+    for (int s = 1; s < S; ++s) {
+        uint32_t f;
+        switch (S - 1 - s) {   // field position, a compile-time constant after unrolling
+            case 0: f = field_pair<0, 7>(b0, b1); break;
+            case 1: f = field_pair<7, 7>(b0, b1); break;
+            case 2: f = field_pair<14, 7>(b0, b1); break;
+            case 3: f = field_pair<21, 7>(b0, b1); break;
+            case 4: f = field_pair<28, 7>(b0, b1); break;
+            case 5: f = field_pair<35, 7>(b0, b1); break;
+            default: f = field_pair<42, 7>(b0, b1); break;
+        }
+        w[s] = bf16x2_fma(f | m128, bf16_pair_pow2(-7 * (s + 1)), bf16_pair_m192(-7 * (s + 1)));
+    }
+}
+
+// V' and V'' of every pair row of a block from its int64 V (N on the grid of exponent f_ab), on
+// the grid of exponent f_ab + 1: N' = round((N_cd + N_dc) / 2) (c < d) or round(N_cc / 2),
+// N'' = round((N_cd - N_dc) / 2), halves rounded up, so |N'|, |N''| <= 2^(7S-1) and the digits
+// stay within +-64.  One block per (pair row, 32x32 tile of (c,d) with c-tile <= d-tile), in
+// row-major tile order so that the blocks writing neighbouring segments of a V' row run at the
+// same time (their partial sectors meet in L2); the tile and its transpose pass through shared
+// memory so that every global access is a row segment, and each thread writes whole words
+// (slots d, d + 1) of the packed V' and V''.  128 threads: with 17 KB of shared memory per
+// block, twelve blocks per SM keep their loads in flight together.
+constexpr int kCombineThreads = 128;
+
+template <int S>
+__global__ void __launch_bounds__(kCombineThreads) vpm_combine_kernel(CombineArgs p) {
+    __shared__ long long ta[32][33], tb[32][33];   // ta[c][d] = N(c,d), tb[d][c] = N(d,c)
+    __shared__ long long base_p[32], base_m[32];  // pm_base of the tile's rows c
     const long long ntp = (long long)p.ntile * (p.ntile + 1) / 2;
     const long long blk = blockIdx.x;
     const int row = (int)(blk / ntp);
     int tc, td;
     tri_unpack((int)(blk % ntp), p.ntile, true, &tc, &td);
     const int c0 = tc * 32, d0 = td * 32;
-    const __nv_bfloat16 zero = __float2bfloat16_rn(0.0f);
-    // 16-byte loads: 8 consecutive columns of one (c or d) row segment per thread and plane
-    // (vp % 8 == 0 keeps every segment aligned; the pad columns up to vp hold zeros).
-    for (int t = threadIdx.x; t < 2 * S * 32 * 4; t += blockDim.x) {
-        const int q = t & 3, u = (t >> 2) & 31, s2 = (t >> 7) % S, which = t / (128 * S);
-        const int rr = (which == 0 ? c0 : d0) + u, col0 = (which == 0 ? d0 : c0) + 8 * q;
-        __nv_bfloat16 (*dst)[33] = which == 0 ? ta[s2] : tb[s2];
-        const __nv_bfloat16* src = p.v + s2 * p.vplane + (size_t)row * p.kpad + (size_t)rr * p.vp + col0;
-        if (rr < p.nv && col0 + 8 <= p.vp) {
-            const uint4 x = *reinterpret_cast<const uint4*>(src);
-            const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(&x);
-#pragma unroll
-            for (int k = 0; k < 8; ++k) dst[u][8 * q + k] = h[k];
-        } else {
-#pragma unroll
-            for (int k = 0; k < 8; ++k) dst[u][8 * q + k] = (rr < p.nv && col0 + k < p.nv) ? src[k] : zero;
-        }
+    // 16-byte streaming loads of two columns (vp % 8 == 0: a pair never straddles vp; the pad
+    // columns nv <= d < vp are read but not used).
+    for (int t = threadIdx.x; t < 2 * 32 * 16; t += kCombineThreads) {
+        const int q = t & 15, u = (t >> 4) & 31, which = t >> 9;
+        const int rr = (which == 0 ? c0 : d0) + u, col0 = (which == 0 ? d0 : c0) + 2 * q;
+        long long (*dst)[33] = which == 0 ? ta : tb;
+        longlong2 x = make_longlong2(0, 0);
+        if (rr < p.nv && col0 < p.vp)
+            x = __ldcs(reinterpret_cast<const longlong2*>(p.vi + (size_t)row * p.kpad + (size_t)rr * p.vp + col0));
+        dst[u][2 * q] = x.x;
+        dst[u][2 * q + 1] = x.y;
+    }
+    if (threadIdx.x < 32) {
+        base_p[threadIdx.x] = pm_base(c0 + threadIdx.x, p.nv, true);
+        base_m[threadIdx.x] = pm_base(c0 + threadIdx.x, p.nv, false);
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
-        const int u = t >> 5, w = t & 31;
-        const int c = c0 + u, d = d0 + w;
-        if (c >= p.nv || d >= p.nv || c > d) continue;
-        long long ncd = 0, ndc = 0;
+    uint32_t* const outp = reinterpret_cast<uint32_t*>(p.vp_out + (size_t)row * p.kp_pad);
+    uint32_t* const outm = reinterpret_cast<uint32_t*>(p.vm_out + (size_t)row * p.km_pad);
+    const size_t pw = p.pplane / 2, mw = p.mplane / 2;   // plane strides in words
+    // Items (c row u, word of slots d = d0 + 2k, d + 1): a warp covers 16 words of two rows.
+    for (int t = threadIdx.x; t < 32 * 16; t += kCombineThreads) {
+        const int u = t >> 4, k = t & 15;
+        const int c = c0 + u, d = d0 + 2 * k;
+        if (c >= p.nv || d >= p.nv) continue;
+        const bool in1 = d + 1 < p.nv;
+        const long long a0 = ta[u][2 * k], a1 = ta[u][2 * k + 1], b0 = tb[2 * k][u], b1 = tb[2 * k + 1][u];
+        uint32_t w[S];
+        if (d + 1 >= c) {   // a word of row c of V'
+            const long long n0 = d < c ? 0 : ((d > c ? a0 + b0 : a0) + 1) >> 1;
+            const long long n1 = in1 ? ((d + 1 > c ? a1 + b1 : a1) + 1) >> 1 : 0;
+            digit_words<S>(n0, n1, w);
+            const long long wi = (base_p[u] + d) >> 1;
+            if (LADDER_IN_BOUNDS(((size_t)row * p.kp_pad >> 1) + wi < pw, p.status))
 #pragma unroll
-        for (int s = 0; s < S; ++s) {
-            const float sc = pow2f(7 * (s + 1));
-            ncd = ncd * 128 + (long long)__float2int_rn(__bfloat162float(ta[s][u][w]) * sc);
-            ndc = ndc * 128 + (long long)__float2int_rn(__bfloat162float(tb[s][w][u]) * sc);
+                for (int s = 0; s < S; ++s) outp[s * pw + wi] = w[s];
         }
-        __nv_bfloat16 dg[S];
-        const long long kp = tri_off(c, p.nv, true) + (d - c);
-        const long long np_ = (c < d ? ncd + ndc : ncd) + 1;
-        digits_of<S>(np_ >> 1, dg);
-        if (LADDER_IN_BOUNDS((size_t)row * p.kp_pad + kp < p.pplane, p.status))
+        if (d >= c && c < p.nv - 1) {   // a word of row c of V''
+            const long long n0 = d > c ? (a0 - b0 + 1) >> 1 : 0;
+            const long long n1 = in1 ? (a1 - b1 + 1) >> 1 : 0;
+            digit_words<S>(n0, n1, w);
+            const long long wi = (base_m[u] + d) >> 1;
+            if (LADDER_IN_BOUNDS(((size_t)row * p.km_pad >> 1) + wi < mw, p.status))
 #pragma unroll
-            for (int s = 0; s < S; ++s) p.vp_out[s * p.pplane + (size_t)row * p.kp_pad + kp] = dg[s];
-        if (c < d) {
-            const long long km = tri_off(c, p.nv, false) + (d - c - 1);
-            digits_of<S>((ncd - ndc + 1) >> 1, dg);
-            if (LADDER_IN_BOUNDS((size_t)row * p.km_pad + km < p.mplane, p.status))
-#pragma unroll
-                for (int s = 0; s < S; ++s) p.vm_out[s * p.mplane + (size_t)row * p.km_pad + km] = dg[s];
+                for (int s = 0; s < S; ++s) outm[s * mw + wi] = w[s];
         }
     }
 }
@@ -627,6 +715,7 @@ struct EriItem {
     const int* lt_exp;
     const int* f_tab;
     __nv_bfloat16* vplanes;
+    long long* vint;      // non-null: V as int64 N (row stride kpad) instead of digit planes
 };
 
 struct EriBatch {
@@ -813,9 +902,19 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsEri, 1)
                     e_bd = p.lt_exp[(p.b0 * p.vp + col) / kG];
                 }
                 const int sh = f_ab - e_ac - e_bd + 49 - 7 * S;
+                const size_t off = (size_t)(rs + (b - max(a, p.b0))) * p.kpad + (size_t)c * p.vp + d;
+                if (p.vint != nullptr) {   // 64 bytes: two whole sectors
+                    __align__(16) long long N[8];
+                    round_run<S>(run[g], sh, N, B.status);
+                    const uint4* w4 = reinterpret_cast<const uint4*>(N);
+                    if (LADDER_IN_BOUNDS(off + 8 <= p.plane_stride, B.status)) {
+                        st_cs_32B(p.vint + off, w4[0], w4[1]);
+                        st_cs_32B(p.vint + off + 4, w4[2], w4[3]);
+                    }
+                    continue;
+                }
                 __align__(16) __nv_bfloat162 out[S][4];
                 slice_run<S>(run[g], sh, out, B.status);
-                const size_t off = (size_t)(rs + (b - max(a, p.b0))) * p.kpad + (size_t)c * p.vp + d;
                 // streaming stores: V is read back only by the ladder
                 if (!sector_pairs) {
 #pragma unroll
@@ -864,6 +963,7 @@ struct SelfArgs {
     const int* f_tab;
     const double* lsq;      // ||L[:, a, c]||^2 [nv][nv]
     __nv_bfloat16* vplanes;
+    long long* vint;        // non-null: V held as int64 N
     unsigned* status;
 };
 
@@ -896,10 +996,14 @@ __global__ void __launch_bounds__(256) eri_self_kernel(SelfArgs p) {
         atomicOr(p.status, kStatusNumeric);
         N = lim;
     }
-    __nv_bfloat16 dg[S];
-    digits_of<S>(N, dg);
     const size_t off = (size_t)row * p.kpad + (size_t)c * p.vp + d;
     if (!LADDER_IN_BOUNDS(off < p.plane_stride, p.status)) return;
+    if (p.vint != nullptr) {
+        p.vint[off] = N;
+        return;
+    }
+    __nv_bfloat16 dg[S];
+    digits_of<S>(N, dg);
 #pragma unroll
     for (int s = 0; s < S; ++s) p.vplanes[s * p.plane_stride + off] = dg[s];
 }
@@ -1385,7 +1489,7 @@ bool eri_item(const ladder_plan_s& p, const BlockPair& bp, void* ws, EriItem* it
     const int* row_start = reinterpret_cast<const int*>(p.d_tables) + bp.rows_off;
     *it = EriItem{p.nv, vp, p.nchol, bp.a0, bp.a1 - bp.a0, bp.b0, bp.b1 - bp.b0, (int)rows,
                   (size_t)p.max_pairs * (size_t)rows, row_start, at<int>(ws, p.ws.lt_exp), at<int>(ws, p.ws.v_exp),
-                  at<__nv_bfloat16>(ws, p.ws.v_blk)};
+                  at<__nv_bfloat16>(ws, p.ws.v_blk), p.form == 1 ? at<long long>(ws, p.ws.v_blk) : nullptr};
     return true;
 }
 
@@ -1409,7 +1513,8 @@ void launch_self(const ladder_plan_s& p, const BlockPair& bp, void* ws, cudaStre
     const long long nself = (long long)bp.npairs + (long long)ndiag * p.nv;
     SelfArgs sa{p.nv, vp, kpad, bp.a0, bp.a1, bp.b0, bp.b1, bp.npairs, (size_t)p.max_pairs * kpad,
                 table + bp.pairs_off, row_start, at<int>(ws, p.ws.v_exp), at<double>(ws, p.ws.lsq),
-                at<__nv_bfloat16>(ws, p.ws.v_blk), p.d_status};
+                at<__nv_bfloat16>(ws, p.ws.v_blk), p.form == 1 ? at<long long>(ws, p.ws.v_blk) : nullptr,
+                p.d_status};
     eri_self_kernel<S><<<(unsigned)((nself + 255) / 256), 256, 0, s>>>(sa);
 }
 
@@ -1511,15 +1616,18 @@ cudaError_t block_pm_impl(const ladder_plan_s& p, const BlockPair& bp, double* R
     if (!eri_item<S>(p, bp, ws, &eb.item[0], &eb.ta[0], &eb.tb[0])) return cudaErrorInvalidValue;
     const int vp = padded_vp(p.nv);
     {
-        LaunchTimer tm(p, s, LADDER_KERNEL_ERI, 3);
+        LaunchTimer tm(p, s, LADDER_KERNEL_ERI, 2);
         launch_eri_batch<S>(eb, p.eri_clusters > 0 ? p.eri_clusters : p.num_sms / 2, s);
         launch_self<S>(p, bp, ws, s);
-        CombineArgs ca{p.nv, vp, bp.npairs, (p.nv + 31) / 32, (size_t)p.max_pairs * p.nv * vp,
-                       (size_t)p.max_pairs * d.kp_pad, (size_t)p.max_pairs * d.km_pad, (long long)p.nv * vp,
-                       d.kp_pad, d.km_pad, at<__nv_bfloat16>(ws, p.ws.v_blk), at<__nv_bfloat16>(ws, p.ws.vp_blk),
+    }
+    {
+        LaunchTimer tm(p, s, LADDER_KERNEL_COMBINE);
+        CombineArgs ca{p.nv, vp, bp.npairs, (p.nv + 31) / 32, (size_t)p.max_pairs * d.kp_pad,
+                       (size_t)p.max_pairs * d.km_pad, (long long)p.nv * vp, d.kp_pad, d.km_pad,
+                       at<long long>(ws, p.ws.v_blk), at<__nv_bfloat16>(ws, p.ws.vp_blk),
                        at<__nv_bfloat16>(ws, p.ws.vm_blk), p.d_status};
-        const long long blocks = (long long)bp.npairs * ca.ntile * (ca.ntile + 1) / 2;
-        vpm_combine_kernel<S><<<(unsigned)blocks, 256, 0, s>>>(ca);
+        const long long units = (long long)bp.npairs * ca.ntile * (ca.ntile + 1) / 2;
+        vpm_combine_kernel<S><<<(unsigned)units, kCombineThreads, 0, s>>>(ca);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int fit = p.pair_clusters > 0 ? p.pair_clusters : p.num_sms / 2;

@@ -72,15 +72,30 @@ struct WsLayout {
 };
 
 // Symmetric/antisymmetric ladder form: packed sizes of its K and row ranges.
+// Packed (c,d) index of the symmetric (c <= d, plus) and antisymmetric (c < d) forms, in
+// 4-byte words of two slots (d even, d + 1): row c holds the words that contain one of its
+// elements, from d = c (plus) or c + 1 rounded down to even up to d = nv - 1, so element (c,d)
+// sits in slot pm_base(c) + d with pm_base(c) even and every word belongs to one row; the slots
+// without an element (d = c - 1 or c, d = nv) hold zero.  Rows of the antisymmetric form stop
+// at c = nv - 2.  pm_words(c) is the first word of row c.
+__host__ __device__ inline long long pm_words(int c, int nv, bool plus) {
+    const long long h1 = (nv - 1) / 2 + 1;
+    return plus ? (long long)c * h1 - (long long)(c / 2) * ((c - 1) / 2)
+                : (long long)c * h1 - (long long)((c + 1) / 2) * (c / 2);
+}
+__host__ __device__ inline long long pm_base(int c, int nv, bool plus) {
+    return 2 * (pm_words(c, nv, plus) - (plus ? c / 2 : (c + 1) / 2));
+}
+
 struct PmDims {
-    long long kp, km;      // K' = nv(nv+1)/2, K'' = nv(nv-1)/2
+    long long kp, km;      // slots of the packed K' (c <= d) and K'' (c < d), pads included
     long long kp_pad, km_pad;  // rounded up to 8 (16-byte rows)
     int np, nm;            // rows: o(o+1)/2 (i <= j), o(o-1)/2 (i < j)
 };
 inline PmDims pm_dims(int no, int nv) {
     PmDims d;
-    d.kp = (long long)nv * (nv + 1) / 2;
-    d.km = (long long)nv * (nv - 1) / 2;
+    d.kp = 2 * pm_words(nv, nv, true);
+    d.km = nv >= 2 ? 2 * pm_words(nv - 1, nv, false) : 0;
     d.kp_pad = (d.kp + 7) / 8 * 8;
     d.km_pad = (d.km + 7) / 8 * 8;
     d.np = no * (no + 1) / 2;
