@@ -70,6 +70,37 @@ def captured_traffic(precision: str, workload: str):
     return rec[1], rec[2]
 
 
+def eri_products(nv: int, n_a: int, n_b: int) -> int:
+    """Row-column products (each over K = nchol) that the emulated ERI of one call needs, for
+    the blocking n_a x n_b (blocks: b outer, a inner, kept when they hold a pair a <= b).  L^P is
+    symmetric, so only the rows (x, y) of L^T with x <= y are multiplied: a block with a range
+    [a0, a1) uses the rows (x, [x, nv)) for x in the range, which store to V rows (x, b >= x),
+    and (x, [a0, a1)) for x < a0, which store to (y, b >= y); each row meets the nv columns (b, d)
+    of every b in the block's b range at or above that first index."""
+    total = 0
+    for b0 in range(0, nv, n_b):
+        b1 = min(nv, b0 + n_b)
+        for a0 in range(0, nv, n_a):
+            a1 = min(nv, a0 + n_a)
+            if a0 > b1 - 1:
+                continue
+            for x in range(a0, a1):
+                total += (nv - x) * nv * max(0, b1 - max(b0, x))
+            for y in range(a0, a1):
+                total += a0 * nv * max(0, b1 - max(b0, y))
+    return total
+
+
+def ladder_products(no: int, nv: int, form: str) -> int:
+    """Row-column products of the ladder GEMM of one call over all a <= b pairs: rows (i,j) and
+    K = (c,d) in the plain form; rows i <= j with K = c <= d plus rows i < j with K = c < d in the
+    symmetric/antisymmetric form."""
+    pairs = nv * (nv + 1) // 2
+    if form == "pm":
+        return pairs * ((no * (no + 1) // 2) * (nv * (nv + 1) // 2) + (no * (no - 1) // 2) * (nv * (nv - 1) // 2))
+    return pairs * no * no * nv * nv
+
+
 def load_peaks():
     try:
         with open(PEAKS_FILE) as f:
@@ -469,6 +500,8 @@ def main():
     nv2 = cfg.nv * cfg.nv
     pairs_total = cfg.nv * (cfg.nv + 1) // 2
     eri_flops_call = 2.0 * cfg.nchol * nv2 * pairs_total
+    if precision == lad.LADDER_EMU_BF16:   # only the rows (x <= y) of L^T are multiplied
+        eri_flops_call = 2.0 * cfg.nchol * eri_products(cfg.nv, desc["n_a"], desc["n_b"])
     peaks, peak_src = load_peaks()
     # Burst peak for a timed region under a second, the sustained (power-capped) one for longer.
     long_region = ms_total >= 1000.0
@@ -502,7 +535,8 @@ def main():
         roof["traffic_source"] = traffic_src
     # The whole call against the same peak (every kernel of the step, executed flops).
     if precision == lad.LADDER_EMU_BF16:
-        call_exec = flops * desc["nslices"] * (desc["nslices"] + 1) // 2
+        useful = eri_flops_call + 2.0 * ladder_products(cfg.no, cfg.nv, form_used)
+        call_exec = useful * desc["nslices"] * (desc["nslices"] + 1) // 2
         roof["call_frac"] = call_exec / (ms_step * 1e-3) / 1e12 / peak
 
     # End to end through the public call with host buffers: H2D of L and t2 from pinned memory,

@@ -150,13 +150,16 @@ long long max_pairs_of(const std::vector<BlockPair>& bps) {
     return m;
 }
 
+std::vector<int> eri_entries(const BlockPair& bp, int nv, int tile_n, size_t row_bytes);
+
 double model_time(const ladder_plan_s& p, const std::vector<BlockPair>& bps) {
     const Geometry g = geometry_for(p);
     const double slots_e = (double)p.num_sms * g.eri_occ, slots_l = (double)p.num_sms * g.lad_occ;
     const long long nt = (long long)(p.no * p.no + g.lad_tn - 1) / g.lad_tn;
     double t = 0.0;
     for (auto& bp : bps) {
-        const long long te = count_eri_tiles(bp, p.nv, g.eri_tm, g.eri_tn);
+        const long long te = p.precision == LADDER_FP64 ? count_eri_tiles(bp, p.nv, g.eri_tm, g.eri_tn)
+                                                        : (long long)eri_entries(bp, p.nv, g.eri_tn, 0).size() / 4;
         const long long tl = ((long long)(bp.npairs + g.lad_tm - 1) / g.lad_tm) * nt;
         t += std::ceil(te / (p.precision == LADDER_FP64 ? slots_e : slots_e / 2)) * g.eri_occ * g.eri_tile_s;
         t += std::ceil(tl / slots_l) * g.lad_occ * g.lad_tile_s;
@@ -165,25 +168,57 @@ double model_time(const ladder_plan_s& p, const std::vector<BlockPair>& bps) {
     return t;
 }
 
+// ERI row tiles of the emulated path.  The rows of L^T are (x, y) = x vp + y, and L^P is
+// symmetric, so the rows (x, y) and (y, x) hold the same vector: only rows with x <= y are
+// multiplied.  A computed row (x, y) serves the V rows (x, b) at column block y (x in the block's
+// a range, b >= x) and (y, b) at column block x (y in the a range, x < y, b >= y).  The rows one
+// block needs are the segments (x, [x, nv)) for x in [a0, a1) and (x, [a0, a1)) for x < a0; each
+// is cut into chunks of 8 consecutive rows (one TMA box), 32 chunks to a 256-row tile, the last
+// tile padded with empty chunks.  key[t]: the smallest b that a row of tile t stores to.
+struct EriRowTiles {
+    std::vector<int> chunks;  // (first row, rows) per chunk
+    std::vector<int> key;     // per tile
+};
+
+EriRowTiles eri_row_tiles(const BlockPair& bp, int nv) {
+    const int vp = (nv + 7) / 8 * 8, cr = ladder::kEmuTile * 2 / 32;   // 8 rows per chunk
+    EriRowTiles t;
+    std::vector<int> ckey;
+    auto segment = [&](int x, int y0, int y1, bool upper) {
+        for (int y = y0; y < y1; y += cr) {
+            t.chunks.push_back(x * vp + y);
+            t.chunks.push_back(std::min(cr, y1 - y));
+            ckey.push_back(upper ? x : y);
+        }
+    };
+    for (int x = bp.a0; x < bp.a1; ++x) segment(x, x, nv, true);
+    for (int x = 0; x < bp.a0; ++x) segment(x, bp.a0, bp.a1, false);
+    const size_t ntile = (ckey.size() + 31) / 32;
+    t.chunks.resize(2 * 32 * ntile, 0);
+    t.key.assign(ntile, nv);
+    for (size_t c = 0; c < ckey.size(); ++c) t.key[c / 32] = std::min(t.key[c / 32], ckey[c]);
+    return t;
+}
+
 // Build device tables for the chosen blocking: per block pair its pair list
 // (int2 (a, b), a-major) and row_start (first packed row of each a).
-// ERI work entries of one block pair, (rt, qt, 0, 0): a 256-row tile rt of (a,c)
-// (computed by a CTA pair, 128 rows each) and a 96-column tile qt of (b,d), kept
-// when it holds some a <= b.  Order: a band of row tiles whose operand slices take
-// ~40 MB of L2 stays resident while every column tile of the band streams past it.
-std::vector<int> eri_entries(const BlockPair& bp, int nv, int tile, int tile_n, size_t row_bytes) {
-    nv = (nv + 7) / 8 * 8;  // rows and columns run over the padded (c, d) range
+// ERI work entries of one block pair, (rt, qt, 0, 0): a 256-row tile rt (computed by a CTA pair,
+// 128 rows each) and a 96-column tile qt of (b,d), kept when one of its rows stores to one of
+// its b.  Order: a band of row tiles whose operand slices take ~40 MB of L2 stays resident while
+// every column tile of the band streams past it.
+std::vector<int> eri_entries(const BlockPair& bp, int nv, int tile_n, size_t row_bytes) {
+    const EriRowTiles rt = eri_row_tiles(bp, nv);
+    nv = (nv + 7) / 8 * 8;  // columns run over the padded (b, d) range
     std::vector<int> out;
-    const long long M = (long long)(bp.a1 - bp.a0) * nv, N = (long long)(bp.b1 - bp.b0) * nv;
-    const int nrt = (int)((M + tile - 1) / tile), nqt = (int)((N + tile_n - 1) / tile_n);
-    const int band = (int)std::max<size_t>(4, std::min<size_t>(32, (40u << 20) / std::max<size_t>(1, row_bytes * tile)));
+    const long long N = (long long)(bp.b1 - bp.b0) * nv;
+    const int nrt = (int)rt.key.size(), nqt = (int)((N + tile_n - 1) / tile_n);
+    const int band = (int)std::max<size_t>(4, std::min<size_t>(32, (40u << 20) / std::max<size_t>(1, row_bytes * 256)));
     for (int r0 = 0; r0 < nrt; r0 += band)
         for (int qt = 0; qt < nqt; ++qt)
-            for (int rt = r0; rt < std::min(nrt, r0 + band); ++rt) {
-                const int a_min = bp.a0 + (int)((long long)rt * tile / nv);
+            for (int r = r0; r < std::min(nrt, r0 + band); ++r) {
                 const long long last = std::min((long long)(qt + 1) * tile_n, N) - 1;
-                if (a_min > bp.b0 + (int)(last / nv)) continue;
-                out.push_back(rt);
+                if (rt.key[r] > bp.b0 + (int)(last / nv)) continue;
+                out.push_back(r);
                 out.push_back(qt);
                 out.push_back(0);
                 out.push_back(0);
@@ -193,13 +228,14 @@ std::vector<int> eri_entries(const BlockPair& bp, int nv, int tile, int tile_n, 
 
 int build_tables(ladder_plan_s& p) {
     size_t n_int2 = 0, n_int = 0;
-    std::vector<std::vector<int>> tiles;
+    std::vector<std::vector<int>> tiles, chunks;
     for (auto& bp : p.bps) n_int2 += bp.npairs;
     if (p.precision != LADDER_FP64)
         for (auto& bp : p.bps) {
-            tiles.push_back(eri_entries(bp, p.nv, 2 * ladder::kEmuTile, ladder::kEmuTileN,
+            tiles.push_back(eri_entries(bp, p.nv, ladder::kEmuTileN,
                                         (size_t)p.nslices * 2 * ladder::align_up((size_t)p.nchol, 8)));
-            n_int2 += tiles.back().size() / 2;
+            chunks.push_back(eri_row_tiles(bp, p.nv).chunks);
+            n_int2 += tiles.back().size() / 2 + chunks.back().size() / 2;
         }
     n_int2 += 1;  // room to align the int4 ERI entries to 16 bytes
     for (auto& bp : p.bps) n_int += (size_t)(bp.a1 - bp.a0 + 1);
@@ -226,6 +262,9 @@ int build_tables(ladder_plan_s& p) {
         p.bps[k].ntiles = (int)(tiles[k].size() / 4);  // number of entries
         for (size_t t = 0; t < tiles[k].size(); ++t) host[2 * o2 + t] = tiles[k][t];
         o2 += tiles[k].size() / 2;
+        p.bps[k].chunks_off = o2;
+        for (size_t t = 0; t < chunks[k].size(); ++t) host[2 * o2 + t] = chunks[k][t];
+        o2 += chunks[k].size() / 2;
     }
     if (p.d_tables) {
         cudaFree(p.d_tables);
@@ -504,7 +543,7 @@ int schedule_groups(ladder_plan_s& p, size_t cap) {
         if (grp.size() > 1 || groupable(*p.sub[grp[0]]))
             for (int i = 0; i < (int)grp.size(); ++i) {
                 const ladder_plan_s& q = *p.sub[grp[i]];
-                const std::vector<int> t = eri_entries(q.bps[0], q.nv, 2 * ladder::kEmuTile, ladder::kEmuTileN,
+                const std::vector<int> t = eri_entries(q.bps[0], q.nv, ladder::kEmuTileN,
                                                        (size_t)q.nslices * 2 * ladder::align_up((size_t)q.nchol, 8));
                 for (size_t j = 0; j < t.size(); j += 4) {
                     host.push_back(t[j]);

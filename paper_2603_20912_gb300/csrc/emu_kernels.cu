@@ -661,10 +661,12 @@ struct Ring {
 // Issue the S(S+1)/2 slice-pair MMAs of one stage (BK / 16 K-steps) into the 5 accumulators.
 // The shared-memory descriptors are built once per stage; each MMA only adds the plane
 // and K-step offset (in 16-byte units) to the start-address field.
+// a_group_bytes: distance of the 8-row core groups of A (0: dense planes).
 template <int S, bool PAIR = false, int BK = bk_for(S)>
 __device__ __forceinline__ void issue_pairs(uint32_t tmem, uint32_t sA, uint32_t sB, uint32_t a_plane_bytes,
-                                            uint32_t b_plane_bytes, uint32_t idesc, bool (&first)[kNumAcc]) {
-    const uint64_t da = smem_desc_kmajor(sA, BK * 2), db = smem_desc_kmajor(sB, BK * 2);
+                                            uint32_t b_plane_bytes, uint32_t idesc, bool (&first)[kNumAcc],
+                                            uint32_t a_group_bytes = 0) {
+    const uint64_t da = smem_desc_kmajor(sA, BK * 2, a_group_bytes), db = smem_desc_kmajor(sB, BK * 2);
     const uint32_t ap = a_plane_bytes >> 4, bp = b_plane_bytes >> 4;
 #pragma unroll
     for (int kk = 0; kk < BK / 16; ++kk) {
@@ -697,10 +699,18 @@ template <int U>
 __device__ __forceinline__ long long acc_head(uint32_t b2, uint32_t b3) {
     return (long long)(acc_int(b2, 2) * 128 + acc_int(b3, 3)) << (7 * (U - 3));
 }
+// round-half-even(f 2^k) for |f 2^k| < 2^40 with 32-bit conversions only (a 64-bit conversion
+// runs on this GPU's slow FP64 pipe): t = f 2^(k-16) splits exactly into its integer part q and
+// fraction r, and f 2^k = q 2^16 + r 2^16 with q 2^16 even, so rounding r 2^16 rounds the sum.
+__device__ __forceinline__ long long f32_scaled_rint(float f, int k) {
+    const float t = f * pow2f(k - 16);
+    const int q = __float2int_rz(t);
+    const float r = t - (float)q;
+    return ((long long)q << 16) + __float2int_rn(r * 65536.0f);
+}
 template <int U>
 __device__ __forceinline__ long long acc_tail(int i4, uint32_t b5, uint32_t b6) {
-    return ((long long)(i4 * 128 + acc_int(b5, 5)) << (7 * (U - 5))) +
-           __float2ll_rn(__uint_as_float(b6) * pow2f(7 * U));
+    return ((long long)(i4 * 128 + acc_int(b5, 5)) << (7 * (U - 5))) + f32_scaled_rint(__uint_as_float(b6), 7 * U);
 }
 
 // Work of one ERI launch: up to kMaxItems items (an instance's block pair each), every one with
@@ -708,9 +718,14 @@ __device__ __forceinline__ long long acc_tail(int i4, uint32_t b5, uint32_t b6) 
 // persistent launch covers several instances.
 constexpr int kMaxItems = 32;
 
+// Rows of L^T per ERI tile: 256 rows as 32 chunks of 8 consecutive rows (one TMA box each).
+constexpr int kEriChunkRows = 8;
+constexpr int kEriTileChunks = 2 * kEmuTile / kEriChunkRows;
+
 struct EriItem {
     int nv, vp, nchol, a0, na, b0, nb, kpad;
     size_t plane_stride;  // elements between V planes
+    const int2* chunks;   // (first L^T row, rows) of every chunk, kEriTileChunks per row tile
     const int* row_start;
     const int* lt_exp;
     const int* f_tab;
@@ -719,7 +734,7 @@ struct EriItem {
 };
 
 struct EriBatch {
-    CUtensorMap ta[kMaxItems];  // L^T slices, 128-row boxes (A)
+    CUtensorMap ta[kMaxItems];  // L^T slices, 8-row boxes (A chunks)
     CUtensorMap tb[kMaxItems];  // L^T slices, 48-row boxes (B)
     EriItem item[kMaxItems];
     const int4* entries;        // (row tile, column tile, item, 0)
@@ -728,19 +743,26 @@ struct EriBatch {
 };
 
 // ------------------------------------------------------------------ ERI kernel
-// A CTA pair computes one 256-row (a,c) x 96-column (b,d) tile with 2-SM MMAs
-// (cta_group::2, M = 256): CTA r holds A rows [128r, 128r+128) and B rows
-// [48r, 48r+48) of every stage and the accumulators of its 128 rows.  Both CTAs'
-// TMA loads complete on the leader's (rank 0) full barrier; the leader issues the
-// MMAs and its commits release the stage and publish the accumulators in both CTAs;
-// the epilogue warps of both CTAs release the accumulators to the leader.
-// K = nchol runs in exact chunks of kEmuChunkK.
+// L^P is symmetric, so the rows (x,y) = x vp + y and (y,x) of L^T hold the same vector and the
+// Gram matrix only needs the rows with x <= y: (xy|bd) is V_xb at column y vp + d (x in the
+// block's a range, b >= x) and V_yb at column x vp + d (y in the a range, x < y, b >= y).
+// A CTA pair computes one 256-row x 96-column (b,d) tile with 2-SM MMAs (cta_group::2,
+// M = 256); the tile's rows are 32 chunks of 8 consecutive L^T rows taken from the row
+// segments the block needs.  CTA r holds chunks [16r, 16r+16) (A) and B rows [48r, 48r+48)
+// of every stage and the accumulators of its 128 rows.  In shared memory a stage's A part is
+// [chunk][plane][8 rows][BK]: one 3-D TMA box per chunk, and every plane is a K-major operand
+// whose 8-row groups lie S*8*BK*2 bytes apart.  Both CTAs' TMA loads complete on the leader's
+// (rank 0) full barrier; the leader issues the MMAs and its commits release the stage and
+// publish the accumulators in both CTAs; the epilogue warps of both CTAs release the
+// accumulators to the leader.  K = nchol runs in exact chunks of kEmuChunkK.
 template <int S>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsEri, 1)
     eri_emu_kernel(const __grid_constant__ EriBatch B) {
     constexpr int BK = eri_bk_for(S), STAGES = eri_stages_for(S);
-    constexpr uint32_t APLANE = kEmuTile * BK * 2, BPLANE = (kEmuTileN / 2) * BK * 2;
-    constexpr uint32_t ABYTES = S * APLANE;
+    constexpr int CPC = kEmuTile / kEriChunkRows;                       // chunks per CTA
+    constexpr uint32_t AGROUP = kEriChunkRows * BK * 2;                 // 8 rows of one plane
+    constexpr uint32_t ACHUNK = S * AGROUP, BPLANE = (kEmuTileN / 2) * BK * 2;
+    constexpr uint32_t ABYTES = CPC * ACHUNK;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     __shared__ uint64_t full[STAGES], empty[STAGES], acc_full, acc_empty, done;
@@ -780,14 +802,19 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsEri, 1)
             const int4 en = B.entries[e];
             const EriItem& p = B.item[en.z];
             const int nkb = (p.nchol + BK - 1) / BK;
-            const int arow = p.a0 * p.vp + en.x * (2 * kEmuTile) + kEmuTile * (int)rank;
+            int arow[CPC];
+            const int2* ch = p.chunks + (size_t)en.x * kEriTileChunks + CPC * (int)rank;
+#pragma unroll
+            for (int c = 0; c < CPC; ++c) arow[c] = ch[c].x;
             const int brow = p.b0 * p.vp + en.y * kEmuTileN + (kEmuTileN / 2) * (int)rank;
             for (int kb = 0; kb < nkb && ok; ++kb) {
                 if (!(ok = mbar_wait(&empty[ring.stage], ring.phase ^ 1u, B.status, kStatusTimeout))) break;
                 unsigned char* st = smem + ring.stage * eri_stage_bytes(S);
                 if (rank == 0) mbar_arrive_expect_tx(&full[ring.stage], 2 * eri_stage_bytes(S));
                 const uint32_t fb = mapa_rank(smem_u32(&full[ring.stage]), 0);
-                tma_load_3d_2sm_hint(st, &B.ta[en.z], fb, kb * BK, arow, 0, keep);
+#pragma unroll
+                for (int c = 0; c < CPC; ++c)
+                    tma_load_3d_2sm_hint(st + c * ACHUNK, &B.ta[en.z], fb, kb * BK, arow[c], 0, keep);
                 tma_load_3d_2sm_hint(st + ABYTES, &B.tb[en.z], fb, kb * BK, brow, 0, keep);
                 ring.next(STAGES);
             }
@@ -811,7 +838,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsEri, 1)
                     if (!(ok = mbar_wait(&full[ring.stage], ring.phase, B.status, kStatusTimeout))) break;
                     tc_fence_after();
                     const uint32_t st = smem_u32(smem + ring.stage * eri_stage_bytes(S));
-                    issue_pairs<S, true, BK>(tmem, st, st + ABYTES, APLANE, BPLANE, idesc, first);
+                    issue_pairs<S, true, BK>(tmem, st, st + ABYTES, AGROUP, BPLANE, idesc, first, ACHUNK);
                     mma_commit_pair_mc(&empty[ring.stage], (uint16_t)0x3);
                     ring.next(STAGES);
                 }
@@ -831,29 +858,41 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsEri, 1)
         int it = 0;
         bool ok = true;
         // With vp >= 48 the warp's 48 columns touch at most two b and two exponent groups, so
-        // the exponent tables of a tile come down to six loads per thread, issued before the
+        // the exponent tables of a tile come down to ten loads per thread, issued before the
         // accumulators are waited for so that their latency hides behind the MMAs.
         for (int e = cluster; e < B.nentries && ok; e += nclusters) {
             const int4 en = B.entries[e];
             const EriItem& p = B.item[en.z];
-            const int Mrows = p.na * p.vp, Ncols = p.nb * p.vp;
+            const int Ncols = p.nb * p.vp;
             const bool few_tables = p.vp >= 8 * kEriRuns;
             const int nkb = (p.nchol + BK - 1) / BK;
             const int nch = (nkb + kb_per_chunk - 1) / kb_per_chunk;
             const int qt = en.y;
-            const int r_local = en.x * (2 * kEmuTile) + kEmuTile * (int)rank + 32 * q + lane;
-            const int a = p.a0 + r_local / p.vp, c = r_local % p.vp;
-            const bool row_ok = r_local < Mrows && c < p.nv;
+            // this thread's tile row: chunk (first L^T row, rows) and the row (x, y) in it
+            const int r_tile = kEmuTile * (int)rank + 32 * q + lane;
+            const int2 chk = p.chunks[(size_t)en.x * kEriTileChunks + r_tile / kEriChunkRows];
+            const int row = chk.x + r_tile % kEriChunkRows;
+            const int x = row / p.vp, y = row - x * p.vp;
+            const bool row_ok = r_tile % kEriChunkRows < chk.y;
+            const bool direct = row_ok && x >= p.a0 && x < p.a0 + p.na;             // V_xb, column y
+            const bool mirror = row_ok && y > x && y >= p.a0 && y < p.a0 + p.na;    // V_yb, column x
             const int col0 = qt * kEmuTileN + 8 * kEriRuns * h;            // first column of the warp
             const int colz = min(col0 + 8 * (kEriRuns - 1), Ncols - 1);   // last valid run start
             const int bq0 = col0 / p.vp, gq0 = (p.b0 * p.vp + col0) / kG;
-            int e_ac = 0, rs = 0, f0 = 0, f1 = 0, x0 = 0, x1 = 0;
+            int e_row = 0, rs_d = 0, rs_m = 0, fd0 = 0, fd1 = 0, fm0 = 0, fm1 = 0, x0 = 0, x1 = 0;
             if (row_ok) {
-                e_ac = p.lt_exp[(p.a0 * p.vp + r_local) / kG];
-                rs = p.row_start[a - p.a0];
+                e_row = p.lt_exp[row / kG];
+                if (direct) rs_d = p.row_start[x - p.a0];
+                if (mirror) rs_m = p.row_start[y - p.a0];
                 if (few_tables && col0 < Ncols) {
-                    f0 = p.f_tab[a * p.nv + p.b0 + bq0];
-                    f1 = p.f_tab[a * p.nv + p.b0 + colz / p.vp];
+                    if (direct) {
+                        fd0 = p.f_tab[x * p.nv + p.b0 + bq0];
+                        fd1 = p.f_tab[x * p.nv + p.b0 + colz / p.vp];
+                    }
+                    if (mirror) {
+                        fm0 = p.f_tab[y * p.nv + p.b0 + bq0];
+                        fm1 = p.f_tab[y * p.nv + p.b0 + colz / p.vp];
+                    }
                     x0 = p.lt_exp[gq0];
                     x1 = p.lt_exp[(p.b0 * p.vp + colz) / kG];
                 }
@@ -866,30 +905,40 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsEri, 1)
                 if (!(ok = mbar_wait(&acc_full, (uint32_t)(it & 1), B.status, kStatusTimeout))) break;
                 tc_fence_after();
 #pragma unroll
-                for (int g = 0; g < kEriRuns; ++g) {
+                for (int g = 0; g < kEriRuns; ++g) {   // accumulators 0-1, then 2-4: fewer live registers
                     const uint32_t base = tmem + ((uint32_t)(32 * q) << 16) + 8 * (kEriRuns * h + g);
-                    uint32_t v[kNumAcc][8];
-#pragma unroll
-                    for (int j = 0; j < kNumAcc; ++j) tmem_ld8(base + j * kAccStride, v[j]);
+                    uint32_t v[3][8];
+                    tmem_ld8(base, v[0]);
+                    tmem_ld8(base + kAccStride, v[1]);
                     tmem_ld_wait();
 #pragma unroll
-                    for (int k = 0; k < 8; ++k)
-                        run[g][k] += acc_head<7>(v[0][k], v[1][k]) + acc_tail<7>(acc_int(v[2][k], 4), v[3][k], v[4][k]);
+                    for (int k = 0; k < 8; ++k) run[g][k] += acc_head<7>(v[0][k], v[1][k]);
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) tmem_ld8(base + (2 + j) * kAccStride, v[j]);
+                    tmem_ld_wait();
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) run[g][k] += acc_tail<7>(acc_int(v[0][k], 4), v[1][k], v[2][k]);
                 }
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive_remote(acc_empty_leader);
             }
             if (!ok) break;
-            if (!row_ok) continue;   // past the block or a pad row
             // With vp % 8 == 0 each run of 8 columns lies in one b and starts at d % 8 == 0, so it is
             // one 16-byte store per plane (pad columns come out zero).  With vp % 16 == 0 the runs
             // 2k, 2k+1 fill one 32-byte sector and go out as one store: partial sectors written
             // back before their other half arrives cost DRAM read-modify-writes.
             const bool sector_pairs = (p.vp & 15) == 0;
+            // Run pairs outermost, so that a pair's registers die once both targets have it.
+#pragma unroll
+            for (int gp = 0; gp < kEriRuns / 2; ++gp)
+            for (int tg = 0; tg < 2; ++tg) {   // target 0: V_xb at column y; 1: V_yb at column x
+            if (!(tg == 0 ? direct : mirror)) continue;
+            const int a = tg == 0 ? x : y, c = tg == 0 ? y : x;
+            const int rs = tg == 0 ? rs_d : rs_m, f0 = tg == 0 ? fd0 : fm0, f1 = tg == 0 ? fd1 : fm1;
             uint4 prev[S];
 #pragma unroll
-            for (int g = 0; g < kEriRuns; ++g) {
+            for (int g = 2 * gp; g < 2 * gp + 2; ++g) {
                 const int col = col0 + 8 * g;
                 const int bq = col / p.vp, b = p.b0 + bq, d = col - bq * p.vp;
                 if (col >= Ncols || a > b) continue;
@@ -901,7 +950,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsEri, 1)
                     f_ab = p.f_tab[a * p.nv + b];
                     e_bd = p.lt_exp[(p.b0 * p.vp + col) / kG];
                 }
-                const int sh = f_ab - e_ac - e_bd + 49 - 7 * S;
+                const int sh = f_ab - e_row - e_bd + 49 - 7 * S;
                 const size_t off = (size_t)(rs + (b - max(a, p.b0))) * p.kpad + (size_t)c * p.vp + d;
                 if (p.vint != nullptr) {   // 64 bytes: two whole sectors
                     __align__(16) long long N[8];
@@ -932,6 +981,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsEri, 1)
                             st_cs_32B(p.vplanes + s2 * p.plane_stride + off - 8, prev[s2],
                                       *reinterpret_cast<const uint4*>(out[s2]));
                 }
+            }
             }
         }
         failed = !ok;
@@ -1482,13 +1532,14 @@ bool eri_item(const ladder_plan_s& p, const BlockPair& bp, void* ws, EriItem* it
     const long long rows = (long long)p.nv * vp;
     const int xpad = (int)align_up((size_t)p.nchol, 8);
     if (!make_tmap(ta, at<char>(ws, p.ws.lt_slices), p.nchol, rows, S, (uint64_t)xpad * 2, (uint64_t)rows * xpad * 2,
-                   EBK, kEmuTile) ||
+                   EBK, kEriChunkRows) ||
         !make_tmap(tb, at<char>(ws, p.ws.lt_slices), p.nchol, rows, S, (uint64_t)xpad * 2, (uint64_t)rows * xpad * 2,
                    EBK, kEmuTileN / 2))
         return false;
     const int* row_start = reinterpret_cast<const int*>(p.d_tables) + bp.rows_off;
+    const int2* chunks = reinterpret_cast<const int2*>(p.d_tables) + bp.chunks_off;
     *it = EriItem{p.nv, vp, p.nchol, bp.a0, bp.a1 - bp.a0, bp.b0, bp.b1 - bp.b0, (int)rows,
-                  (size_t)p.max_pairs * (size_t)rows, row_start, at<int>(ws, p.ws.lt_exp), at<int>(ws, p.ws.v_exp),
+                  (size_t)p.max_pairs * (size_t)rows, chunks, row_start, at<int>(ws, p.ws.lt_exp), at<int>(ws, p.ws.v_exp),
                   at<__nv_bfloat16>(ws, p.ws.v_blk), p.form == 1 ? at<long long>(ws, p.ws.v_blk) : nullptr};
     return true;
 }

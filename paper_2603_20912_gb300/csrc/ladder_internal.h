@@ -44,8 +44,9 @@ struct BlockPair {
     int npairs;        // number of (a, b) with a <= b in the block pair
     size_t pairs_off;  // offset (in int2) of this block pair's pair list in the device table
     size_t rows_off;   // offset (in int) of this block pair's row_start table (a1 - a0 + 1 ints)
-    size_t tiles_off = 0;  // emulated path: offset (in int2) of the ERI entries (int4: rt, qt0, qt1, 0)
+    size_t tiles_off = 0;  // emulated path: offset (in int2) of the ERI entries (int4: rt, qt, 0, 0)
     int ntiles = 0;        // emulated path: number of ERI entries (one 2-CTA cluster each)
+    size_t chunks_off = 0; // emulated path: offset (in int2) of the ERI row chunks (first L^T row, rows)
 };
 
 // Workspace layout of one plan (byte offsets from the workspace base).

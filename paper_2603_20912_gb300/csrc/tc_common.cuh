@@ -267,10 +267,10 @@ __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.
 // ---------------------------------------------------------------- descriptors
 // Shared-memory matrix descriptor (tcgen05): K-major operand, rows of
 // `row_bytes` (32, 64 or 128 = the swizzle span), 8-row core groups
-// `8 * row_bytes` apart.  Swizzle codes: 128B = 2, 64B = 4, 32B = 6.
-__device__ __forceinline__ uint64_t smem_desc_kmajor(uint32_t saddr, uint32_t row_bytes) {
+// `group_bytes` apart (default 8 * row_bytes: dense).  Swizzle codes: 128B = 2, 64B = 4, 32B = 6.
+__device__ __forceinline__ uint64_t smem_desc_kmajor(uint32_t saddr, uint32_t row_bytes, uint32_t group_bytes = 0) {
     const uint32_t swz = row_bytes == 128 ? 2u : (row_bytes == 64 ? 4u : 6u);
-    const uint64_t sbo = (8u * row_bytes) >> 4;
+    const uint64_t sbo = (group_bytes ? group_bytes : 8u * row_bytes) >> 4;
     uint64_t d = 0;
     d |= (uint64_t)((saddr >> 4) & 0x3FFFu);      // start address, bits [0,14)
     d |= (uint64_t)1u << 16;                       // leading byte offset (unused for swizzled K-major)

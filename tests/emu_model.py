@@ -20,7 +20,9 @@ Scheme (FP64 emulated by BF16 digit slices, Ozaki-style splitting):
   (chunks of K <= 1024): each has its own FP32 accumulator; the levels >= 6
   share a fifth (inexact, weight <= 2^-28 of the leading level).
 * ERI (K = nchol): the level sums form I = acc2 2^35 + acc3 2^28 + acc4 2^21
-  + acc5 2^14 + round(A6 2^49), V = 2^(e_ac + e_bd - 49) I.  V is re-sliced
+  + acc5 2^14 + round(A6 2^49), V = 2^(e_ac + e_bd - 49) I, where the row
+  (a, c) of L^T is taken as (min(a, c), max(a, c)) (the same vector: L^P is
+  symmetric; the kernels multiply only those rows).  V is re-sliced
   per pair row (a, b) with the exponent f_ab of the Cauchy-Schwarz bound
   |(ac|bd)| <= max_c ||L_ac|| max_d ||L_bd||.
 * Entries where a row of L^T meets itself, V_ab,ba = ||L_ab||^2 and
@@ -138,10 +140,18 @@ def emulated_ladder(L: np.ndarray, t2: np.ndarray, S: int = 6, group: int = GROU
         a2, a3, a4, a5, a6 = level_sums(dL[:, :, sl], dL[:, :, sl])   # [(ac), (bd)]
         I += (a2 << 35) + (a3 << 28) + (a4 << 21) + (a5 << 14) + np.rint(np.ldexp(a6, 49)).astype(np.int64)
     f = pair_exponent_bound(L)
-    # rows (a, c), cols (b, d) -> V[(a, b), (c, d)]
-    I4 = I.reshape(nv, nv, nv, nv).transpose(0, 2, 1, 3)          # [a, b, c, d]
-    e4 = eL.reshape(nv, nv)                                      # e_ac
-    sh = f[:, :, None, None] - e4[:, None, :, None] - e4[None, :, None, :] + 49 - DIGIT_BITS * S
+    # rows (a, c), cols (b, d) -> V[(a, b), (c, d)].  L^P is symmetric, so the rows (a, c) and
+    # (c, a) of L^T hold the same vector; the kernels multiply only the rows with a <= c, and
+    # V_ab,cd comes from the row (min(a, c), max(a, c)) with that row's digits and exponent.
+    ar = np.arange(nv)
+    lo = np.minimum(ar[:, None], ar[None, :])
+    hi = np.maximum(ar[:, None], ar[None, :])
+    Ir = I.reshape(nv, nv, nv, nv)                               # [a, c, b, d]
+    I4 = Ir[lo, hi].transpose(0, 2, 1, 3)                        # [a, b, c, d]
+    e2 = eL.reshape(nv, nv)
+    e4 = e2[lo, hi]                                              # e of the row used for (a, c)
+    eb = e2                                                      # e of the column row (b, d)
+    sh = f[:, :, None, None] - e4[:, None, :, None] - eb[None, :, None, :] + 49 - DIGIT_BITS * S
     Np = _round_shift(I4, sh).reshape(nv * nv, nv * nv)          # rows (a, b), K = (c, d)
     if exact_self:
         sq = np.sum(L * L, axis=0)                               # [a, c] = ||L[:, a, c]||^2
