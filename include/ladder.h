@@ -23,7 +23,11 @@
  *   Device pointers must be 256-byte aligned, otherwise LADDER_ERR_ARG.
  * - Precondition ASSUMED, not checked: t2[i,j,a,b] == t2[j,i,b,a].  The
  *   a <= b packing relies on it (with a non-symmetric t2 the result differs
- *   from the definition).  Symmetry of L[P] in (a, c) is not required.
+ *   from the definition).  The emulated path (LADDER_EMU_BF16) also assumes
+ *   L[P,a,c] == L[P,c,a], as Cholesky vectors of (ac|bd) with real orbitals
+ *   are: it multiplies only the rows (a <= c) of L^T and takes the entries
+ *   where a row meets itself from squared norms.  The FP64 path needs no
+ *   symmetry of L.
  * - Ownership: the caller owns L, t2, R and the workspace.  A plan owns only
  *   host metadata and a small device table written at plan time.
  * - ladder_apply / ladder_apply_batched perform no allocation and no host

@@ -121,6 +121,13 @@ def test_edge_shapes(no, nv, nchol):
     assert rel_fro(R, oracle.ladder(L, t2)) <= TOL_R
 
 
+def test_nonsymmetric_L_violates_the_emulated_precondition():
+    # The emulated path multiplies only the rows (a <= c) of L^T (L[P] symmetric in (a, c)).
+    L, t2 = make_integer_inputs(3, 11, 13, seed=7, symmetric_L=False)
+    R, _ = gpu_ladder(L, t2, EMU)
+    assert rel_fro(R, oracle.ladder(L, t2)) > 1e-3
+
+
 def test_deterministic():
     L, t2, _, _ = make_inputs(5, 45, 60, seed=41)
     R1, _ = gpu_ladder(L, t2, EMU)
