@@ -47,8 +47,8 @@ NOMINAL_FP64_TFLOPS = 1.25
 # sources hash to the value recorded with the capture; any change to them makes it null.
 TRAFFIC_CAPTURES = {
     # (precision, workload): (sources sha256 prefix, bytes per launch, profiles/ summary)
-    ("emu", "c2"): ("20e7275c739538cd", 9759341568 + 12133569024, "profiles/dram_traffic_no10_nv200_nchol630.md"),
-    ("fp64", "c2"): ("20e7275c739538cd", 49997810432 + 6438575104, "profiles/dram_traffic_no10_nv200_nchol630.md"),
+    ("emu", "c2"): ("a9abc7ac756ca71c", 19813719040 + 14225706240, "profiles/dram_traffic_no10_nv200_nchol630.md"),
+    ("fp64", "c2"): ("a9abc7ac756ca71c", 50267811584 + 6436400896, "profiles/dram_traffic_no10_nv200_nchol630.md"),
 }
 KERNEL_SOURCE_DIR = os.path.join(ROOT, "paper_2603_20912_gb300", "csrc")
 
@@ -369,8 +369,12 @@ def run_batched(args):
     peak = peaks.get(peak_key, peaks.get("bf16_tflops", FALLBACK_BF16_TFLOPS))
     roof = None
     if precision == lad.LADDER_EMU_BF16:
+        # executed slice products of the work each instance needs (one block pair per instance:
+        # every instance's V fits the budget; plain ladder form, as batched instances use)
         S = args.nslices or 6
-        achieved = value / world * (S * (S + 1) // 2)
+        useful = sum(2.0 * s.nchol * eri_products(s.nv, s.nv, s.nv) + 2.0 * ladder_products(s.no, s.nv, "plain")
+                     for s in shapes)
+        achieved = useful * (S * (S + 1) // 2) * args.steps / (ms_total * 1e-3) / 1e12
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "frac_of_burst": achieved / peaks.get("bf16_tflops", FALLBACK_BF16_TFLOPS),
                 "traffic": None, "kernel": "whole batched call (executed slice products, all kernels)",
