@@ -109,9 +109,9 @@ ladder::WsLayout layout_for(const ladder_plan_s& p, long long max_pairs) {
     if (p.precision == LADDER_FP64) {
         w.v_blk = take((size_t)max_pairs * nv2 * sizeof(double));
     } else {
-        // (c, d) rows padded to vp = nv rounded up to 8: K index c*vp + d, zero for d >= nv.
+        // (c, d) rows padded to vp (ladder::emu_vp): K index c*vp + d, zero for d >= nv.
         const size_t S = p.nslices;
-        const size_t vp = align_up((size_t)p.nv, 8), nvp = (size_t)p.nv * vp;
+        const size_t vp = (size_t)ladder::emu_vp(p.nv), nvp = (size_t)p.nv * vp;
         const size_t kpad = nvp, xpad = align_up((size_t)p.nchol, 8);
         const size_t G = ladder::kExpGroupRows;
         // V digit planes, or V as int64 for the symmetric/antisymmetric form (combined first)
@@ -181,7 +181,7 @@ struct EriRowTiles {
 };
 
 EriRowTiles eri_row_tiles(const BlockPair& bp, int nv) {
-    const int vp = (nv + 7) / 8 * 8, cr = ladder::kEmuTile * 2 / 32;   // 8 rows per chunk
+    const int vp = ladder::emu_vp(nv), cr = ladder::kEmuTile * 2 / 32;   // 8 rows per chunk
     EriRowTiles t;
     std::vector<int> ckey;
     auto segment = [&](int x, int y0, int y1, bool upper) {
@@ -208,7 +208,7 @@ EriRowTiles eri_row_tiles(const BlockPair& bp, int nv) {
 // every column tile of the band streams past it.
 std::vector<int> eri_entries(const BlockPair& bp, int nv, int tile_n, size_t row_bytes) {
     const EriRowTiles rt = eri_row_tiles(bp, nv);
-    nv = (nv + 7) / 8 * 8;  // columns run over the padded (b, d) range
+    nv = ladder::emu_vp(nv);  // columns run over the padded (b, d) range
     std::vector<int> out;
     const long long N = (long long)(bp.b1 - bp.b0) * nv;
     const int nrt = (int)rt.key.size(), nqt = (int)((N + tile_n - 1) / tile_n);
@@ -398,7 +398,7 @@ struct DeviceGuard {
 int auto_form(int no, int nv, int nchol, int nslices) {
     const double pairs = 0.5 * nv * (nv + 1.0);
     auto rows_pad = [](double r) { return r <= ladder::kEmuTile ? ladder::kEmuTile : std::ceil(r / 256.0) * 256.0; };
-    const double vp = std::ceil(nv / 8.0) * 8.0;
+    const double vp = ladder::emu_vp(nv);
     const double per_row_k = pairs * 2.0 * nslices * (nslices + 1) / 2 / 1.3e15;   // s per (row, K element)
     const double eri = (double)nchol * nv * vp * per_row_k;
     const double plain = eri + rows_pad((double)no * no) * nv * vp * per_row_k;

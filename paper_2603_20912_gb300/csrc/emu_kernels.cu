@@ -1470,8 +1470,8 @@ T* at(void* ws, size_t off) {
 }
 
 
-// Padded (c, d) layout of the emulated path: vp = nv rounded up to 8, K = nv * vp.
-inline int padded_vp(int nv) { return (nv + 7) / 8 * 8; }
+// Padded (c, d) layout of the emulated path: vp = nv rounded up to 16 (emu_vp), K = nv * vp.
+inline int padded_vp(int nv) { return emu_vp(nv); }
 
 template <int S>
 cudaError_t prep_impl(const ladder_plan_s& p, const double* L, const double* t2, void* ws, cudaStream_t s) {

@@ -73,6 +73,11 @@ struct WsLayout {
 };
 
 // Symmetric/antisymmetric ladder form: packed sizes of its K and row ranges.
+// Padded (c, d) layout of the emulated path: vp = nv rounded up to 16, K index c * vp + d (zero
+// for d >= nv).  With vp % 16 == 0 every pair of 8-column runs of a V row is one whole 32-byte
+// sector, so V never leaves L2 half written.
+inline int emu_vp(int nv) { return (nv + 15) / 16 * 16; }
+
 // Packed (c,d) index of the symmetric (c <= d, plus) and antisymmetric (c < d) forms, in
 // 4-byte words of two slots (d even, d + 1): row c holds the words that contain one of its
 // elements, from d = c (plus) or c + 1 rounded down to even up to d = nv - 1, so element (c,d)

@@ -10,7 +10,7 @@ Scheme (FP64 emulated by BF16 digit slices, Ozaki-style splitting):
 
 * Row groups of G consecutive rows share one exponent e with
   max|x| < 2^(e-1), so u = x 2^-e lies in (-1/2, 1/2).  The rows of L^T are
-  (a, c) with c padded to vp = nv rounded up to 8 (zero pad rows), so the
+  (a, c) with c padded to vp = nv rounded up to 16 (zero pad rows), so the
   groups are 64 consecutive padded rows, as in the kernels.
 * N = round_half_even(x 2^(7S - e)) (|N| <= 2^(7S-1)) is written in
   balanced base 128: N = sum_s d_s 128^(S-s), |d_s| <= 64.  Slice plane s
@@ -128,7 +128,7 @@ def emulated_ladder(L: np.ndarray, t2: np.ndarray, S: int = 6, group: int = GROU
     (the uncorrected scheme, for comparison)."""
     nchol, nv, _ = L.shape
     no = t2.shape[0]
-    vp = (nv + 7) // 8 * 8
+    vp = (nv + 15) // 16 * 16                                     # the kernels' padded layout
     Ltp = np.zeros((nv, vp, nchol))
     Ltp[:, :nv, :] = L.transpose(1, 2, 0)                        # rows (a, c padded), K = P
     dLp, eLp = to_digits(Ltp.reshape(nv * vp, nchol), S, group)

@@ -63,7 +63,7 @@ def test_c1_matches_cpu_model_of_the_scheme():
 
 @pytest.mark.parametrize("no,nv,nchol", [(3, 32, 50), (2, 47, 40), (4, 80, 33)])
 def test_sector_paired_layouts_match_the_model(no, nv, nchol):
-    # nv rounded up to 8 is a multiple of 16 here: the ERI epilogue stores V in whole
+    # vp (nv rounded up to 16): the ERI epilogue stores V in whole
     # 32-byte sectors.  Same digits as the model, and blocking-independent bit for bit.
     # With K = nv^2 near a full 1024 chunk the FP32 accumulator of the levels >= 6 is no
     # longer exact (the model keeps it in FP64); modelling it as FP32 with truncation moves
