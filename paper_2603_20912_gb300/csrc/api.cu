@@ -390,7 +390,7 @@ struct DeviceGuard {
 };
 
 // Emulated ladder form from a cost model of a whole call over all a <= b pairs: the ERI (the same
-// in both forms; K = nchol), the ladder GEMM, whose MMA rows are padded to its tiles (128 rows
+// in both forms; K = nchol, symmetric rows), the ladder GEMM, whose MMA rows are padded to its tiles (128 rows
 // on one SM up to 128 (i,j) rows, else 256 on CTA pairs) and which the symmetric/antisymmetric
 // form halves in K and splits into rows i <= j and i < j, and the split's one pass that reads V
 // as int64 and writes the V' and V'' digit planes (~3.5 TB/s measured).  The split is chosen
@@ -400,7 +400,9 @@ int auto_form(int no, int nv, int nchol, int nslices) {
     auto rows_pad = [](double r) { return r <= ladder::kEmuTile ? ladder::kEmuTile : std::ceil(r / 256.0) * 256.0; };
     const double vp = ladder::emu_vp(nv);
     const double per_row_k = pairs * 2.0 * nslices * (nslices + 1) / 2 / 1.3e15;   // s per (row, K element)
-    const double eri = (double)nchol * nv * vp * per_row_k;
+    // the ERI multiplies the rows x <= y of L^T against the columns b >= x: (2 nv + 1) / (3 nv)
+    // of the a <= b pairs' row-column products
+    const double eri = (double)nchol * nv * vp * per_row_k * (2.0 * nv + 1.0) / (3.0 * nv);
     const double plain = eri + rows_pad((double)no * no) * nv * vp * per_row_k;
     const ladder::PmDims d = ladder::pm_dims(no, nv);
     double pm = eri + rows_pad(d.np) * (double)d.kp * per_row_k;
