@@ -431,7 +431,7 @@ __global__ void __launch_bounds__(256) tpm_rowmax_kernel(const double* __restric
         atomicMax((plus ? gmax_p : gmax_m) + r / kG, (unsigned long long)__double_as_longlong(m));
 }
 
-// T' and T'' digit planes: one block per packed row, threads over the rows c of its (c,d) triangle.
+// T' and T'' digit planes: one block per packed row (i,j).
 template <int S>
 __global__ void __launch_bounds__(128) tpm_slice_kernel(const double* __restrict__ t2, int no, int nv, int np,
                                                         long long kp_pad, long long km_pad, int nm,
@@ -452,11 +452,12 @@ __global__ void __launch_bounds__(128) tpm_slice_kernel(const double* __restrict
     const size_t plane = (size_t)(plus ? np : nm) * kpad;
     __nv_bfloat16* out = (plus ? tp : tm) + (size_t)r * kpad;
     const int dend = 2 * ((nv - 1) / 2) + 1;   // last slot of every row's last word
-    for (int c = threadIdx.x; c < (plus ? nv : nv - 1); c += blockDim.x) {
+    // Rows c in turn, threads over its slots (coalesced reads of t_ij and t_ji, coalesced stores).
+    for (int c = 0; c < (plus ? nv : nv - 1); ++c) {
         const long long k0 = pm_base(c, nv, plus);
         const int dlo = plus ? c : c + 1;
-        for (int d = dlo & ~1; d <= dend; ++d) {   // whole words: the slots outside the row get zero
-            double v = 0.0;
+        for (int d = (dlo & ~1) + (int)threadIdx.x; d <= dend; d += blockDim.x) {   // whole words
+            double v = 0.0;   // the slots outside the row get zero
             if (d >= dlo && d < nv) {
                 const double a = __ldg(tij + (size_t)c * nv + d), b = __ldg(tji + (size_t)c * nv + d);
                 v = plus ? (c == d ? a : 0.5 * (a + b)) : 0.5 * (a - b);
@@ -924,11 +925,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsEri, 1)
                 if (lane == 0) mbar_arrive_remote(acc_empty_leader);
             }
             if (!ok) break;
-            // With vp % 8 == 0 each run of 8 columns lies in one b and starts at d % 8 == 0, so it is
-            // one 16-byte store per plane (pad columns come out zero).  With vp % 16 == 0 the runs
-            // 2k, 2k+1 fill one 32-byte sector and go out as one store: partial sectors written
-            // back before their other half arrives cost DRAM read-modify-writes.
-            const bool sector_pairs = (p.vp & 15) == 0;
+            // With vp % 16 == 0 each run of 8 columns lies in one b and starts at d % 8 == 0, and the
+            // runs 2k, 2k+1 (same b) fill one 32-byte sector, which goes out as one store per plane
+            // (pad columns come out zero): half-written sectors would come back from DRAM.
             // Run pairs outermost, so that a pair's registers die once both targets have it.
 #pragma unroll
             for (int gp = 0; gp < kEriRuns / 2; ++gp)
@@ -965,13 +964,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsEri, 1)
                 __align__(16) __nv_bfloat162 out[S][4];
                 slice_run<S>(run[g], sh, out, B.status);
                 // streaming stores: V is read back only by the ladder
-                if (!sector_pairs) {
-#pragma unroll
-                    for (int s2 = 0; s2 < S; ++s2)
-                        if (LADDER_IN_BOUNDS(off + 8 <= p.plane_stride, B.status))
-                            __stcs(reinterpret_cast<uint4*>(p.vplanes + s2 * p.plane_stride + off),
-                                   *reinterpret_cast<const uint4*>(out[s2]));
-                } else if ((g & 1) == 0) {  // runs 2k, 2k+1: same b, both valid or both skipped
+                if ((g & 1) == 0) {  // runs 2k, 2k+1: same b, both valid or both skipped
 #pragma unroll
                     for (int s2 = 0; s2 < S; ++s2) prev[s2] = *reinterpret_cast<const uint4*>(out[s2]);
                 } else {
@@ -1529,6 +1522,7 @@ template <int S>
 bool eri_item(const ladder_plan_s& p, const BlockPair& bp, void* ws, EriItem* it, CUtensorMap* ta, CUtensorMap* tb) {
     constexpr int EBK = eri_bk_for(S);
     const int vp = padded_vp(p.nv);
+    if (vp % 16 != 0) return false;   // the epilogue stores whole 32-byte sectors
     const long long rows = (long long)p.nv * vp;
     const int xpad = (int)align_up((size_t)p.nchol, 8);
     if (!make_tmap(ta, at<char>(ws, p.ws.lt_slices), p.nchol, rows, S, (uint64_t)xpad * 2, (uint64_t)rows * xpad * 2,
