@@ -537,6 +537,15 @@ def main():
         dtype = "f64"
     if traffic_src:
         roof["traffic_source"] = traffic_src
+    if form_used == "pm" and kms.get("combine", 0.0) > 0:
+        # The split form's combine pass is HBM work: it reads V as int64 and writes the V' and V''
+        # digit planes, (8 + 2S) bytes per V element of the a <= b pairs.
+        comb_bytes = (8 + 2 * desc["nslices"]) * nv2 * pairs_total
+        comb_gbs = comb_bytes * args.steps / (kms["combine"] * 1e-3) / 1e9
+        hbm = peaks.get("hbm_gbs", FALLBACK_HBM_GBS)
+        roof["combine"] = {"bound": "hbm", "achieved": comb_gbs, "peak": hbm, "unit": "GB/s",
+                           "frac": comb_gbs / hbm, "kernel": "vpm_combine_kernel",
+                           "bytes_per_call": comb_bytes}
     # The whole call against the same peak (every kernel of the step, executed flops).
     if precision == lad.LADDER_EMU_BF16:
         useful = eri_flops_call + 2.0 * ladder_products(cfg.no, cfg.nv, form_used)
