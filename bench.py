@@ -47,8 +47,8 @@ NOMINAL_FP64_TFLOPS = 1.25
 # sources hash to the value recorded with the capture; any change to them makes it null.
 TRAFFIC_CAPTURES = {
     # (precision, workload): (sources sha256 prefix, bytes per launch, profiles/ summary)
-    ("emu", "c2"): ("3ae670831ab76026", 13470540288 + 10954794240, "profiles/dram_traffic_no10_nv200_nchol630.md"),
-    ("fp64", "c2"): ("3ae670831ab76026", 50274909696 + 6438905088, "profiles/dram_traffic_no10_nv200_nchol630.md"),
+    ("emu", "c2"): ("dc648a0aa46087db", 12063834880 + 10939927808, "profiles/dram_traffic_no10_nv200_nchol630.md"),
+    ("fp64", "c2"): ("dc648a0aa46087db", 49657817856 + 6438093312, "profiles/dram_traffic_no10_nv200_nchol630.md"),
 }
 KERNEL_SOURCE_DIR = os.path.join(ROOT, "paper_2603_20912_gb300", "csrc")
 

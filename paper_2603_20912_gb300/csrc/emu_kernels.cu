@@ -1650,7 +1650,9 @@ cudaError_t block_pm_impl(const ladder_plan_s& p, const BlockPair& bp, double* R
     const bool has_y = d.nm > 0 && d.km > 0;
     cudaError_t e;
     if ((e = cudaMemsetAsync(at<char>(ws, p.ws.rpx), 0, (size_t)bp.npairs * d.np * 8, s)) != cudaSuccess) return e;
-    if (has_y && (e = cudaMemsetAsync(at<char>(ws, p.ws.rpy), 0, (size_t)bp.npairs * d.nm * 8, s)) != cudaSuccess)
+    // Y's accumulator starts at zero whenever there are rows i < j, also when K'' is empty
+    // (nv = 1): the finalisation reads it for those rows.
+    if (d.nm > 0 && (e = cudaMemsetAsync(at<char>(ws, p.ws.rpy), 0, (size_t)bp.npairs * d.nm * 8, s)) != cudaSuccess)
         return e;
     const int2* table = reinterpret_cast<const int2*>(p.d_tables);
     EriBatch eb{};

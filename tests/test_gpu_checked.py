@@ -1,8 +1,10 @@
 """The index-checked build (-DLADDER_CHECK): every store of the emulated kernels into the
 workspace and into R tests its index and, on failure, records LADDER_ERR_BOUNDS and skips
 the store (no trap, no fault).  Small shapes covering the kernels' index paths - ragged tiles,
-padded layouts, whole-sector V stores, both ladder shapes, forced blockings and the grouped
-batched schedule - must run with a clean status and the usual parity."""
+padded layouts, whole-sector V stores, both ladder shapes, forced blockings, the
+symmetric/antisymmetric form (int64 V, combine pass, T' and T'' slices, two ladder items, four-way
+finalisation) and the grouped batched schedule - must run with a clean status and the usual
+parity."""
 import json
 import os
 import subprocess
@@ -38,6 +40,20 @@ for no, nv, x, blocks in cases:
     out.append({"shape": [no, nv, x], "status": plan.last_status(),
                 "rel": rel(R.cpu().numpy(), oracle.ladder(L, t2))})
 
+# the symmetric/antisymmetric form: odd and even nv, one tile and several, both ladder shapes
+for no, nv, x, blocks in [(5, 19, 72, None), (1, 7, 9, None), (2, 1, 5, None), (4, 45, 60, (7, 3)),
+                          (18, 30, 40, None), (3, 64, 70, None)]:
+    L, t2, _, _ = make_inputs(no, nv, x, seed=no * 100 + nv + 1)
+    plan = lad.ladder_plan(no, nv, x, EMU)
+    plan.set_form(1)
+    if blocks:
+        plan.set_blocks(*blocks)
+    R = torch.zeros(t2.shape, dtype=torch.float64, device="cuda")
+    lad.ladder_apply(plan, torch.from_numpy(L).cuda(), torch.from_numpy(t2).cuda(), R)
+    torch.cuda.synchronize()
+    out.append({"shape": [no, nv, x, "pm"], "status": plan.last_status(),
+                "rel": rel(R.cpu().numpy(), oracle.ladder(L, t2))})
+
 shapes = [(5, 19, 72), (3, 37, 45), (12, 40, 60), (2, 88, 50)]
 host = [make_inputs(o, v, x, seed=700 + k)[:2] for k, (o, v, x) in enumerate(shapes)]
 plan = lad.ladder_plan_batched([s[0] for s in shapes], [s[1] for s in shapes], [s[2] for s in shapes], EMU)
@@ -60,7 +76,7 @@ def test_checked_build_runs_clean():
                        timeout=900)
     assert r.returncode == 0, r.stdout[-3000:] + r.stderr[-3000:]
     results = json.loads(r.stdout.strip().splitlines()[-1])
-    assert len(results) == 11
+    assert len(results) == 17
     for res in results:
         assert res["status"] == 0, res
         assert res["rel"] <= 1e-10, res
