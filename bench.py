@@ -43,29 +43,34 @@ NOMINAL_FP64_TFLOPS = 1.25
 
 
 # DRAM traffic (ncu dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the dominant
-# kernel, from a single-pass capture of this workload.  It is reported only while the kernel
-# sources hash to the value recorded with the capture; any change to them makes it null.
+# kernel, from a single-pass capture of this workload.  It is reported only while the sources
+# holding device code hash to the value recorded with the capture and the plan has the blocking
+# it had then; any change to either makes it null.
 TRAFFIC_CAPTURES = {
-    # (precision, workload): (sources sha256 prefix, bytes per launch, profiles/ summary)
-    ("emu", "c2"): ("dc648a0aa46087db", 12063834880 + 10939927808, "profiles/dram_traffic_no10_nv200_nchol630.md"),
-    ("fp64", "c2"): ("dc648a0aa46087db", 49657817856 + 6438093312, "profiles/dram_traffic_no10_nv200_nchol630.md"),
+    # (precision, workload): (device sources sha256 prefix, bytes per launch, profiles/ summary,
+    #                         (n_a, n_b))
+    ("emu", "c2"): ("efd514e3bd5bd3a9", 12063834880 + 10939927808, "profiles/dram_traffic_no10_nv200_nchol630.md",
+                    (200, 200)),
+    ("fp64", "c2"): ("efd514e3bd5bd3a9", 49657817856 + 6438093312, "profiles/dram_traffic_no10_nv200_nchol630.md",
+                     (200, 200)),
 }
 KERNEL_SOURCE_DIR = os.path.join(ROOT, "paper_2603_20912_gb300", "csrc")
+HOST_ONLY_SOURCES = {"api.cu"}   # the planner and the C ABI glue: no device code
 
 
 def kernel_sources_sha() -> str:
     import hashlib
     h = hashlib.sha256()
     for name in sorted(os.listdir(KERNEL_SOURCE_DIR)):
-        if name.endswith((".cu", ".cuh", ".h")):
+        if name.endswith((".cu", ".cuh", ".h")) and name not in HOST_ONLY_SOURCES:
             with open(os.path.join(KERNEL_SOURCE_DIR, name), "rb") as f:
                 h.update(name.encode() + b"\0" + f.read())
     return h.hexdigest()[:16]
 
 
-def captured_traffic(precision: str, workload: str):
+def captured_traffic(precision: str, workload: str, blocking):
     rec = TRAFFIC_CAPTURES.get((precision, workload))
-    if rec is None or rec[0] != kernel_sources_sha():
+    if rec is None or rec[0] != kernel_sources_sha() or tuple(rec[3]) != tuple(blocking):
         return None, None
     return rec[1], rec[2]
 
@@ -511,7 +516,7 @@ def main():
     long_region = ms_total >= 1000.0
     peak_key = "bf16_tflops_sustained" if long_region else "bf16_tflops"
     bf16 = peaks.get(peak_key, peaks.get("bf16_tflops", FALLBACK_BF16_TFLOPS))
-    traffic, traffic_src = captured_traffic(args.precision, cfg.name)
+    traffic, traffic_src = captured_traffic(args.precision, cfg.name, (desc["n_a"], desc["n_b"]))
     burst = peaks.get("bf16_tflops", FALLBACK_BF16_TFLOPS)
     if precision == lad.LADDER_EMU_BF16:
         S = desc["nslices"]

@@ -150,7 +150,37 @@ long long max_pairs_of(const std::vector<BlockPair>& bps) {
     return m;
 }
 
-std::vector<int> eri_entries(const BlockPair& bp, int nv, int tile_n, size_t row_bytes);
+// Number of ERI entries (tiles) eri_entries keeps for one block pair, from the row segments and
+// the column-tile rule directly: segment by segment, 32 chunks to a tile, a tile with smallest
+// key k meeting the column tiles whose last b reaches k (no chunk list is built).
+long long eri_tile_count(const BlockPair& bp, int nv, int tile_n) {
+    const int vp = ladder::emu_vp(nv), cr = 8;
+    const long long N = (long long)(bp.b1 - bp.b0) * vp, nqt = (N + tile_n - 1) / tile_n;
+    auto cols = [&](int key) -> long long {   // column tiles holding a b >= key
+        const long long first = (long long)std::max(0, key - bp.b0) * vp;
+        return first >= N ? 0 : nqt - first / tile_n;
+    };
+    long long total = 0;
+    int in_tile = 0, kmin = nv;
+    // m chunks with keys key0, key0 + step, ... (ascending within the segment)
+    auto segment = [&](long long m, int key0, int step) {
+        for (long long j = 0; j < m;) {
+            const long long take = std::min<long long>(m - j, 32 - in_tile);
+            kmin = std::min(kmin, key0 + step * (int)j);
+            in_tile += (int)take;
+            j += take;
+            if (in_tile == 32) {
+                total += cols(kmin);
+                in_tile = 0;
+                kmin = nv;
+            }
+        }
+    };
+    for (int x = bp.a0; x < bp.a1; ++x) segment((nv - x + cr - 1) / cr, x, 0);
+    for (int x = 0; x < bp.a0; ++x) segment((bp.a1 - bp.a0 + cr - 1) / cr, bp.a0, cr);
+    if (in_tile > 0) total += cols(kmin);
+    return total;
+}
 
 double model_time(const ladder_plan_s& p, const std::vector<BlockPair>& bps) {
     const Geometry g = geometry_for(p);
@@ -159,7 +189,7 @@ double model_time(const ladder_plan_s& p, const std::vector<BlockPair>& bps) {
     double t = 0.0;
     for (auto& bp : bps) {
         const long long te = p.precision == LADDER_FP64 ? count_eri_tiles(bp, p.nv, g.eri_tm, g.eri_tn)
-                                                        : (long long)eri_entries(bp, p.nv, g.eri_tn, 0).size() / 4;
+                                                        : eri_tile_count(bp, p.nv, g.eri_tn);
         const long long tl = ((long long)(bp.npairs + g.lad_tm - 1) / g.lad_tm) * nt;
         t += std::ceil(te / (p.precision == LADDER_FP64 ? slots_e : slots_e / 2)) * g.eri_occ * g.eri_tile_s;
         t += std::ceil(tl / slots_l) * g.lad_occ * g.lad_tile_s;
