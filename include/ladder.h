@@ -124,6 +124,9 @@ int ladder_plan_set_form(ladder_plan_t plan, int form);
  * large share of the call: large no^2 with respect to the 128/256-row MMA tiles and to nchol)
  * and the workspace fits, else 0.  The instances of a batched plan use form 0.  -1 for NULL. */
 int ladder_plan_get_form(ladder_plan_t plan);
+/* The form the cost model above picks for an emulated plan of this shape (nslices 0 = the
+ * default), before the workspace check: 0 or 1; -1 for invalid arguments.  Host only. */
+int ladder_form_model(int no, int nv, int nchol, int nslices);
 
 /*
  * Data-parallel sharding over several GPUs (the multi-GPU direction named in

@@ -66,6 +66,8 @@ def _load():
     lib.ladder_plan_set_form.restype = ci
     lib.ladder_plan_get_form.argtypes = [vp]
     lib.ladder_plan_get_form.restype = ci
+    lib.ladder_form_model.argtypes = [ci, ci, ci, ci]
+    lib.ladder_form_model.restype = ci
     lib.ladder_batched_schedule.argtypes = [vp, ci, pint]
     lib.ladder_batched_schedule.restype = ci
     lib.ladder_watchdog_selftest.argtypes = [ctypes.POINTER(ctypes.c_double), vp]
@@ -260,6 +262,14 @@ def ladder_plan_dry(no, nv, nchol, precision=LADDER_FP64, nslices=0, ws_budget_b
     return {"n_a": na.value, "n_b": nb.value, "ws_bytes": ws.value, "n_block_pairs": nbp.value, "blocks": blocks}
 
 
+def ladder_form_model(no, nv, nchol, nslices=0) -> int:
+    """Form the emulated path's cost model picks for a shape (0 plain, 1 symmetric/antisymmetric)."""
+    r = int(_load().ladder_form_model(int(no), int(nv), int(nchol), int(nslices)))
+    if r < 0:
+        raise LadderError(LADDER_ERR_ARG, "ladder_form_model")
+    return r
+
+
 def ladder_shard_blocks(npairs, world: int):
     """Owner rank of each block pair (pair counts `npairs`) when spread over `world` ranks."""
     n = len(npairs)
@@ -357,4 +367,5 @@ EXPORTED_SYMBOLS = [
     "ladder_strerror", "ladder_flops", "ladder_plan_dry", "ladder_plan_set_timing", "ladder_plan_timing",
     "ladder_energy_noalloc", "ladder_tune_batched", "ladder_plan_shard", "ladder_shard_blocks",
     "ladder_watchdog_selftest", "ladder_batched_schedule", "ladder_plan_set_form", "ladder_plan_get_form",
+    "ladder_form_model",
 ]

@@ -681,6 +681,13 @@ int ladder_plan_set_form(ladder_plan_t plan, int form) {
 
 int ladder_plan_get_form(ladder_plan_t plan) { return plan ? plan->form : -1; }
 
+int ladder_form_model(int no, int nv, int nchol, int nslices) {
+    if (no < 1 || nv < 1 || nchol < 1) return -1;
+    if (nslices == 0) nslices = ladder::kDefaultSlices;
+    if (nslices < 5 || nslices > 8) return -1;
+    return auto_form(no, nv, nchol, nslices);
+}
+
 size_t ladder_workspace_bytes(ladder_plan_t plan) {
     if (!plan) return 0;
     return plan->ws.total;

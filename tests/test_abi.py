@@ -142,3 +142,17 @@ def test_planner_workspace_formula_fp64(lib):
     assert r["ws_bytes"] < maxp * 200 * 200 * 8 + 4096
     # One batch at c2 when the budget allows the whole packed triangle (6.43 GB).
     assert r["n_block_pairs"] == 1 and maxp == 200 * 201 // 2
+
+
+def test_form_model_decisions():
+    # The split (symmetric/antisymmetric) form pays where the ladder is a large share of the call:
+    # not at c1/c2 (100 (i,j) rows fill one 128-row tile; the combine pass costs more than it
+    # saves), yes at c3 and at the paper-scale shapes (nocc = 100).
+    assert lad.ladder_form_model(5, 19, 72) == 0
+    assert lad.ladder_form_model(10, 200, 630) == 0
+    assert lad.ladder_form_model(20, 400, 1260) == 1
+    assert lad.ladder_form_model(100, 700, 4000) == 1
+    assert lad.ladder_form_model(100, 800, 4500) == 1
+    for bad in [(0, 5, 5, 0), (5, 0, 5, 0), (5, 5, 0, 0), (5, 5, 5, 4), (5, 5, 5, 9)]:
+        with pytest.raises(lad.LadderError):
+            lad.ladder_form_model(*bad)
