@@ -173,8 +173,9 @@ int ladder_plan_dry(int no, int nv, int nchol, int precision, int nslices, size_
  * ladder_watchdog_selftest -- check, on the current device, the bounded wait that every
  * tcgen05 kernel of the library uses for its mbarriers (the watchdog that turns a lost
  * producer into LADDER_ERR_TIMEOUT instead of a hang).  Launches one CTA on `stream` that
- * waits on an mbarrier nothing arrives on, with that same wait (limit: 2 s of the GPU's
- * global timer), then synchronises the stream.  Returns LADDER_ERR_TIMEOUT when the wait
+ * waits on an mbarrier nothing arrives on, with that same wait (limit: limit_s seconds of the
+ * GPU's global timer, 0 = the plans' default of 2 s; at most 60 s, else LADDER_ERR_ARG), then
+ * synchronises the stream.  Returns LADDER_ERR_TIMEOUT when the wait
  * gave up and reported it through its status word -- the expected outcome -- and stores the
  * time it waited in *waited_ms (may be NULL); LADDER_OK means the wait ended without the
  * timeout being reported (a broken watchdog); LADDER_ERR_CUDA on a CUDA error.  Allocates and
@@ -182,7 +183,7 @@ int ladder_plan_dry(int no, int nv, int nchol, int precision, int nslices, size_
  * with a CPU fallback (Sec. "A Generic Interface for a Dynamic Switching Between CuPy,
  * PyTorch, and CPU-only Libraries"); this library has no fallback and no counterpart there.
  */
-int ladder_watchdog_selftest(double* waited_ms, cudaStream_t stream);
+int ladder_watchdog_selftest(double limit_s, double* waited_ms, cudaStream_t stream);
 
 /* Workspace bytes ladder_apply needs (device memory, 256-byte aligned start). */
 size_t ladder_workspace_bytes(ladder_plan_t plan);
@@ -300,16 +301,38 @@ enum {
 int ladder_plan_set_timing(ladder_plan_t plan, int enable);
 int ladder_plan_timing(ladder_plan_t plan, int kernel_class, float* total_ms, int* launches, int reset);
 
+/*
+ * ladder_plan_set_wait_limit -- time limit of the bounded waits in the plan's tensor-core
+ * kernels (and, for a batched plan, its instances').  Every mbarrier wait of those kernels polls
+ * the GPU's global nanosecond timer and gives up after this long: the kernel then records
+ * LADDER_ERR_TIMEOUT in the plan's status word, waits (bounded) for its own copies and MMAs,
+ * frees its tensor memory and returns, so a lost producer never hangs the GPU.  A stage can
+ * legitimately wait longer than the default 2 s on a time-sliced GPU or under a profiler's
+ * replay; raise the limit for such runs.  seconds = 0 restores the default; otherwise it must
+ * lie in [0.001, 3600].  Takes effect for calls enqueued afterwards.  Returns LADDER_OK or
+ * LADDER_ERR_ARG.  ladder_plan_get_wait_limit returns the limit in seconds (-1 for NULL).
+ * This failure handling is the library's own: the paper's is a CUDA availability probe with a
+ * CPU fallback (Sec. "A Generic Interface for a Dynamic Switching Between CuPy, PyTorch, and
+ * CPU-only Libraries").
+ */
+int ladder_plan_set_wait_limit(ladder_plan_t plan, double seconds);
+double ladder_plan_get_wait_limit(ladder_plan_t plan);
+
 /* Read (and clear) the plan's device status word: LADDER_OK, LADDER_ERR_BOUNDS
  * (only in a library built with LADDER_CHECK, whose kernels test the index of
  * every store into the workspace and into R, record a failure here and skip the
- * store), LADDER_ERR_TIMEOUT or LADDER_ERR_NUMERIC.  Synchronises the stream. */
+ * store), LADDER_ERR_TIMEOUT or LADDER_ERR_NUMERIC.  Synchronises the stream.
+ * After LADDER_ERR_TIMEOUT or LADDER_ERR_NUMERIC the R of the calls enqueued since the last
+ * read is undefined (partly accumulated, or built from clamped digits): restore R and repeat
+ * the call.  The workspace needs no repair; the context stays usable. */
 int ladder_last_status(ladder_plan_t plan, cudaStream_t stream);
 
 /*
- * ladder_energy_noalloc -- E_L exactly as ladder_energy defines it, for
+ * ladder_energy_noalloc -- the E_L of ladder_energy (same definition), for
  * callers that cannot allocate device memory.  The paper has no counterpart
- * to this entry point.
+ * to this entry point.  Its fixed reduction tree (contiguous runs of 64 tiles)
+ * differs from ladder_energy's, so the two may differ by rounding; for a given
+ * (no, nv) and data every call returns the same bits.
  *
  * Who needs it: code that runs while a stream is being captured into a CUDA
  * graph (allocation cannot be captured), frameworks that own all device
@@ -327,7 +350,8 @@ int ladder_last_status(ladder_plan_t plan, cudaStream_t stream);
  * call rejects, with LADDER_ERR_ARG and before launching anything, shapes
  * with ceil(no^2 ceil(nv/32)^2 / 64) > LADDER_NOALLOC_MAX_PARTIALS.
  * The first call on a device looks up the array's device address with that
- * device current; make that first call before any stream capture.  All calls
+ * device current (again after cudaDeviceReset, or under another driver
+ * context of the device); make that first call before any stream capture.  All calls
  * share the one array: calls whose kernels may overlap on the GPU (other
  * streams, other threads) race and return wrong values -- order them.
  * Every partial is rewritten by each call, so nothing is cleared in between.

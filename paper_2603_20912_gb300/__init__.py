@@ -70,7 +70,7 @@ def _load():
     lib.ladder_form_model.restype = ci
     lib.ladder_batched_schedule.argtypes = [vp, ci, pint]
     lib.ladder_batched_schedule.restype = ci
-    lib.ladder_watchdog_selftest.argtypes = [ctypes.POINTER(ctypes.c_double), vp]
+    lib.ladder_watchdog_selftest.argtypes = [ctypes.c_double, ctypes.POINTER(ctypes.c_double), vp]
     lib.ladder_watchdog_selftest.restype = ci
     lib.ladder_plan_shard.argtypes = [vp, ci, ci]
     lib.ladder_plan_shard.restype = ci
@@ -101,6 +101,10 @@ def _load():
     lib.ladder_plan_dry.argtypes = [ci, ci, ci, ci, ci, sz, ci, ci, ci, pint, pint, ctypes.POINTER(sz), ci, pint,
                                     pint]
     lib.ladder_plan_dry.restype = ci
+    lib.ladder_plan_set_wait_limit.argtypes = [vp, ctypes.c_double]
+    lib.ladder_plan_set_wait_limit.restype = ci
+    lib.ladder_plan_get_wait_limit.argtypes = [vp]
+    lib.ladder_plan_get_wait_limit.restype = ctypes.c_double
     lib.ladder_plan_set_timing.argtypes = [vp, ci]
     lib.ladder_plan_set_timing.restype = ci
     lib.ladder_plan_timing.argtypes = [vp, ci, ctypes.POINTER(ctypes.c_float), pint, ci]
@@ -189,6 +193,13 @@ class Plan:
     def shard(self, rank: int, world: int):
         """Keep only the block pairs rank `rank` of `world` owns (see ladder_plan_shard)."""
         _check(_load().ladder_plan_shard(self._h, int(rank), int(world)), "ladder_plan_shard")
+
+    def set_wait_limit(self, seconds: float):
+        """Limit of the kernels' bounded waits (0 = the default 2 s); see ladder_plan_set_wait_limit."""
+        _check(_load().ladder_plan_set_wait_limit(self._h, float(seconds)), "ladder_plan_set_wait_limit")
+
+    def wait_limit(self) -> float:
+        return float(_load().ladder_plan_get_wait_limit(self._h))
 
     def set_timing(self, enable: bool):
         _check(_load().ladder_plan_set_timing(self._h, int(bool(enable))), "ladder_plan_set_timing")
@@ -346,10 +357,11 @@ def ladder_energy_noalloc(t2, R, E_dev, stream=None):
     return E_dev
 
 
-def ladder_watchdog_selftest(stream=None):
-    """(status, waited_ms): status is LADDER_ERR_TIMEOUT when the bounded wait fired as designed."""
+def ladder_watchdog_selftest(limit_s=0.0, stream=None):
+    """(status, waited_ms): status is LADDER_ERR_TIMEOUT when the bounded wait fired as designed
+    (limit_s seconds of the GPU's global timer, 0 = the default 2 s)."""
     ms = ctypes.c_double()
-    rc = _load().ladder_watchdog_selftest(ctypes.byref(ms), _stream_handle(stream))
+    rc = _load().ladder_watchdog_selftest(float(limit_s), ctypes.byref(ms), _stream_handle(stream))
     return int(rc), ms.value
 
 
@@ -367,5 +379,5 @@ EXPORTED_SYMBOLS = [
     "ladder_strerror", "ladder_flops", "ladder_plan_dry", "ladder_plan_set_timing", "ladder_plan_timing",
     "ladder_energy_noalloc", "ladder_tune_batched", "ladder_plan_shard", "ladder_shard_blocks",
     "ladder_watchdog_selftest", "ladder_batched_schedule", "ladder_plan_set_form", "ladder_plan_get_form",
-    "ladder_form_model",
+    "ladder_form_model", "ladder_plan_set_wait_limit", "ladder_plan_get_wait_limit",
 ]

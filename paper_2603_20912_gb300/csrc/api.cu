@@ -952,6 +952,18 @@ int ladder_tune_batched(ladder_plan_t plan, const double* const* L, const double
     return rc;
 }
 
+int ladder_plan_set_wait_limit(ladder_plan_t plan, double seconds) {
+    if (!plan || !(seconds >= 0.0) || seconds > 3600.0) return LADDER_ERR_ARG;
+    if (seconds > 0.0 && seconds < 1e-3) return LADDER_ERR_ARG;
+    const unsigned long long ns =
+        seconds == 0.0 ? ladder::kDefaultWaitNs : (unsigned long long)std::llround(seconds * 1e9);
+    plan->wait_ns = ns;
+    for (auto* s : plan->sub) s->wait_ns = ns;
+    return LADDER_OK;
+}
+
+double ladder_plan_get_wait_limit(ladder_plan_t plan) { return plan ? (double)plan->wait_ns * 1e-9 : -1.0; }
+
 int ladder_plan_set_timing(ladder_plan_t plan, int enable) {
     if (!plan) return LADDER_ERR_ARG;
     DeviceGuard guard(plan->device);

@@ -741,6 +741,7 @@ struct EriBatch {
     const int4* entries;        // (row tile, column tile, item, 0)
     int nentries, nitems;
     unsigned* status;
+    unsigned long long wait_ns; // limit of every bounded mbarrier wait (ns of the global timer)
 };
 
 // ------------------------------------------------------------------ ERI kernel
@@ -809,7 +810,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsEri, 1)
             for (int c = 0; c < CPC; ++c) arow[c] = ch[c].x;
             const int brow = p.b0 * p.vp + en.y * kEmuTileN + (kEmuTileN / 2) * (int)rank;
             for (int kb = 0; kb < nkb && ok; ++kb) {
-                if (!(ok = mbar_wait(&empty[ring.stage], ring.phase ^ 1u, B.status, kStatusTimeout))) break;
+                if (!(ok = mbar_wait(&empty[ring.stage], ring.phase ^ 1u, B.status, kStatusTimeout, B.wait_ns))) break;
                 unsigned char* st = smem + ring.stage * eri_stage_bytes(S);
                 if (rank == 0) mbar_arrive_expect_tx(&full[ring.stage], 2 * eri_stage_bytes(S));
                 const uint32_t fb = mapa_rank(smem_u32(&full[ring.stage]), 0);
@@ -831,12 +832,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsEri, 1)
             const int nkb = (B.item[B.entries[e].z].nchol + BK - 1) / BK;
             const int nch = (nkb + kb_per_chunk - 1) / kb_per_chunk;
             for (int ch = 0; ch < nch && ok; ++ch, ++it) {
-                if (!(ok = mbar_wait(&acc_empty, (uint32_t)(it & 1) ^ 1u, B.status, kStatusTimeout))) break;
+                if (!(ok = mbar_wait(&acc_empty, (uint32_t)(it & 1) ^ 1u, B.status, kStatusTimeout, B.wait_ns))) break;
                 tc_fence_after();
                 bool first[kNumAcc] = {true, true, true, true, true};
                 const int kb1 = min((ch + 1) * kb_per_chunk, nkb);
                 for (int kb = ch * kb_per_chunk; kb < kb1 && ok; ++kb) {
-                    if (!(ok = mbar_wait(&full[ring.stage], ring.phase, B.status, kStatusTimeout))) break;
+                    if (!(ok = mbar_wait(&full[ring.stage], ring.phase, B.status, kStatusTimeout, B.wait_ns))) break;
                     tc_fence_after();
                     const uint32_t st = smem_u32(smem + ring.stage * eri_stage_bytes(S));
                     issue_pairs<S, true, BK>(tmem, st, st + ABYTES, AGROUP, BPLANE, idesc, first, ACHUNK);
@@ -903,7 +904,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsEri, 1)
 #pragma unroll
                 for (int k = 0; k < 8; ++k) run[g][k] = 0;
             for (int ch = 0; ch < nch; ++ch, ++it) {
-                if (!(ok = mbar_wait(&acc_full, (uint32_t)(it & 1), B.status, kStatusTimeout))) break;
+                if (!(ok = mbar_wait(&acc_full, (uint32_t)(it & 1), B.status, kStatusTimeout, B.wait_ns))) break;
                 tc_fence_after();
 #pragma unroll
                 for (int g = 0; g < kEriRuns; ++g) {   // accumulators 0-1, then 2-4: fewer live registers
@@ -980,7 +981,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsEri, 1)
         failed = !ok;
     }
     // Every CTA waits for the leader's last commit (all MMAs that read its shared memory are done).
-    if (threadIdx.x == 64) mbar_wait(&done, 0, B.status, kStatusTimeout);
+    if (threadIdx.x == 64) mbar_wait(&done, 0, B.status, kStatusTimeout, B.wait_ns);
     if (failed) grace_delay(2000000);  // an aborted pipeline: let copies already in flight land
     tc_fence_before();
     cluster_sync();  // no CTA leaves while its peer may still write into it or signal it
@@ -1070,6 +1071,7 @@ struct LadBatch {
     long long units;            // all items' units
     int nitems, BN;
     unsigned* status;
+    unsigned long long wait_ns; // limit of every bounded mbarrier wait (ns of the global timer)
 };
 
 // Item of a unit, for units visited in increasing order.
@@ -1139,7 +1141,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) ladder_emu_kernel(const __grid_
             const int nt = (int)(tile % p.n_nt), mt = (int)(tile / p.n_nt);
             const int kb1 = min((ch + 1) * p.kb_per_chunk, p.nkb);
             for (int kb = ch * p.kb_per_chunk; kb < kb1 && ok; ++kb) {
-                if (!(ok = mbar_wait(&empty[ring.stage], ring.phase ^ 1u, B.status, kStatusTimeout))) break;
+                if (!(ok = mbar_wait(&empty[ring.stage], ring.phase ^ 1u, B.status, kStatusTimeout, B.wait_ns))) break;
                 unsigned char* st = smem + ring.stage * stage_bytes(S);
                 mbar_arrive_expect_tx(&full[ring.stage], bytes);
                 tma_load_3d_hint(st, &B.ta[ik], &full[ring.stage], kb * BK, mt * kEmuTile, 0, keep);
@@ -1149,7 +1151,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) ladder_emu_kernel(const __grid_
             }
         }
         for (int i = 0; i < STAGES; ++i)
-            if (issued[i]) mbar_wait(&full[i], (uint32_t)((issued[i] - 1) & 1), B.status, kStatusTimeout);
+            if (issued[i]) mbar_wait(&full[i], (uint32_t)((issued[i] - 1) & 1), B.status, kStatusTimeout, B.wait_ns);
     } else if (warp == 1 && lane == 0) {
         Ring ring;
         const uint32_t idesc = idesc_bf16_f32(kEmuTile, B.BN);
@@ -1159,12 +1161,12 @@ __global__ void __launch_bounds__(kThreadsTC, 1) ladder_emu_kernel(const __grid_
         for (long long u = u0; u < u1 && ok; ++u, ++it) {
             const LadItem& p = B.item[cur.seek(B, u)];
             const int ch = (int)((u - p.ubeg) % p.n_ch);
-            if (!(ok = mbar_wait(&acc_empty, (uint32_t)(it & 1) ^ 1u, B.status, kStatusTimeout))) break;
+            if (!(ok = mbar_wait(&acc_empty, (uint32_t)(it & 1) ^ 1u, B.status, kStatusTimeout, B.wait_ns))) break;
             tc_fence_after();
             bool first[kNumAcc] = {true, true, true, true, true};
             const int kb1 = min((ch + 1) * p.kb_per_chunk, p.nkb);
             for (int kb = ch * p.kb_per_chunk; kb < kb1 && ok; ++kb) {
-                if (!(ok = mbar_wait(&full[ring.stage], ring.phase, B.status, kStatusTimeout))) break;
+                if (!(ok = mbar_wait(&full[ring.stage], ring.phase, B.status, kStatusTimeout, B.wait_ns))) break;
                 tc_fence_after();
                 const uint32_t st = smem_u32(smem + ring.stage * stage_bytes(S));
                 issue_pairs<S>(tmem, st, st + S * APLANE, APLANE, BPLANE, idesc, first);
@@ -1174,7 +1176,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) ladder_emu_kernel(const __grid_
             if (ok) mma_commit(&acc_full);
         }
         mma_commit(&done);
-        mbar_wait(&done, 0, B.status, kStatusTimeout);
+        mbar_wait(&done, 0, B.status, kStatusTimeout, B.wait_ns);
     } else if (warp >= 2) {
         // Each warp: TMEM lane quadrant q, column chunks ci = h, h+2, h+4 (16 columns each).
         const int q = warp & 3, h = (warp - 2) >> 2;
@@ -1187,7 +1189,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) ladder_emu_kernel(const __grid_
         int it = 0;
         ItemCursor cur;
         for (long long u = u0; u < u1; ++u, ++it) {
-            if (!mbar_wait(&acc_full, (uint32_t)(it & 1), B.status, kStatusTimeout)) break;
+            if (!mbar_wait(&acc_full, (uint32_t)(it & 1), B.status, kStatusTimeout, B.wait_ns)) break;
             tc_fence_after();
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
@@ -1305,7 +1307,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
             const int brow = nt * kEmuTileN + (kEmuTileN / 2) * (int)rank;
             const int kb1 = min((ch + 1) * p.kb_per_chunk, p.nkb);
             for (int kb = ch * p.kb_per_chunk; kb < kb1 && ok; ++kb) {
-                if (!(ok = mbar_wait(&empty[ring.stage], ring.phase ^ 1u, B.status, kStatusTimeout))) break;
+                if (!(ok = mbar_wait(&empty[ring.stage], ring.phase ^ 1u, B.status, kStatusTimeout, B.wait_ns))) break;
                 unsigned char* st = smem + ring.stage * pair_stage_bytes(S);
                 if (rank == 0) mbar_arrive_expect_tx(&full[ring.stage], 2 * pair_stage_bytes(S));
                 const uint32_t fb = mapa_rank(smem_u32(&full[ring.stage]), 0);
@@ -1324,12 +1326,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
         for (long long u = u0; u < u1 && ok; ++u, ++it) {
             const LadItem& p = B.item[cur.seek(B, u)];
             const int ch = (int)((u - p.ubeg) % p.n_ch);
-            if (!(ok = mbar_wait(&acc_empty, (uint32_t)(it & 1) ^ 1u, B.status, kStatusTimeout))) break;
+            if (!(ok = mbar_wait(&acc_empty, (uint32_t)(it & 1) ^ 1u, B.status, kStatusTimeout, B.wait_ns))) break;
             tc_fence_after();
             bool first[kNumAcc] = {true, true, true, true, true};
             const int kb1 = min((ch + 1) * p.kb_per_chunk, p.nkb);
             for (int kb = ch * p.kb_per_chunk; kb < kb1 && ok; ++kb) {
-                if (!(ok = mbar_wait(&full[ring.stage], ring.phase, B.status, kStatusTimeout))) break;
+                if (!(ok = mbar_wait(&full[ring.stage], ring.phase, B.status, kStatusTimeout, B.wait_ns))) break;
                 tc_fence_after();
                 const uint32_t st = smem_u32(smem + ring.stage * pair_stage_bytes(S));
                 issue_pairs<S, true>(tmem, st, st + ABYTES, APLANE, BPLANE, idesc, first);
@@ -1352,7 +1354,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
         bool ok = true;
         ItemCursor cur;
         for (long long u = u0; u < u1; ++u, ++it) {
-            if (!(ok = mbar_wait(&acc_full, (uint32_t)(it & 1), B.status, kStatusTimeout))) break;
+            if (!(ok = mbar_wait(&acc_full, (uint32_t)(it & 1), B.status, kStatusTimeout, B.wait_ns))) break;
             tc_fence_after();
 #pragma unroll
             for (int cc = 0; cc < 3; ++cc) {
@@ -1397,7 +1399,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
         }
         failed = !ok;
     }
-    if (threadIdx.x == 64) mbar_wait(&done, 0, B.status, kStatusTimeout);
+    if (threadIdx.x == 64) mbar_wait(&done, 0, B.status, kStatusTimeout, B.wait_ns);
     if (failed) grace_delay(2000000);
     tc_fence_before();
     cluster_sync();
@@ -1660,6 +1662,7 @@ cudaError_t block_pm_impl(const ladder_plan_s& p, const BlockPair& bp, double* R
     eb.nentries = bp.ntiles;
     eb.entries = reinterpret_cast<const int4*>(table + bp.tiles_off);
     eb.status = p.d_status;
+    eb.wait_ns = p.wait_ns;
     if (!eri_item<S>(p, bp, ws, &eb.item[0], &eb.ta[0], &eb.tb[0])) return cudaErrorInvalidValue;
     const int vp = padded_vp(p.nv);
     {
@@ -1683,6 +1686,8 @@ cudaError_t block_pm_impl(const ladder_plan_s& p, const BlockPair& bp, double* R
         lb.nitems = 1;
         lb.BN = kEmuTileN;
         lb.status = p.d_status;
+    lb.wait_ns = p.wait_ns;
+        lb.wait_ns = p.wait_ns;
         if (!ladder_item_pm<S>(p, bp, ws, 0, part == 0, &lb.item[0], &lb.ta[0], &lb.tb[0]))
             return cudaErrorInvalidValue;
         lb.units = lb.item[0].units;
@@ -1716,6 +1721,7 @@ cudaError_t block_impl(const ladder_plan_s& p, const BlockPair& bp, double* R, v
     eb.nentries = bp.ntiles;
     eb.entries = reinterpret_cast<const int4*>(table + bp.tiles_off);
     eb.status = p.d_status;
+    eb.wait_ns = p.wait_ns;
     if (!eri_item<S>(p, bp, ws, &eb.item[0], &eb.ta[0], &eb.tb[0])) return cudaErrorInvalidValue;
     {
         LaunchTimer tm(p, s, LADDER_KERNEL_ERI, 2);
@@ -1730,6 +1736,7 @@ cudaError_t block_impl(const ladder_plan_s& p, const BlockPair& bp, double* R, v
     lb.nitems = 1;
     lb.BN = kEmuTileN;
     lb.status = p.d_status;
+    lb.wait_ns = p.wait_ns;
     if (!ladder_item<S>(p, bp, ws, 0, &lb.item[0], &lb.ta[0], &lb.tb[0])) return cudaErrorInvalidValue;
     lb.units = lb.item[0].units;
     {
@@ -1774,6 +1781,7 @@ cudaError_t group_impl(const ladder_plan_s& parent, const ladder_plan_s* const* 
     eb.nentries = nentries;
     eb.entries = entries;
     eb.status = parent.d_status;
+    eb.wait_ns = parent.wait_ns;
     for (int k = 0; k < n; ++k)
         if (!eri_item<S>(*subs[k], subs[k]->bps[0], ws[k], &eb.item[k], &eb.ta[k], &eb.tb[k]))
             return cudaErrorInvalidValue;
@@ -1790,6 +1798,7 @@ cudaError_t group_impl(const ladder_plan_s& parent, const ladder_plan_s* const* 
         lb = LadBatch{};
         lb.BN = kEmuTileN;
         lb.status = parent.d_status;
+        lb.wait_ns = parent.wait_ns;
         long long units = 0;
         for (int k = 0; k < n; ++k) {
             if ((int)ladder_on_pairs(*subs[k]) != shape) continue;

@@ -30,6 +30,9 @@ constexpr int kEmuChunkK = 1024;            // K per exact chunk: level 5 has 4 
 constexpr int kEmuTile = 128;               // tcgen05 tile rows (M)
 constexpr int kEmuTileN = 96;               // widest tile N: 5 TMEM accumulators x 96 <= 512 columns
 
+// Default limit of the kernels' bounded mbarrier waits (ladder_plan_set_wait_limit changes it).
+constexpr unsigned long long kDefaultWaitNs = 2000000000ull;   // 2 s
+
 // Device status bits (ORed into the plan's status word by kernels).
 constexpr unsigned kStatusTimeout = 1u;
 constexpr unsigned kStatusNumeric = 2u;
@@ -132,6 +135,7 @@ struct ladder_plan_s {
     void* d_tables = nullptr;          // pair lists (int2) + row_start tables (int)
     size_t tables_bytes = 0;
     unsigned* d_status = nullptr;      // status word
+    unsigned long long wait_ns = ladder::kDefaultWaitNs;  // limit of the kernels' bounded waits
     double* d_partials = nullptr;      // energy reduction partials
     int n_partials = 0;
     // Optional per-kernel timing (benchmarks): event pairs tagged by kernel class.

@@ -13,9 +13,14 @@
 // Host code must not pass the array's name to a kernel: in host code that
 // name is only a host-side shadow, so a kernel given it would fault or, where
 // the GPU can reach host memory, silently use the wrong memory.  The device
-// address is looked up once per device with cudaGetSymbolAddress, with that
-// device current, on the first call made on that device.
+// address is looked up with cudaGetSymbolAddress, with that device current, on
+// the first call made on that device, and again whenever the driver context
+// current on the calling thread is not the one the address was taken in (after
+// cudaDeviceReset the module is loaded afresh and the array may sit elsewhere;
+// a caller's own driver-API context holds its own copy of the array).
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <mutex>
 
@@ -23,7 +28,8 @@
 
 namespace {
 
-constexpr int kMaxPartials = 16384;        // scratch capacity (doubles)
+constexpr int kMaxPartials = LADDER_NOALLOC_MAX_PARTIALS;  // scratch capacity (doubles)
+static_assert(kMaxPartials * sizeof(double) == 128 * 1024, "the header documents 128 KiB of scratch");
 constexpr int kUnitsPerBlock = 64;         // 32x32 tiles reduced by one block (fixed: reproducible sums)
 constexpr int kThreads = 256;
 constexpr int kTile = 32;
@@ -32,7 +38,11 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) double g_energy_scratch[kMaxPartials];
 
 std::mutex g_setup_mutex;
-double* g_scratch_addr[kMaxDevices] = {};
+struct ScratchAddr {
+    CUcontext ctx = nullptr;   // driver context the address belongs to
+    double* addr = nullptr;
+};
+ScratchAddr g_scratch_addr[kMaxDevices];
 
 __device__ __forceinline__ double block_sum(double v, double* red) {
     const int t = threadIdx.x;
@@ -93,16 +103,39 @@ __global__ void __launch_bounds__(kThreads) energy_final_fixed(const double* __r
     if (threadIdx.x == 0) *E = s;
 }
 
-// Device address of the scratch array on the current device (looked up once per device).
+// The driver's cuCtxGetCurrent, reached through the runtime (no link-time libcuda dependency).
+PFN_cuCtxGetCurrent_v4000 ctx_get_current() {
+    static PFN_cuCtxGetCurrent_v4000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(f);
+    });
+    return fn;
+}
+
+// Device address of the scratch array on the current device, looked up once per device and
+// driver context.  Before the runtime has bound a context to the thread, cuCtxGetCurrent gives
+// none; the lookup itself binds the device's primary context, which is then recorded.
 int scratch_address(int dev, double** out) {
     if (dev < 0 || dev >= kMaxDevices) return LADDER_ERR_UNSUPPORTED;
+    auto get_ctx = ctx_get_current();
+    if (!get_ctx) return LADDER_ERR_CUDA;
+    CUcontext ctx = nullptr;
+    if (get_ctx(&ctx) != CUDA_SUCCESS) return LADDER_ERR_CUDA;
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[dev]) {
+    ScratchAddr& e = g_scratch_addr[dev];
+    if (e.addr == nullptr || ctx == nullptr || e.ctx != ctx) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_energy_scratch) != cudaSuccess || p == nullptr) return LADDER_ERR_CUDA;
-        g_scratch_addr[dev] = static_cast<double*>(p);
+        if (ctx == nullptr && (get_ctx(&ctx) != CUDA_SUCCESS || ctx == nullptr)) return LADDER_ERR_CUDA;
+        e.addr = static_cast<double*>(p);
+        e.ctx = ctx;
     }
-    *out = g_scratch_addr[dev];
+    *out = e.addr;
     return LADDER_OK;
 }
 

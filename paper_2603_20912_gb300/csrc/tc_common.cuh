@@ -2,10 +2,10 @@
 // waits, TMA tensor loads, TMEM allocation, tcgen05.mma / commit / ld, and
 // the shared-memory and instruction descriptors of tcgen05 (kind::f16).
 //
-// Every wait here is bounded: after kWaitLimitNs of polling (read from the
-// global nanosecond timer) it gives up, records the caller's flag in its status
-// word and returns false, so a kernel whose producer died still terminates and
-// frees its TMEM.
+// Every wait here is bounded: after the caller's limit (ns of the global
+// nanosecond timer; plans default to kDefaultWaitNs) of polling it gives up,
+// records the caller's flag in its status word and returns false, so a kernel
+// whose producer died still terminates and frees its TMEM.
 #pragma once
 
 #include <cstdint>
@@ -15,7 +15,6 @@
 namespace ladder {
 namespace tc {
 
-constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s of polling before a wait is declared dead
 
 __device__ __forceinline__ uint64_t global_ns() {
     uint64_t t;
@@ -60,12 +59,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 
 // Bounded wait for the phase with the given parity to complete.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned* status, unsigned flag) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned* status, unsigned flag,
+                                          uint64_t limit_ns) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     for (uint32_t i = 1;; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
-        if ((i & 1023u) == 0 && global_ns() - t0 > kWaitLimitNs) break;
+        if ((i & 1023u) == 0 && global_ns() - t0 > limit_ns) break;
     }
     if (status) atomicOr(status, flag);
     return false;
@@ -81,18 +81,6 @@ __device__ __forceinline__ void tma_load_3d(void* smem_dst, const void* tmap, ui
         "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
         ::"r"(smem_u32(smem_dst)), "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(z),
           "r"(smem_u32(bar))
-        : "memory");
-}
-
-// Multicast TMA load: the box lands at the same shared-memory offset in every CTA of
-// `cta_mask` and completes `bytes` on the mbarrier at the same offset in each of them.
-__device__ __forceinline__ void tma_load_3d_mc(void* smem_dst, const void* tmap, uint64_t* bar, int x, int y, int z,
-                                               uint16_t cta_mask) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
-        " [%0], [%1, {%2, %3, %4}], [%5], %6;"
-        ::"r"(smem_u32(smem_dst)), "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(z),
-          "r"(smem_u32(bar)), "h"(cta_mask)
         : "memory");
 }
 

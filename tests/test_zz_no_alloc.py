@@ -4,14 +4,16 @@ Callers running under CUDA graph capture, or inside frameworks that forbid
 any allocator but their own, cannot let the library call cudaMalloc.  This
 entry point keeps its reduction scratch in a fixed array inside the library.
 The test calls it through the C ABI and checks it against ladder_energy (the
-plan-based entry point) on two calls in a row, within the tolerance the
-energy tests use.  This file is collected last on purpose.
+plan-based entry point) and against the CPU oracle's E_L, on two calls in a
+row, within the tolerance the energy tests use.  This file is collected last
+on purpose.
 """
 import ctypes
 
 import numpy as np
 import pytest
 
+import oracle
 import paper_2603_20912_gb300 as lad
 from ladder_inputs import CONFIGS, make_inputs
 
@@ -34,7 +36,7 @@ def _case(no, nv, nchol, seed):
     # Any R works for the energy; use a random one so both entry points see the same data.
     R = torch.from_numpy(np.random.default_rng(seed).standard_normal(t2.shape)).cuda()
     plan = lad.ladder_plan(no, nv, nchol)
-    return plan, td, R
+    return plan, td, R, oracle.energy(t2, R.cpu().numpy())
 
 
 def _noalloc_c_abi(td, R):
@@ -51,11 +53,12 @@ def _noalloc_c_abi(td, R):
 def test_noalloc_energy_matches_plan_energy_two_calls_in_a_row():
     s = CONFIGS["c1"]
     cases = [_case(s.no, s.nv, s.nchol, s.seed), _case(7, 45, 30, 77)]
-    for plan, td, R in cases + cases[::-1]:
+    for plan, td, R, E_oracle in cases + cases[::-1]:
         E_ref = lad.ladder_energy(plan, td, R)
         E1 = _noalloc_c_abi(td, R)
         E2 = _noalloc_c_abi(td, R)
         assert abs(E1 - E_ref) <= TOL_E * abs(E_ref)
+        assert abs(E1 - E_oracle) <= TOL_E * abs(E_oracle)
         assert E1 == E2
 
 
