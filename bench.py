@@ -3,19 +3,27 @@
 
 One step = one ladder_apply (all steps of the hot path: operand preparation,
 Cholesky->ERI GEMM, ladder GEMM, a<=b unpack) on the synthetic workload.
-Default workload: no=10, nv=200, nchol=630 (the one-batch configuration whose
-packed ERI is 6.4 GB), seeded generators of ``ladder_inputs``.
+Default workload: no=20, nv=400, nchol=1260 (seed 1237), the nv = 400 shape
+the tensor-roofline target is stated at, emulated FP64 (BF16 digit slices)
+with the ladder form the planner picks; seeded generators of ``ladder_inputs``.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision emu|fp64]
-                    [--config c2] [--impl ours|reference]
+                    [--config c3] [--impl ours|reference] [--mode replicas|shard]
 
 Prints one JSON line (rank 0).  ``value`` = algorithmic TFLOP/s
 (2 X v^2 p + 2 o^2 v^2 p with p = v(v+1)/2, per instance) summed over ranks,
 timed with CUDA events on the launching stream between barriers, max over
 ranks; inputs resident in HBM.  ``e2e`` repeats the measurement through the
 same public call with the inputs copied from pinned host memory and R read
-back every step.  Multi-GPU runs (torchrun) give each rank its own
-independent instance (weak scaling, no collective on the data path).
+back every step.  ``fp64`` times the native FP64 (DMMA) path on the same
+workload (``speedup_vs_fp64`` = its ms/call over the emulated one) and
+``accuracy`` states both results' error against the CPU oracle: sampled
+(a, b) pairs against the oracle's pair mode, E_L against the stored oracle
+value, and the whole R of one path against the other.  Multi-GPU runs
+(torchrun): ``--mode replicas`` (default) gives each rank its own independent
+instance (weak scaling, no collective on the data path); ``--mode shard``
+splits one contraction's block pairs over the ranks (ladder_plan_shard) and
+sums E_L with one scalar all-reduce (strong scaling).
 """
 from __future__ import annotations
 
@@ -400,44 +408,125 @@ def run_batched(args):
         print(json.dumps(line), flush=True)
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--config", default="c2", choices=sorted(CONFIGS) + ["c5"])
-    ap.add_argument("--shape", default=None, help="no,nv,nchol overriding --config (profiling runs)")
-    ap.add_argument("--precision", default="emu", choices=["emu", "fp64"])
-    ap.add_argument("--nslices", type=int, default=0)
-    ap.add_argument("--form", default="auto", choices=["auto", "plain", "pm"],
-                    help="emulated ladder form: the planner's choice, plain, or the symmetric/antisymmetric split")
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--device-inputs", action="store_true",
-                    help="draw L and t2 on the GPU (timing-only runs at large shapes)")
-    ap.add_argument("--budget-gb", type=float, default=0.0, help="workspace budget (0: 0.9*0.98*free)")
-    ap.add_argument("--fp64-reference", action="store_true",
-                    help="c5: also time 24 sequential native-FP64 calls (slow)")
-    ap.add_argument("--measure-peaks", action="store_true",
-                    help="print torch/cuBLAS matmul throughput for fp64, bf16 and int8 and exit")
-    args = ap.parse_args()
-    if args.measure_peaks:
-        measure_peaks()
-        return
-    if args.config == "c5":
-        run_batched(args)
-        return
-    cfg = CONFIGS[args.config]
-    if args.shape:
-        no, nv, nchol = (int(x) for x in args.shape.split(","))
-        cfg = LadderShape(no=no, nv=nv, nchol=nchol, seed=4242, name="custom")
-    if args.warmup < 3:
-        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
-    if args.impl == "reference":
-        run_reference(args, cfg)
-        return
+GOLDEN_FILE = os.path.join(ROOT, "tests", "golden", "energies.json")
 
+
+def golden_for(cfg):
+    """E_L and ||R||_F of the workload as the oracle computed them (stored by oracle/make_golden.py),
+    or None when the workload is not one of the stored ones."""
+    try:
+        with open(GOLDEN_FILE) as f:
+            g = json.load(f).get(cfg.name)
+    except Exception:
+        return None
+    if not g or (g["no"], g["nv"], g["nchol"], g["seed"]) != (cfg.no, cfg.nv, cfg.nchol, cfg.seed):
+        return None
+    return g
+
+
+def sampled_error(L, t2, R_host_list, npairs=48, seed=5):
+    """||R - R_oracle||_F / ||R_oracle||_F over `npairs` random (a <= b) pairs, all (i,j), for
+    each R in R_host_list (the oracle's pair mode computes the pairs once)."""
+    import oracle
+    nv = L.shape[1]
+    rng = np.random.default_rng(seed)
+    a = rng.integers(0, nv, npairs)
+    b = rng.integers(0, nv, npairs)
+    a, b = np.minimum(a, b), np.maximum(a, b)
+    ref = oracle.ladder_pairs(L, t2, a, b)                    # [k, i, j]
+    den = float(np.linalg.norm(ref.ravel()))
+    out = []
+    for R in R_host_list:
+        got = R[:, :, a, b].transpose(2, 0, 1)
+        out.append(float(np.linalg.norm((got - ref).ravel())) / den if den > 0 else 0.0)
+    return out, f"{npairs} random (a<=b) pairs (seed {seed}), all (i,j), against the oracle's pair mode"
+
+
+def measure_dgemm_tflops(n=8192, reps=2):
+    """torch/cuBLAS FP64 matmul throughput now, on this GPU (the FP64 roofline denominator)."""
+    import torch
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    a @ b
+    torch.cuda.synchronize()
+    best = 1e30
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        a @ b
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1) * 1e-3)
+    del a, b
+    torch.cuda.empty_cache()
+    return 2.0 * n ** 3 / best / 1e12
+
+
+def kernel_times(lad, plan, steps):
+    kms, counts = {}, {}
+    for kind, name in [(lad.LADDER_KERNEL_PREP, "prep"), (lad.LADDER_KERNEL_ERI, "eri"),
+                       (lad.LADDER_KERNEL_LADDER, "ladder"), (lad.LADDER_KERNEL_FINISH, "finish"),
+                       (lad.LADDER_KERNEL_COMBINE, "combine")]:
+        ms, n = plan.timing(kind)
+        kms[name] = ms
+        counts[name] = n
+    return kms, counts
+
+
+def run_fp64_compare(args, cfg, lad, Ld, td, local, stream):
+    """Native FP64 (DMMA) path on the same workload: a warm-up call on a small shape (loads the
+    kernels), then `--fp64-steps` timed calls with CUDA events on the launching stream.  Returns the
+    record, the R of the last call (a single application) and the plan's ERI time share."""
+    import torch
+    dgemm = measure_dgemm_tflops()
+    warm = lad.ladder_plan(5, 19, 72, lad.LADDER_FP64, device=local)
+    Lw = torch.zeros((72, 19, 19), dtype=torch.float64, device="cuda")
+    tw = torch.zeros((5, 5, 19, 19), dtype=torch.float64, device="cuda")
+    lad.ladder_apply(warm, Lw, tw, torch.zeros_like(tw))
+    torch.cuda.synchronize()
+    warm.close()
+    torch.cuda.empty_cache()
+    plan = lad.ladder_plan(cfg.no, cfg.nv, cfg.nchol, lad.LADDER_FP64, device=local)
+    ws = plan.workspace()
+    desc = plan.describe()
+    R = torch.zeros_like(td)
+    plan.set_timing(True)
+    sampler = ClockSampler(local)
+    sampler.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.fp64_steps):
+        R.zero_()   # every call into a zeroed R (a memset of R inside the timed region)
+        lad.ladder_apply(plan, Ld, td, R, ws)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.fp64_steps
+    kms, counts = kernel_times(lad, plan, args.fp64_steps)
+    plan.set_timing(False)
+    assert plan.last_status() == lad.LADDER_OK
+    E = lad.ladder_energy(plan, td, R)
+    eri_flops = 2.0 * cfg.nchol * cfg.nv * cfg.nv * (cfg.nv * (cfg.nv + 1) // 2)
+    eri_tf = eri_flops * args.fp64_steps / (kms["eri"] * 1e-3) / 1e12 if kms["eri"] > 0 else None
+    rec = {"ms_per_call": ms, "tflops": lad.ladder_flops(cfg.no, cfg.nv, cfg.nchol) / (ms * 1e-3) / 1e12,
+           "steps": args.fp64_steps, "warmup": "one call on a no=5 nv=19 nchol=72 shape (loads the kernels)",
+           "kernel_ms_per_call": {k: v / args.fp64_steps for k, v in kms.items()},
+           "gpu_launches": sum(counts.values()), "n_a": desc["n_a"], "n_b": desc["n_b"],
+           "block_pairs": desc["n_block_pairs"], "E_L": E,
+           "roofline": {"bound": "tensor", "kernel": "eri_fp64_kernel (DMMA m8n8k4 f64)", "achieved": eri_tf,
+                        "peak": dgemm, "unit": "TFLOP/s", "frac": eri_tf / dgemm if eri_tf else None,
+                        "peak_source": "torch float64 matmul 8192^3 measured in this run (cuBLAS DGEMM)"},
+           "clocks": clocks}
+    del ws
+    plan.close()
+    torch.cuda.empty_cache()
+    return rec, R
+
+
+def run_single(args, cfg):
     import torch
     import paper_2603_20912_gb300 as lad
     from paper_2603_20912_gb300 import build
@@ -445,25 +534,38 @@ def main():
     torch.cuda.set_device(local)
     build.build()
     precision = lad.LADDER_EMU_BF16 if args.precision == "emu" else lad.LADDER_FP64
-    # Each rank: its own independent instance (seed offset by rank).
+    shard = args.mode == "shard" and world > 1
+    # replicas: each rank its own independent instance (seed offset by rank); shard: one instance
+    seed = cfg.seed + (0 if shard else 7919 * rank)
     if args.device_inputs:
         # timing-only shapes: inputs drawn on the GPU, no host copies (no e2e, no CPU baseline)
         from ladder_inputs import make_device_inputs
-        Ld, td = make_device_inputs(cfg.no, cfg.nv, cfg.nchol, cfg.seed + 7919 * rank, device=f"cuda:{local}")
+        Ld, td = make_device_inputs(cfg.no, cfg.nv, cfg.nchol, seed, device=f"cuda:{local}")
         args.no_e2e = args.no_cpu_baseline = True
+        args.fp64 = "off"
         L = t2 = Lh = th = None
     else:
-        L, t2, _, _ = make_inputs(cfg.no, cfg.nv, cfg.nchol, cfg.seed + 7919 * rank)
+        L, t2, _, _ = make_inputs(cfg.no, cfg.nv, cfg.nchol, seed)
         Lh = torch.from_numpy(L).pin_memory()
         th = torch.from_numpy(t2).pin_memory()
         Ld = Lh.to("cuda", non_blocking=True)
         td = th.to("cuda", non_blocking=True)
     R = torch.zeros_like(td)
     torch.cuda.synchronize()
+    budget = int(args.budget_gb * 1e9)
+    if shard and budget == 0:
+        # every rank must plan under the same budget to see the same blocking
+        import torch.distributed as dist
+        free_b, _ = torch.cuda.mem_get_info()
+        b = torch.tensor([float(free_b) * 0.98 * 0.9], dtype=torch.float64, device="cuda")
+        dist.all_reduce(b, op=dist.ReduceOp.MIN)
+        budget = int(b.item())
     plan = lad.ladder_plan(cfg.no, cfg.nv, cfg.nchol, precision, nslices=args.nslices,
-                           ws_budget_bytes=int(args.budget_gb * 1e9), device=local)
+                           ws_budget_bytes=budget, device=local)
     if args.form != "auto":
         plan.set_form(1 if args.form == "pm" else 0)
+    if shard:
+        plan.shard(rank, world)
     form_used = "pm" if plan.form() == 1 else "plain"
     ws = plan.workspace()
     desc = plan.describe()
@@ -491,18 +593,12 @@ def main():
     ms_total = ev0.elapsed_time(ev1)
     ms_total = max_over_ranks(ms_total, world)
     ms_step = ms_total / args.steps
-    value = world * flops * args.steps / (ms_total * 1e-3) / 1e12
-
-    counts = {}
-    kms = {}
-    for kind, name in [(lad.LADDER_KERNEL_PREP, "prep"), (lad.LADDER_KERNEL_ERI, "eri"),
-                       (lad.LADDER_KERNEL_LADDER, "ladder"), (lad.LADDER_KERNEL_FINISH, "finish"),
-                       (lad.LADDER_KERNEL_COMBINE, "combine")]:
-        ms, n = plan.timing(kind)
-        kms[name] = ms
-        counts[name] = n
+    # replicas: every rank did a whole contraction; shard: the ranks together did one
+    value = (1 if shard else world) * flops * args.steps / (ms_total * 1e-3) / 1e12
+    kms, counts = kernel_times(lad, plan, args.steps)
     plan.set_timing(False)
     launches = sum(counts.values())
+    assert plan.last_status() == lad.LADDER_OK
 
     # Dominant kernel: the ERI GEMM.  Algorithmic flops per launch = 2 X v^2 (pairs in the block);
     # the emulated kernel executes S(S+1)/2 BF16 slice products per FP64 product.
@@ -511,6 +607,8 @@ def main():
     eri_flops_call = 2.0 * cfg.nchol * nv2 * pairs_total
     if precision == lad.LADDER_EMU_BF16:   # only the rows (x <= y) of L^T are multiplied
         eri_flops_call = 2.0 * cfg.nchol * eri_products(cfg.nv, desc["n_a"], desc["n_b"])
+    if shard:
+        eri_flops_call = None   # a shard's share of the block pairs: no per-call count here
     peaks, peak_src = load_peaks()
     # Burst peak for a timed region under a second, the sustained (power-capped) one for longer.
     long_region = ms_total >= 1000.0
@@ -521,8 +619,8 @@ def main():
     if precision == lad.LADDER_EMU_BF16:
         S = desc["nslices"]
         slice_products = S * (S + 1) // 2
-        eri_exec_flops_call = eri_flops_call * slice_products
-        achieved = eri_exec_flops_call * args.steps / (kms["eri"] * 1e-3) / 1e12 if kms["eri"] > 0 else None
+        achieved = (eri_flops_call * slice_products * args.steps / (kms["eri"] * 1e-3) / 1e12
+                    if kms["eri"] > 0 and eri_flops_call else None)
         peak = bf16
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": (achieved / peak) if achieved else None, "traffic": traffic,
@@ -531,18 +629,17 @@ def main():
                 "executed_slice_products": slice_products}
         dtype = "f64-emulated(bf16 slices)"
     else:
-        # The DMMA path runs at full clock (no power capping), so its peak is derived from the
-        # burst BF16 measurement for every length of timed region.
-        achieved = eri_flops_call * args.steps / (kms["eri"] * 1e-3) / 1e12 if kms["eri"] > 0 else None
-        peak = burst * NOMINAL_FP64_TFLOPS / NOMINAL_BF16_TFLOPS
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+        achieved = (eri_flops_call * args.steps / (kms["eri"] * 1e-3) / 1e12
+                    if kms["eri"] > 0 and eri_flops_call else None)
+        dgemm = measure_dgemm_tflops()
+        roof = {"bound": "tensor", "achieved": achieved, "peak": dgemm, "unit": "TFLOP/s",
+                "frac": (achieved / dgemm) if achieved else None, "traffic": traffic,
                 "kernel": "eri_fp64_kernel (DMMA)",
-                "peak_source": f"bf16_tflops ({peak_src}) x nominal FP64/BF16 ratio 1.25/2250"}
+                "peak_source": "torch float64 matmul 8192^3 measured in this run (cuBLAS DGEMM)"}
         dtype = "f64"
     if traffic_src:
         roof["traffic_source"] = traffic_src
-    if form_used == "pm" and kms.get("combine", 0.0) > 0:
+    if form_used == "pm" and kms.get("combine", 0.0) > 0 and not shard:
         # The split form's combine pass is HBM work: it reads V as int64 and writes the V' and V''
         # digit planes, (8 + 2S) bytes per V element of the a <= b pairs.
         comb_bytes = (8 + 2 * desc["nslices"]) * nv2 * pairs_total
@@ -552,14 +649,15 @@ def main():
                            "frac": comb_gbs / hbm, "kernel": "vpm_combine_kernel",
                            "bytes_per_call": comb_bytes}
     # The whole call against the same peak (every kernel of the step, executed flops).
-    if precision == lad.LADDER_EMU_BF16:
+    if precision == lad.LADDER_EMU_BF16 and not shard:
         useful = eri_flops_call + 2.0 * ladder_products(cfg.no, cfg.nv, form_used)
         call_exec = useful * desc["nslices"] * (desc["nslices"] + 1) // 2
         roof["call_frac"] = call_exec / (ms_step * 1e-3) / 1e12 / peak
 
     # End to end through the public call with host buffers: H2D of L and t2 from pinned memory,
-    # apply into a zeroed R, D2H of R, every step.
+    # apply into a zeroed R, D2H of R, every step.  The last step leaves one application in R.
     e2e = None
+    Rh = None
     if not args.no_e2e:
         Rh = torch.empty(t2.shape, dtype=torch.float64).pin_memory()
 
@@ -582,10 +680,49 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         ms_e2e = max_over_ranks(e0.elapsed_time(e1), world)
-        e2e = {"value": world * flops * args.steps / (ms_e2e * 1e-3) / 1e12, "unit": "TFLOP/s",
+        e2e = {"value": (1 if shard else world) * flops * args.steps / (ms_e2e * 1e-3) / 1e12, "unit": "TFLOP/s",
                "ms_per_step": ms_e2e / args.steps,
                "h2d_bytes_per_step": int(L.nbytes + t2.nbytes), "d2h_bytes_per_step": int(t2.nbytes)}
+    elif L is not None:
+        R.zero_()
+        lad.ladder_apply(plan, Ld, td, R, ws)
+        torch.cuda.synchronize()
+    E_main = lad.ladder_energy(plan, td, R)
+    if shard:
+        import torch.distributed as dist
+        Et = torch.tensor([E_main], dtype=torch.float64, device="cuda")
+        dist.all_reduce(Et)   # the one exchange of the sharded contraction: a scalar
+        E_main = float(Et.item())
+    del ws
+    plan.close()
+    torch.cuda.empty_cache()
 
+    # FP64 (DMMA) path on the same workload, and both results against the oracle.
+    fp64 = None
+    accuracy = None
+    want_fp64 = args.fp64 == "on" or (args.fp64 == "auto" and precision == lad.LADDER_EMU_BF16 and world == 1)
+    R64 = None
+    if want_fp64 and L is not None:
+        fp64, R64 = run_fp64_compare(args, cfg, lad, Ld, td, local, stream)
+        fp64["speedup_vs_fp64"] = fp64["ms_per_call"] / ms_step
+    if L is not None and rank == 0 and not shard and not args.no_accuracy:
+        gold = golden_for(cfg)
+        R_host = Rh.numpy() if Rh is not None else R.cpu().numpy()
+        hosts = [R_host] + ([R64.cpu().numpy()] if R64 is not None else [])
+        errs, how = sampled_error(L, t2, hosts)
+        accuracy = {"tolerance": {"R_rel_fro": 1e-10 if precision == lad.LADDER_EMU_BF16 else 1e-12,
+                                  "E_L_abs_Eh": 1e-8},
+                    "sample": how, "R_rel_fro_sampled": errs[0], "E_L": E_main,
+                    "E_L_oracle": gold["E_L"] if gold else None,
+                    "E_L_abs_err": abs(E_main - gold["E_L"]) if gold else None,
+                    "R_fro": float(np.linalg.norm(R_host.ravel())),
+                    "R_fro_oracle": gold["R_fro"] if gold else None}
+        if R64 is not None:
+            accuracy["fp64_R_rel_fro_sampled"] = errs[1]
+            accuracy["fp64_E_L_abs_err"] = abs(fp64["E_L"] - gold["E_L"]) if gold else None
+            # the whole R of the two paths against each other (every element, on the device)
+            accuracy["R_rel_fro_vs_fp64_whole"] = float(torch.linalg.norm((R - R64).ravel()) /
+                                                        torch.linalg.norm(R64.ravel()))
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu, _, _ = cpu_baseline_sample(L, t2)
@@ -594,13 +731,13 @@ def main():
         line = {
             "metric": "PP-ladder TFLOP/s", "value": value, "unit": "TFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+            "scaling": "strong" if shard else "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
             "config": {"workload": f"{cfg.name}: no={cfg.no} nv={cfg.nv} nchol={cfg.nchol} seed={cfg.seed}",
                        "precision": args.precision, "form": form_used, "nslices": desc["nslices"],
-                       "n_a": desc["n_a"],
-                       "n_b": desc["n_b"], "block_pairs": desc["n_block_pairs"],
+                       "n_a": desc["n_a"], "n_b": desc["n_b"], "block_pairs": desc["n_block_pairs"],
                        "l2": "inputs+workspace > L2 (V block written and re-read every step)",
-                       "parallelism": f"independent instance per GPU x{world}"},
+                       "parallelism": (f"one contraction, block pairs sharded over {world} GPUs, E_L all-reduced"
+                                       if shard else f"independent instance per GPU x{world}")},
             "ms_per_call": ms_step,
             "kernel_ms_per_call": {k: v / args.steps for k, v in kms.items()},
             "gpu_launches": launches,
@@ -608,11 +745,60 @@ def main():
             "clocks": clocks,
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "fp64": fp64,
+            "speedup_vs_fp64": fp64["speedup_vs_fp64"] if fp64 else None,
+            "accuracy": accuracy,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--config", default="c3", choices=sorted(CONFIGS) + ["c5"])
+    ap.add_argument("--shape", default=None, help="no,nv,nchol overriding --config (profiling runs)")
+    ap.add_argument("--precision", default="emu", choices=["emu", "fp64"])
+    ap.add_argument("--nslices", type=int, default=0)
+    ap.add_argument("--form", default="auto", choices=["auto", "plain", "pm"],
+                    help="emulated ladder form: the planner's choice, plain, or the symmetric/antisymmetric split")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mode", default="replicas", choices=["replicas", "shard"],
+                    help="N>1: an independent instance per GPU, or one contraction sharded over the GPUs")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true", help="skip the error report against the oracle")
+    ap.add_argument("--fp64", default="auto", choices=["auto", "on", "off"],
+                    help="also time the native FP64 path on the workload (auto: emulated runs on one GPU)")
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--device-inputs", action="store_true",
+                    help="draw L and t2 on the GPU (timing-only runs at large shapes)")
+    ap.add_argument("--budget-gb", type=float, default=0.0, help="workspace budget (0: 0.9*0.98*free)")
+    ap.add_argument("--fp64-reference", action="store_true",
+                    help="c5: also time 24 sequential native-FP64 calls (slow)")
+    ap.add_argument("--measure-peaks", action="store_true",
+                    help="print torch/cuBLAS matmul throughput for fp64, bf16 and int8 and exit")
+    args = ap.parse_args()
+    if args.measure_peaks:
+        measure_peaks()
+        return
+    if args.config == "c5":
+        run_batched(args)
+        return
+    cfg = CONFIGS[args.config]
+    if args.shape:
+        no, nv, nchol = (int(x) for x in args.shape.split(","))
+        cfg = LadderShape(no=no, nv=nv, nchol=nchol, seed=4242, name="custom")
+    if args.warmup < 3:
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args, cfg)
+        return
+    run_single(args, cfg)
 
 
 if __name__ == "__main__":

@@ -164,7 +164,15 @@ int ladder_plan_shard(ladder_plan_t plan, int rank, int world);
  * workspace bytes, the number of (A,B) block pairs, and up to max_blocks rows
  * of blocks[5*k..5*k+4] = {a0, a1, b0, b1, npairs} in execution order.
  * Returns LADDER_OK, LADDER_ERR_ARG, LADDER_ERR_BUDGET or LADDER_ERR_UNSUPPORTED.
+ *
+ * ladder_plan_shard_dry -- the same host-only planner followed by the selection that
+ * ladder_plan_shard makes for rank `rank` of `world` (block pairs re-selected when fewer than
+ * 2*world, then the longest-first partition): outputs as above, for the rank's own block pairs
+ * (the workspace bytes are its shard's).  LADDER_ERR_ARG also for rank outside [0, world).
  */
+int ladder_plan_shard_dry(int no, int nv, int nchol, int precision, int nslices, size_t ws_budget_bytes, int num_sms,
+                          int rank, int world, int* n_a, int* n_b, size_t* ws_bytes, int max_blocks,
+                          int* n_block_pairs, int* blocks);
 int ladder_plan_dry(int no, int nv, int nchol, int precision, int nslices, size_t ws_budget_bytes, int num_sms,
                     int force_n_a, int force_n_b, int* n_a, int* n_b, size_t* ws_bytes, int max_blocks,
                     int* n_block_pairs, int* blocks);

@@ -101,6 +101,9 @@ def _load():
     lib.ladder_plan_dry.argtypes = [ci, ci, ci, ci, ci, sz, ci, ci, ci, pint, pint, ctypes.POINTER(sz), ci, pint,
                                     pint]
     lib.ladder_plan_dry.restype = ci
+    lib.ladder_plan_shard_dry.argtypes = [ci, ci, ci, ci, ci, sz, ci, ci, ci, pint, pint, ctypes.POINTER(sz), ci,
+                                          pint, pint]
+    lib.ladder_plan_shard_dry.restype = ci
     lib.ladder_plan_set_wait_limit.argtypes = [vp, ctypes.c_double]
     lib.ladder_plan_set_wait_limit.restype = ci
     lib.ladder_plan_get_wait_limit.argtypes = [vp]
@@ -273,6 +276,22 @@ def ladder_plan_dry(no, nv, nchol, precision=LADDER_FP64, nslices=0, ws_budget_b
     return {"n_a": na.value, "n_b": nb.value, "ws_bytes": ws.value, "n_block_pairs": nbp.value, "blocks": blocks}
 
 
+def ladder_plan_shard_dry(no, nv, nchol, rank, world, precision=LADDER_FP64, nslices=0, ws_budget_bytes=1 << 40,
+                          num_sms=152, max_blocks=1 << 16):
+    """Host-only: the block pairs ladder_plan_shard keeps for rank `rank` of `world`, as
+    dict(n_a, n_b, ws_bytes, blocks=[(a0, a1, b0, b1, npairs), ...])."""
+    na, nb, nbp = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    ws = ctypes.c_size_t()
+    buf = (ctypes.c_int * (5 * max_blocks))()
+    _check(_load().ladder_plan_shard_dry(int(no), int(nv), int(nchol), int(precision), int(nslices),
+                                         int(ws_budget_bytes), int(num_sms), int(rank), int(world), ctypes.byref(na),
+                                         ctypes.byref(nb), ctypes.byref(ws), max_blocks, ctypes.byref(nbp), buf),
+           "ladder_plan_shard_dry")
+    n = min(nbp.value, max_blocks)
+    blocks = [tuple(buf[5 * k:5 * k + 5]) for k in range(n)]
+    return {"n_a": na.value, "n_b": nb.value, "ws_bytes": ws.value, "n_block_pairs": nbp.value, "blocks": blocks}
+
+
 def ladder_form_model(no, nv, nchol, nslices=0) -> int:
     """Form the emulated path's cost model picks for a shape (0 plain, 1 symmetric/antisymmetric)."""
     r = int(_load().ladder_form_model(int(no), int(nv), int(nchol), int(nslices)))
@@ -380,4 +399,5 @@ EXPORTED_SYMBOLS = [
     "ladder_energy_noalloc", "ladder_tune_batched", "ladder_plan_shard", "ladder_shard_blocks",
     "ladder_watchdog_selftest", "ladder_batched_schedule", "ladder_plan_set_form", "ladder_plan_get_form",
     "ladder_form_model", "ladder_plan_set_wait_limit", "ladder_plan_get_wait_limit",
+    "ladder_plan_shard_dry",
 ]

@@ -370,6 +370,29 @@ int select_blocking(const ladder_plan_s& p, int* out_na, int* out_nb, int min_bl
     return LADDER_OK;
 }
 
+// The block pairs rank `rank` of `world` owns: the plan's blocking, or, when it has fewer than
+// 2 * world block pairs and the shape allows more, the best blocking under the same budget with
+// at least that many; then the longest-first partition of shard_owner.
+int shard_select(const ladder_plan_s& p, int rank, int world, int* na, int* nb, std::vector<BlockPair>* mine) {
+    const long long most = (long long)p.nv * (p.nv + 1) / 2;
+    const int want = (int)std::min<long long>(2LL * world, most);
+    std::vector<BlockPair> bps = p.bps;
+    *na = p.n_a;
+    *nb = p.n_b;
+    if ((int)bps.size() < want) {
+        const int rc = select_blocking(p, na, nb, want);
+        if (rc != LADDER_OK) return rc;
+        bps = enumerate_blocks(p.nv, *na, *nb);
+    }
+    std::vector<long long> np;
+    for (auto& b : bps) np.push_back(b.npairs);
+    const std::vector<int> owner = shard_owner(np, world);
+    mine->clear();
+    for (size_t i = 0; i < bps.size(); ++i)
+        if (owner[i] == rank) mine->push_back(bps[i]);
+    return LADDER_OK;
+}
+
 int choose_blocking(ladder_plan_s& p) {
     int na = 0, nb = 0;
     const int rc = select_blocking(p, &na, &nb);
@@ -635,22 +658,10 @@ int ladder_plan_shard(ladder_plan_t plan, int rank, int world) {
     if (world == 1) return LADDER_OK;
     DeviceGuard guard(plan->device);
     if (!guard.ok) return LADDER_ERR_CUDA;
-    // Enough block pairs to balance: at least two per rank where the shape allows it.
-    const long long most = (long long)plan->nv * (plan->nv + 1) / 2;
-    const int want = (int)std::min<long long>(2LL * world, most);
-    std::vector<BlockPair> bps = plan->bps;
-    int na = plan->n_a, nb = plan->n_b;
-    if ((int)bps.size() < want) {
-        const int rc = select_blocking(*plan, &na, &nb, want);
-        if (rc != LADDER_OK) return rc;
-        bps = enumerate_blocks(plan->nv, na, nb);
-    }
-    std::vector<long long> np;
-    for (auto& b : bps) np.push_back(b.npairs);
-    const std::vector<int> owner = shard_owner(np, world);
+    int na = 0, nb = 0;
     std::vector<BlockPair> mine;
-    for (size_t i = 0; i < bps.size(); ++i)
-        if (owner[i] == rank) mine.push_back(bps[i]);
+    const int rc = shard_select(*plan, rank, world, &na, &nb, &mine);
+    if (rc != LADDER_OK) return rc;
     plan->n_a = na;
     plan->n_b = nb;
     plan->bps = std::move(mine);
@@ -1033,15 +1044,19 @@ int ladder_last_status(ladder_plan_t plan, cudaStream_t stream) {
 
 void ladder_plan_destroy(ladder_plan_t plan) { destroy_plan(plan); }
 
-int ladder_plan_dry(int no, int nv, int nchol, int precision, int nslices, size_t ws_budget_bytes, int num_sms,
-                    int force_n_a, int force_n_b, int* n_a, int* n_b, size_t* ws_bytes, int max_blocks,
-                    int* n_block_pairs, int* blocks) {
+}  // extern "C"
+
+namespace {
+
+// Host-only plan of ladder_plan_dry / ladder_plan_shard_dry: the blocking ladder_plan would
+// choose (or the forced one), with no CUDA call.
+int dry_plan(ladder_plan_s& p, int no, int nv, int nchol, int precision, int nslices, size_t ws_budget_bytes,
+             int num_sms, int force_n_a, int force_n_b) {
     if (no < 1 || nv < 1 || nchol < 1 || num_sms < 1 || ws_budget_bytes == 0) return LADDER_ERR_ARG;
     if (precision == LADDER_EMU_INT8) return LADDER_ERR_UNSUPPORTED;
     if (precision != LADDER_FP64 && precision != LADDER_EMU_BF16) return LADDER_ERR_ARG;
     if (nslices == 0) nslices = ladder::kDefaultSlices;
     if (precision == LADDER_EMU_BF16 && (nslices < 5 || nslices > 8)) return LADDER_ERR_ARG;
-    ladder_plan_s p;
     p.no = no;
     p.nv = nv;
     p.nchol = nchol;
@@ -1061,12 +1076,18 @@ int ladder_plan_dry(int no, int nv, int nchol, int precision, int nslices, size_
     } else if (na > nv || nb > nv) {
         return LADDER_ERR_ARG;
     }
-    const std::vector<BlockPair> bps = enumerate_blocks(nv, na, nb);
-    const ladder::WsLayout w = layout_for(p, max_pairs_of(bps));
-    if (w.total > p.budget) return LADDER_ERR_BUDGET;
-    if (n_a) *n_a = na;
-    if (n_b) *n_b = nb;
-    if (ws_bytes) *ws_bytes = w.total;
+    p.bps = enumerate_blocks(nv, na, nb);
+    p.n_a = na;
+    p.n_b = nb;
+    if (layout_for(p, max_pairs_of(p.bps)).total > p.budget) return LADDER_ERR_BUDGET;
+    return LADDER_OK;
+}
+
+void dry_outputs(const ladder_plan_s& p, const std::vector<BlockPair>& bps, int* n_a, int* n_b, size_t* ws_bytes,
+                 int max_blocks, int* n_block_pairs, int* blocks) {
+    if (n_a) *n_a = p.n_a;
+    if (n_b) *n_b = p.n_b;
+    if (ws_bytes) *ws_bytes = layout_for(p, max_pairs_of(bps)).total;
     if (n_block_pairs) *n_block_pairs = (int)bps.size();
     if (blocks) {
         for (int k = 0; k < (int)bps.size() && k < max_blocks; ++k) {
@@ -1077,6 +1098,38 @@ int ladder_plan_dry(int no, int nv, int nchol, int precision, int nslices, size_
             blocks[5 * k + 4] = bps[k].npairs;
         }
     }
+}
+
+}  // namespace
+
+extern "C" {
+
+int ladder_plan_dry(int no, int nv, int nchol, int precision, int nslices, size_t ws_budget_bytes, int num_sms,
+                    int force_n_a, int force_n_b, int* n_a, int* n_b, size_t* ws_bytes, int max_blocks,
+                    int* n_block_pairs, int* blocks) {
+    ladder_plan_s p;
+    const int rc = dry_plan(p, no, nv, nchol, precision, nslices, ws_budget_bytes, num_sms, force_n_a, force_n_b);
+    if (rc != LADDER_OK) return rc;
+    dry_outputs(p, p.bps, n_a, n_b, ws_bytes, max_blocks, n_block_pairs, blocks);
+    return LADDER_OK;
+}
+
+int ladder_plan_shard_dry(int no, int nv, int nchol, int precision, int nslices, size_t ws_budget_bytes,
+                          int num_sms, int rank, int world, int* n_a, int* n_b, size_t* ws_bytes, int max_blocks,
+                          int* n_block_pairs, int* blocks) {
+    if (world < 1 || rank < 0 || rank >= world) return LADDER_ERR_ARG;
+    ladder_plan_s p;
+    int rc = dry_plan(p, no, nv, nchol, precision, nslices, ws_budget_bytes, num_sms, 0, 0);
+    if (rc != LADDER_OK) return rc;
+    if (world > 1) {
+        int na = 0, nb = 0;
+        std::vector<BlockPair> mine;
+        if ((rc = shard_select(p, rank, world, &na, &nb, &mine)) != LADDER_OK) return rc;
+        p.n_a = na;
+        p.n_b = nb;
+        p.bps = std::move(mine);
+    }
+    dry_outputs(p, p.bps, n_a, n_b, ws_bytes, max_blocks, n_block_pairs, blocks);
     return LADDER_OK;
 }
 

@@ -85,3 +85,66 @@ def test_two_gloo_ranks_cover_every_pair_once_and_reduce_the_energy(tmp_path):
     # disjoint parts: their sum is the full R (mirrors agree with the direct sums to rounding)
     assert np.max(np.abs(res["R"] - full)) <= 1e-13 * np.max(np.abs(full))
     assert float(res["E"][0]) == pytest.approx(oracle.energy(t2, full), rel=1e-12)
+
+
+def _shard_rank_main(rank, world, port, out_dir, precision):
+    """One gloo rank: its block pairs from the library's own shard selection (ladder_plan_shard's
+    host logic, run without a GPU), the oracle's contraction of those pairs, E_L all-reduced."""
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        no, nv, nchol = 3, 29, 40
+        L, t2, _, _ = make_inputs(no, nv, nchol, seed=78)
+        # the default plan of this shape is one block pair: the shard selection re-blocks
+        mine = lad.ladder_plan_shard_dry(no, nv, nchol, rank, world, precision=precision)
+        pairs = [(a, b) for (a0, a1, b0, b1, _) in mine["blocks"]
+                 for a in range(a0, a1) for b in range(max(a, b0), b1)]
+        Rp = np.zeros_like(t2)
+        if pairs:
+            out = oracle.ladder_pairs(L, t2, [p[0] for p in pairs], [p[1] for p in pairs])
+            for k, (a, b) in enumerate(pairs):
+                Rp[:, :, a, b] = out[k]
+                if a < b:
+                    Rp[:, :, b, a] = out[k].T
+        E = torch.tensor([oracle.energy(t2, Rp)], dtype=torch.float64)
+        dist.all_reduce(E)
+        owned = torch.zeros(nv, nv, dtype=torch.int64)
+        for a, b in pairs:
+            owned[a, b] += 1
+        dist.all_reduce(owned)
+        blocks = [torch.zeros(1, dtype=torch.int64) for _ in range(world)]
+        dist.all_gather(blocks, torch.tensor([mine["n_block_pairs"]], dtype=torch.int64))
+        if rank == 0:
+            np.savez(os.path.join(out_dir, f"shard{precision}.npz"), E=E.numpy(), owned=owned.numpy(),
+                     blocks=np.array([int(b) for b in blocks]), na=mine["n_a"], nb=mine["n_b"])
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("precision", [lad.LADDER_FP64, lad.LADDER_EMU_BF16])
+def test_two_gloo_ranks_shard_through_the_library_planner(tmp_path, precision):
+    import torch.multiprocessing as mp
+    world = 2
+    no, nv, nchol = 3, 29, 40
+    assert lad.ladder_plan_dry(no, nv, nchol, precision)["n_block_pairs"] == 1
+    mp.spawn(_shard_rank_main, args=(world, _free_port(), str(tmp_path), precision), nprocs=world, join=True)
+    res = np.load(tmp_path / f"shard{precision}.npz")
+    owned = res["owned"]
+    # every a <= b pair exactly once over the ranks, nothing below the diagonal
+    iu = np.triu_indices(nv)
+    assert np.all(owned[iu] == 1)
+    assert int(owned.sum()) == nv * (nv + 1) // 2
+    # re-blocked to at least two block pairs per rank, each rank holding some
+    assert int(res["blocks"].sum()) >= 2 * world and np.all(res["blocks"] >= 1)
+    L, t2, _, _ = make_inputs(no, nv, nchol, seed=78)
+    assert float(res["E"][0]) == pytest.approx(oracle.energy(t2, oracle.ladder(L, t2)), rel=1e-12)
+    # the library's shard of rank r equals its partition of the re-selected blocking
+    both = [lad.ladder_plan_shard_dry(no, nv, nchol, r, world, precision=precision) for r in range(world)]
+    whole = lad.ladder_plan_dry(no, nv, nchol, precision, force_n_a=both[0]["n_a"], force_n_b=both[0]["n_b"])
+    owner = lad.ladder_shard_blocks([b[4] for b in whole["blocks"]], world)
+    for r in range(world):
+        assert both[r]["blocks"] == [blk for blk, o in zip(whole["blocks"], owner) if o == r]
+    with pytest.raises(lad.LadderError):
+        lad.ladder_plan_shard_dry(no, nv, nchol, 2, 2)
