@@ -129,6 +129,30 @@ int ladder_plan_get_form(ladder_plan_t plan);
 int ladder_form_model(int no, int nv, int nchol, int nslices);
 
 /*
+ * ladder_plan_set_path -- evaluation order of a plan (Sec. "Acceleration of CC calculations":
+ * the ladder term can be evaluated by rebuilding (ac|bd) from the Cholesky vectors, 2 x v^4 work
+ * per vector, or by contracting the amplitudes with one Cholesky factor at a time, x o^2 v^3
+ * work per factor; which is cheaper depends on x against o^2 and on v against o^2).
+ *   LADDER_PATH_ERI (0): (ac|bd) rebuilt per (A,B) block pair of a <= b pairs, then the ladder
+ *     GEMM: 2 nchol nv^2 p + 2 no^2 nv^2 p flops (p = nv(nv+1)/2).
+ *   LADDER_PATH_FACTORISED (1): R_ij = sum_P L_P T_ij L_P^T over the amplitude pairs i <= j
+ *     (R_ji = R_ij^T from t_ji^cd = t_ij^dc), as two FP64 DMMA GEMMs per batch of Cholesky
+ *     vectors through a workspace W[o(o+1)/2][nv][batch][nv]: 4 nchol o(o+1)/2 nv^3 flops.
+ *     Native FP64 plans only (LADDER_ERR_UNSUPPORTED for the emulated path).
+ * ladder_plan picks, for an FP64 plan, the path with the fewer modelled flops (the factorised one
+ * must be 1.25x cheaper) when its workspace fits; emulated plans use path 0.  Forcing a blocking
+ * (ladder_plan_set_blocks) or sharding (ladder_plan_shard) returns a plan to path 0.
+ * Returns LADDER_OK, LADDER_ERR_ARG, LADDER_ERR_UNSUPPORTED, LADDER_ERR_BUDGET (the batch of one
+ * Cholesky vector does not fit) or LADDER_ERR_CUDA.  ladder_plan_get_path: the plan's path, -1 for
+ * NULL.  ladder_path_model: host only, the path ladder_plan would pick for this shape and
+ * precision before the workspace check (0 or 1; -1 for invalid arguments).
+ */
+enum { LADDER_PATH_ERI = 0, LADDER_PATH_FACTORISED = 1 };
+int ladder_plan_set_path(ladder_plan_t plan, int path);
+int ladder_plan_get_path(ladder_plan_t plan);
+int ladder_path_model(int no, int nv, int nchol, int precision);
+
+/*
  * Data-parallel sharding over several GPUs (the multi-GPU direction named in
  * Sec. "Conclusions and outlook"; the sharding itself is this library's).
  * The (A,B) block pairs of one contraction are independent: each writes the
@@ -304,7 +328,9 @@ enum {
     LADDER_KERNEL_LADDER = 2,   /* ladder GEMM                                        */
     LADDER_KERNEL_FINISH = 3,   /* accumulator finalisation / unpack                  */
     LADDER_KERNEL_COMBINE = 4,  /* V' and V'' from V (symmetric/antisymmetric form)   */
-    LADDER_KERNEL_CLASSES = 5
+    LADDER_KERNEL_FACT_W = 5,   /* factorised path: W = L_P T_ij                      */
+    LADDER_KERNEL_FACT_R = 6,   /* factorised path: R_ij += W L_P^T                   */
+    LADDER_KERNEL_CLASSES = 7
 };
 int ladder_plan_set_timing(ladder_plan_t plan, int enable);
 int ladder_plan_timing(ladder_plan_t plan, int kernel_class, float* total_ms, int* launches, int reset);

@@ -37,6 +37,11 @@ LADDER_KERNEL_ERI = 1
 LADDER_KERNEL_LADDER = 2
 LADDER_KERNEL_FINISH = 3
 LADDER_KERNEL_COMBINE = 4
+LADDER_KERNEL_FACT_W = 5
+LADDER_KERNEL_FACT_R = 6
+
+LADDER_PATH_ERI = 0
+LADDER_PATH_FACTORISED = 1
 
 # LADDER_CHECKED_LIBRARY=1 loads the index-checked build (build.build(check=True)) instead.
 LIB_PATH = _build_mod.LIB_CHECK if os.environ.get("LADDER_CHECKED_LIBRARY") == "1" else _build_mod.LIB
@@ -68,6 +73,12 @@ def _load():
     lib.ladder_plan_get_form.restype = ci
     lib.ladder_form_model.argtypes = [ci, ci, ci, ci]
     lib.ladder_form_model.restype = ci
+    lib.ladder_plan_set_path.argtypes = [vp, ci]
+    lib.ladder_plan_set_path.restype = ci
+    lib.ladder_plan_get_path.argtypes = [vp]
+    lib.ladder_plan_get_path.restype = ci
+    lib.ladder_path_model.argtypes = [ci, ci, ci, ci]
+    lib.ladder_path_model.restype = ci
     lib.ladder_batched_schedule.argtypes = [vp, ci, pint]
     lib.ladder_batched_schedule.restype = ci
     lib.ladder_watchdog_selftest.argtypes = [ctypes.c_double, ctypes.POINTER(ctypes.c_double), vp]
@@ -189,6 +200,13 @@ class Plan:
     def form(self) -> int:
         return int(_load().ladder_plan_get_form(self._h))
 
+    def path(self) -> int:
+        return int(_load().ladder_plan_get_path(self._h))
+
+    def set_path(self, path: int):
+        """0: rebuild (ac|bd) per block pair; 1: factorised sum_P L_P T_ij L_P^T (FP64 plans)."""
+        _check(_load().ladder_plan_set_path(self._h, int(path)), "ladder_plan_set_path")
+
     def set_form(self, form: int):
         """Emulated ladder form: 0 plain, 1 symmetric/antisymmetric (see ladder_plan_set_form)."""
         _check(_load().ladder_plan_set_form(self._h, int(form)), "ladder_plan_set_form")
@@ -300,6 +318,14 @@ def ladder_form_model(no, nv, nchol, nslices=0) -> int:
     return r
 
 
+def ladder_path_model(no, nv, nchol, precision=LADDER_FP64) -> int:
+    """Evaluation order ladder_plan picks for a shape (0 rebuild, 1 factorised), host only."""
+    r = int(_load().ladder_path_model(int(no), int(nv), int(nchol), int(precision)))
+    if r < 0:
+        raise LadderError(LADDER_ERR_ARG, "ladder_path_model")
+    return r
+
+
 def ladder_shard_blocks(npairs, world: int):
     """Owner rank of each block pair (pair counts `npairs`) when spread over `world` ranks."""
     n = len(npairs)
@@ -399,5 +425,5 @@ EXPORTED_SYMBOLS = [
     "ladder_energy_noalloc", "ladder_tune_batched", "ladder_plan_shard", "ladder_shard_blocks",
     "ladder_watchdog_selftest", "ladder_batched_schedule", "ladder_plan_set_form", "ladder_plan_get_form",
     "ladder_form_model", "ladder_plan_set_wait_limit", "ladder_plan_get_wait_limit",
-    "ladder_plan_shard_dry",
+    "ladder_plan_shard_dry", "ladder_plan_set_path", "ladder_plan_get_path", "ladder_path_model",
 ]

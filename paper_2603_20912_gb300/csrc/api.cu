@@ -106,7 +106,10 @@ ladder::WsLayout layout_for(const ladder_plan_s& p, long long max_pairs) {
     const size_t nv2 = (size_t)p.nv * p.nv, no2 = (size_t)p.no * p.no;
     size_t off = 0;
     auto take = [&](size_t bytes) { const size_t o = off; off = align_up(off + bytes, kAlign); return o; };
-    if (p.precision == LADDER_FP64) {
+    if (p.path == 1) {
+        const size_t npij = (size_t)p.no * (p.no + 1) / 2;
+        w.w_blk = take(npij * nv2 * (size_t)p.fact_pb * sizeof(double));
+    } else if (p.precision == LADDER_FP64) {
         w.v_blk = take((size_t)max_pairs * nv2 * sizeof(double));
     } else {
         // (c, d) rows padded to vp (ladder::emu_vp): K index c*vp + d, zero for d >= nv.
@@ -196,6 +199,53 @@ double model_time(const ladder_plan_s& p, const std::vector<BlockPair>& bps) {
         t += g.overhead_s;
     }
     return t;
+}
+
+// Evaluation order (Sec. "Acceleration of CC calculations"): rebuilding (ac|bd) costs
+// 2 X v^2 p + 2 o^2 v^2 p flops with the a <= b packing; the factorised order
+// R_ij = sum_P L_P T_ij L_P^T costs 4 X v^3 per amplitude pair, o(o+1)/2 pairs with i <= j.
+// Both run on the same FP64 DMMA tiles, so the flop counts compare directly; the factorised
+// order is taken when it needs 1.25x fewer flops (it streams a W batch through HBM per
+// Cholesky batch).  The emulated path has only the rebuild order.
+double eri_path_flops(int no, int nv, int nchol) {
+    const double p = 0.5 * (double)nv * (nv + 1), v2 = (double)nv * nv;
+    return 2.0 * nchol * v2 * p + 2.0 * (double)no * no * v2 * p;
+}
+double fact_path_flops(int no, int nv, int nchol) {
+    return 4.0 * nchol * (0.5 * no * (no + 1.0)) * (double)nv * nv * nv;
+}
+int auto_path(int no, int nv, int nchol, int precision) {
+    if (precision != LADDER_FP64) return 0;
+    return 1.25 * fact_path_flops(no, nv, nchol) < eri_path_flops(no, nv, nchol) ? 1 : 0;
+}
+
+// Cholesky vectors per batch of the factorised path: as many as the budget holds (W is
+// 8 o(o+1)/2 nv^2 bytes per vector), at most nchol and at most 65535 / (o(o+1)/2) (grid z of the
+// first GEMM); LADDER_ERR_BUDGET when not even one vector fits.
+int use_factorised(ladder_plan_s& p) {
+    const long long npij = (long long)p.no * (p.no + 1) / 2;
+    const double per = 8.0 * npij * (double)p.nv * p.nv;
+    long long pb = (long long)std::floor((double)p.budget / per);
+    pb = std::min<long long>(pb, p.nchol);
+    pb = std::min<long long>(pb, 65535 / npij);
+    if (pb < 1) return LADDER_ERR_BUDGET;
+    const int old_pb = p.fact_pb, old_path = p.path;
+    p.fact_pb = (int)pb;
+    p.path = 1;
+    const ladder::WsLayout w = layout_for(p, 0);
+    if (w.total > p.budget) {
+        p.fact_pb = old_pb;
+        p.path = old_path;
+        return LADDER_ERR_BUDGET;
+    }
+    p.ws = w;
+    return LADDER_OK;
+}
+
+// Modelled seconds of one call (scheduling of batched plans).
+double plan_time(const ladder_plan_s& p) {
+    if (p.path == 1) return fact_path_flops(p.no, p.nv, p.nchol) / 1.0e12 + 20e-6;
+    return model_time(p, p.bps);
 }
 
 // ERI row tiles of the emulated path.  The rows of L^T are (x, y) = x vp + y, and L^P is
@@ -518,6 +568,12 @@ int make_plan(ladder_plan_s** out, int no, int nv, int nchol, int precision, int
         p->form = 0;
         rc = choose_blocking(*p);
     }
+    // FP64: the factorised order when the model prefers it and its batch fits (also when no
+    // blocking of the rebuild order fits the budget).
+    if ((rc == LADDER_OK || rc == LADDER_ERR_BUDGET) && precision == LADDER_FP64 &&
+        (auto_path(no, nv, nchol, precision) == 1 || rc == LADDER_ERR_BUDGET)) {
+        if (use_factorised(*p) == LADDER_OK) rc = LADDER_OK;
+    }
     if (rc == LADDER_OK) {
         if (cudaMalloc(&p->d_status, sizeof(unsigned)) != cudaSuccess ||
             cudaMemset(p->d_status, 0, sizeof(unsigned)) != cudaSuccess)
@@ -639,10 +695,18 @@ int ladder_plan_set_blocks(ladder_plan_t plan, int n_a, int n_b) {
     if (n_a < 1 || n_b < 1 || n_a > plan->nv || n_b > plan->nv) return LADDER_ERR_ARG;
     DeviceGuard guard(plan->device);
     if (!guard.ok) return LADDER_ERR_CUDA;
-    // Validate before touching the plan so a rejected request leaves it intact.
+    // Validate before touching the plan so a rejected request leaves it intact.  A blocking
+    // belongs to the rebuild order: a factorised plan returns to it.
     std::vector<BlockPair> bps = enumerate_blocks(plan->nv, n_a, n_b);
-    if (layout_for(*plan, max_pairs_of(bps)).total > plan->budget) return LADDER_ERR_BUDGET;
-    return apply_blocking(*plan, n_a, n_b);
+    const int old_path = plan->path;
+    plan->path = 0;
+    if (layout_for(*plan, max_pairs_of(bps)).total > plan->budget) {
+        plan->path = old_path;
+        return LADDER_ERR_BUDGET;
+    }
+    const int rc = apply_blocking(*plan, n_a, n_b);
+    if (rc != LADDER_OK) plan->path = old_path;
+    return rc;
 }
 
 int ladder_shard_blocks(int n_blocks, const long long* npairs, int world, int* owner) {
@@ -658,6 +722,13 @@ int ladder_plan_shard(ladder_plan_t plan, int rank, int world) {
     if (world == 1) return LADDER_OK;
     DeviceGuard guard(plan->device);
     if (!guard.ok) return LADDER_ERR_CUDA;
+    if (plan->path == 1) {   // sharding splits block pairs of the rebuild order
+        plan->path = 0;
+        if (plan->bps.empty() && choose_blocking(*plan) != LADDER_OK) {
+            plan->path = 1;
+            return LADDER_ERR_BUDGET;
+        }
+    }
     int na = 0, nb = 0;
     std::vector<BlockPair> mine;
     const int rc = shard_select(*plan, rank, world, &na, &nb, &mine);
@@ -699,6 +770,38 @@ int ladder_form_model(int no, int nv, int nchol, int nslices) {
     return auto_form(no, nv, nchol, nslices);
 }
 
+int ladder_plan_set_path(ladder_plan_t plan, int path) {
+    if (!plan || plan->batched || (path != 0 && path != 1)) return LADDER_ERR_ARG;
+    if (path == 1 && plan->precision != LADDER_FP64) return LADDER_ERR_UNSUPPORTED;
+    if (path == plan->path) return LADDER_OK;
+    DeviceGuard guard(plan->device);
+    if (!guard.ok) return LADDER_ERR_CUDA;
+    if (path == 1) {
+        if (plan->shard_world > 1) return LADDER_ERR_ARG;   // a shard holds block pairs only
+        return use_factorised(*plan);
+    }
+    plan->path = 0;
+    int rc = plan->bps.empty() ? LADDER_ERR_BUDGET : LADDER_OK;
+    if (rc == LADDER_OK) {
+        const ladder::WsLayout w = layout_for(*plan, plan->max_pairs);
+        if (w.total <= plan->budget) plan->ws = w; else rc = LADDER_ERR_BUDGET;
+    }
+    if (rc == LADDER_ERR_BUDGET) rc = choose_blocking(*plan);
+    if (rc != LADDER_OK) {
+        plan->path = 1;
+        plan->ws = layout_for(*plan, 0);
+    }
+    return rc;
+}
+
+int ladder_plan_get_path(ladder_plan_t plan) { return plan ? plan->path : -1; }
+
+int ladder_path_model(int no, int nv, int nchol, int precision) {
+    if (no < 1 || nv < 1 || nchol < 1) return -1;
+    if (precision != LADDER_FP64 && precision != LADDER_EMU_BF16) return -1;
+    return auto_path(no, nv, nchol, precision);
+}
+
 size_t ladder_workspace_bytes(ladder_plan_t plan) {
     if (!plan) return 0;
     return plan->ws.total;
@@ -723,7 +826,9 @@ int ladder_apply(ladder_plan_t plan, const double* L, const double* t2, double* 
     DeviceGuard guard(plan->device);
     if (!guard.ok) return LADDER_ERR_CUDA;
     cudaError_t e = cudaSuccess;
-    if (plan->precision == LADDER_FP64) {
+    if (plan->path == 1) {
+        e = ladder::launch_fp64_factorised(*plan, L, t2, R, ws, stream);
+    } else if (plan->precision == LADDER_FP64) {
         for (const auto& bp : plan->bps) {
             e = ladder::launch_fp64_block(*plan, bp, L, t2, R, ws, stream);
             if (e != cudaSuccess) break;
@@ -787,7 +892,7 @@ int ladder_plan_batched(ladder_plan_t* out, int n, const int* no, const int* nv,
             return rc;
         }
         p->sub.push_back(s);
-        p->model_s.push_back(model_time(*s, s->bps));
+        p->model_s.push_back(plan_time(*s));
     }
     p->nslices = p->sub[0]->nslices;
     p->num_sms = p->sub[0]->num_sms;

@@ -14,6 +14,8 @@
 // b > a, which no pair owns directly -- so no atomics are needed.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "ladder_internal.h"
 
 namespace ladder {
@@ -195,7 +197,135 @@ __global__ void __launch_bounds__(THREADS) ladder_fp64_kernel(const double* __re
     }
 }
 
+// ---------------------------------------------------------------- factorised path
+// R_ij = sum_P L_P T_ij L_P^T (Sec. "Acceleration of CC calculations": the evaluation order that
+// contracts the amplitudes with one Cholesky factor at a time, x o^2 v^3 work per factor, instead
+// of rebuilding (ac|bd)), over the amplitude pairs i <= j only (R_ji = R_ij^T, from
+// t_ji^cd = t_ij^dc), in batches of Cholesky vectors P in [P0, P0 + pb):
+//   W[ij][a][p][d] = sum_c L[P0+p, a, c] t2[i, j, c, d]        (fact_w_kernel)
+//   R[i,j,a,b] += sum_{p,d} W[ij][a][p][d] L[P0+p, b, d]        (fact_r_kernel)
+//   and R[j,i,b,a] += the same value for i < j.
+// (i, j) of packed index u of the upper triangle (i <= j) of an n x n grid, row-major.
+__device__ __forceinline__ void upper_pair(int u, int n, int& i, int& j) {
+    int r = 0, start = 0;
+    while (start + (n - r) <= u) {
+        start += n - r;
+        ++r;
+    }
+    i = r;
+    j = r + (u - start);
+}
+
+// L rows b over the contraction index k = (p, d) of a batch of Cholesky vectors:
+// elem(b, k) = L[P0 + k / nv][b][k % nv].
+struct LPanel {
+    const double* base;  // L + P0 * nv^2
+    int nv, M, K;
+    __device__ __forceinline__ void load(double (&r)[8], int m0, int k0) const {
+        const int t = threadIdx.x;
+        const int gk = k0 + (t & 15);
+        const int p = gk / nv, d = gk - p * nv;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int gm = m0 + (t >> 4) + 8 * i;
+            r[i] = (gm < M && gk < K) ? __ldg(base + ((size_t)p * nv + gm) * nv + d) : 0.0;
+        }
+    }
+    __device__ __forceinline__ void store(double (*s)[PADM], const double (&r)[8]) const {
+        const int t = threadIdx.x;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) s[t & 15][(t >> 4) + 8 * i] = r[i];
+    }
+};
+
+// Grid: x over a tiles, y over d tiles, z over (p, ij) with ij fastest (z < pb * npij).
+__global__ void __launch_bounds__(THREADS) fact_w_kernel(const double* __restrict__ L, const double* __restrict__ t2,
+                                                         int no, int nv, int P0, int pb, int npij,
+                                                         double* __restrict__ W) {
+    const int z = blockIdx.z, u = z % npij, p = z / npij;
+    int i, j;
+    upper_pair(u, no, i, j);
+    const size_t nv2 = (size_t)nv * nv;
+    const int m0 = blockIdx.x * TM, n0 = blockIdx.y * TN;
+    KInner A{L + (size_t)(P0 + p) * nv2, (size_t)nv, nv, nv};              // (a, c)
+    KOuter B{t2 + ((size_t)i * no + j) * nv2, (size_t)nv, nv, nv};          // (d, c)
+    double acc[4][4][2];
+    dgemm_tile(A, B, m0, n0, nv, acc);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int wm = warp >> 1, wn = warp & 1;
+    double* Wu = W + (size_t)u * nv * pb * nv;
+#pragma unroll
+    for (int mi = 0; mi < 4; ++mi) {
+        const int a = m0 + wm * 32 + mi * 8 + (lane >> 2);
+        if (a >= nv) continue;
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int d = n0 + wn * 32 + ni * 8 + 2 * (lane & 3) + e;
+                if (d < nv) Wu[((size_t)a * pb + p) * nv + d] = acc[mi][ni][e];
+            }
+    }
+}
+
+// Grid: x over a tiles, y over b tiles, z over ij (packed i <= j).
+__global__ void __launch_bounds__(THREADS) fact_r_kernel(const double* __restrict__ L, const double* __restrict__ W,
+                                                         int no, int nv, int P0, int pb, double* __restrict__ R) {
+    const int u = blockIdx.z;
+    int i, j;
+    upper_pair(u, no, i, j);
+    const size_t nv2 = (size_t)nv * nv;
+    const int K = pb * nv;
+    const int m0 = blockIdx.x * TM, n0 = blockIdx.y * TN;
+    KInner A{W + (size_t)u * nv * K, (size_t)K, nv, K};                     // (a, (p, d))
+    LPanel B{L + (size_t)P0 * nv2, nv, nv, K};                              // (b, (p, d))
+    double acc[4][4][2];
+    dgemm_tile(A, B, m0, n0, K, acc);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int wm = warp >> 1, wn = warp & 1;
+    double* Rij = R + ((size_t)i * no + j) * nv2;
+    double* Rji = R + ((size_t)j * no + i) * nv2;
+#pragma unroll
+    for (int mi = 0; mi < 4; ++mi) {
+        const int a = m0 + wm * 32 + mi * 8 + (lane >> 2);
+        if (a >= nv) continue;
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int b = n0 + wn * 32 + ni * 8 + 2 * (lane & 3) + e;
+                if (b >= nv) continue;
+                const double v = acc[mi][ni][e];
+                Rij[(size_t)a * nv + b] += v;
+                if (i < j) Rji[(size_t)b * nv + a] += v;
+            }
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_fp64_factorised(const ladder_plan_s& p, const double* L, const double* t2, double* R, void* ws,
+                                   cudaStream_t s) {
+    const int npij = p.no * (p.no + 1) / 2;
+    double* W = reinterpret_cast<double*>(static_cast<char*>(ws) + p.ws.w_blk);
+    const unsigned tiles = (unsigned)((p.nv + TM - 1) / TM);
+    for (int P0 = 0; P0 < p.nchol; P0 += p.fact_pb) {
+        const int pb = std::min(p.fact_pb, p.nchol - P0);
+        {
+            LaunchTimer t(p, s, LADDER_KERNEL_FACT_W);
+            fact_w_kernel<<<dim3(tiles, tiles, (unsigned)(pb * npij)), THREADS, 0, s>>>(L, t2, p.no, p.nv, P0, pb,
+                                                                                       npij, W);
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        {
+            LaunchTimer t(p, s, LADDER_KERNEL_FACT_R);
+            fact_r_kernel<<<dim3(tiles, tiles, (unsigned)npij), THREADS, 0, s>>>(L, W, p.no, p.nv, P0, pb, R);
+        }
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
 
 cudaError_t launch_fp64_block(const ladder_plan_s& p, const BlockPair& bp, const double* L,
                               const double* t2, double* R, void* ws, cudaStream_t s) {

@@ -72,6 +72,8 @@ struct WsLayout {
     size_t tp_gmax = 0, tm_gmax = 0;  // max |T'|, |T''| per group of rows (IEEE bits, u64)
     size_t tp_exp = 0, tm_exp = 0;    // exponent per group of rows (int)
     size_t rpx = 0, rpy = 0;          // int64 accumulators [max_pairs][np], [max_pairs][nm]
+    // FP64 factorised path: W batch [o(o+1)/2][nv][fact_pb][nv] f64
+    size_t w_blk = 0;
     size_t total = 0;
 };
 
@@ -127,6 +129,8 @@ struct ladder_plan_s {
     size_t budget = 0;
     int n_a = 0, n_b = 0;
     int form = 0;  // emulated ladder form: 0 = plain (K = (c,d)), 1 = symmetric/antisymmetric
+    int path = 0;     // 0: rebuild (ac|bd) per block pair; 1: factorised sum_P L_P T_ij L_P^T (FP64)
+    int fact_pb = 0;  // factorised path: Cholesky vectors per batch
     int shard_rank = 0, shard_world = 1;  // this plan holds shard `shard_rank` of `shard_world`
     std::vector<ladder::BlockPair> bps;
     int max_pairs = 0;
@@ -193,6 +197,8 @@ struct LaunchTimer {
 // fp64_kernels.cu
 cudaError_t launch_fp64_block(const ladder_plan_s& p, const BlockPair& bp, const double* L,
                               const double* t2, double* R, void* ws, cudaStream_t s);
+cudaError_t launch_fp64_factorised(const ladder_plan_s& p, const double* L, const double* t2, double* R, void* ws,
+                                   cudaStream_t s);
 // energy.cu
 cudaError_t launch_energy(const ladder_plan_s& p, const double* t2, const double* R, double* E_dev,
                           cudaStream_t s);

@@ -9,6 +9,7 @@ import numpy as np
 import pytest
 
 import paper_2603_20912_gb300 as lad
+from ladder_inputs import CONFIGS
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -156,3 +157,24 @@ def test_form_model_decisions():
     for bad in [(0, 5, 5, 0), (5, 0, 5, 0), (5, 5, 0, 0), (5, 5, 5, 4), (5, 5, 5, 9)]:
         with pytest.raises(lad.LadderError):
             lad.ladder_form_model(*bad)
+
+
+def test_path_model_decisions(lib):
+    # the factorised order R_ij = sum_P L_P T_ij L_P^T is taken for FP64 plans when it needs
+    # 1.25x fewer flops than rebuilding (ac|bd): 4 X o(o+1)/2 v^3 against 2 X v^2 p + 2 o^2 v^2 p
+    def rule(no, nv, nchol):
+        p = nv * (nv + 1) / 2
+        eri = 2.0 * nchol * nv * nv * p + 2.0 * no * no * nv * nv * p
+        fact = 4.0 * nchol * no * (no + 1) / 2 * nv ** 3
+        return 1 if 1.25 * fact < eri else 0
+    for name, want in (("c1", 0), ("c2", 0), ("c3", 0)):
+        s = CONFIGS[name]
+        assert lad.ladder_path_model(s.no, s.nv, s.nchol, lad.LADDER_FP64) == want
+    assert lad.ladder_path_model(12, 64, 8, lad.LADDER_FP64) == 1
+    for no in (1, 3, 10, 30):
+        for nv in (5, 40, 300):
+            for nchol in (1, 8, 100, 1000):
+                assert lad.ladder_path_model(no, nv, nchol, lad.LADDER_FP64) == rule(no, nv, nchol)
+                assert lad.ladder_path_model(no, nv, nchol, lad.LADDER_EMU_BF16) == 0
+    with pytest.raises(lad.LadderError):
+        lad.ladder_path_model(0, 5, 5)

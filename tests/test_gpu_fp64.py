@@ -49,12 +49,17 @@ def dev(x):
     return torch.from_numpy(np.ascontiguousarray(x)).cuda()
 
 
-def gpu_ladder(L, t2, precision=lad.LADDER_FP64, R0=None, blocks=None, budget=0, nslices=0):
+def gpu_ladder(L, t2, precision=lad.LADDER_FP64, R0=None, blocks=None, budget=0, nslices=0,
+               path=lad.LADDER_PATH_ERI):
+    """R from one ladder_apply.  FP64 plans are held to the given evaluation order (default:
+    rebuild (ac|bd) per block pair; the factorised order has its own tests)."""
     nchol, nv, _ = L.shape
     no = t2.shape[0]
     # the default budget is a fraction of the free memory: hand torch's cached blocks back first
     torch.cuda.empty_cache()
     plan = lad.ladder_plan(no, nv, nchol, precision, nslices=nslices, ws_budget_bytes=budget)
+    if precision == lad.LADDER_FP64 and path is not None:
+        plan.set_path(path)
     if blocks is not None:
         plan.set_blocks(*blocks)
     Ld, td = dev(L), dev(t2)
@@ -101,7 +106,9 @@ def test_small_budget_forces_split():
     no, nv, nchol = 3, 37, 45   # ragged against every tile size
     L, t2, _, _ = make_inputs(no, nv, nchol, seed=21)
     ref = oracle.ladder(L, t2)
-    full = lad.ladder_plan(no, nv, nchol).workspace_bytes()
+    one = lad.ladder_plan(no, nv, nchol)
+    one.set_path(lad.LADDER_PATH_ERI)
+    full = one.workspace_bytes()
     R, plan = gpu_ladder(L, t2, budget=full // 6)
     d = plan.describe()
     assert d["n_block_pairs"] > 1 and plan.workspace_bytes() <= full // 6

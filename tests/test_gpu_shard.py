@@ -38,6 +38,8 @@ def test_shards_add_up_to_the_whole(precision, world):
     Ld, td = torch.from_numpy(L).cuda(), torch.from_numpy(t2).cuda()
     budget = 1 << 34
     full = lad.ladder_plan(no, nv, nchol, precision, ws_budget_bytes=budget)
+    if precision == lad.LADDER_FP64:
+        full.set_path(lad.LADDER_PATH_ERI)   # the shards run the rebuild order
     R_full, E_full = _run(full, Ld, td)
     R_sum = torch.zeros_like(td)
     E_sum = 0.0
