@@ -314,22 +314,25 @@ def measure_peaks():
     print(json.dumps(out), flush=True)
 
 
-def run_batched(args):
-    """24 uneven instances (no ~ U{5..30}, nv ~ U{60..320}, nchol = 3(no+nv)) in one
-    ladder_apply_batched call per step, captured once into a CUDA graph and replayed."""
+def batched_record(args, lad, local, world, device_inputs, steps, warmup, fp64_sequential=False):
+    """The 24-instance uneven batch (no ~ U{5..30}, nv ~ U{60..320}, nchol = 3(no+nv), seed 1239)
+    in one ladder_apply_batched call per step: the measured tuner picks the schedule and the
+    ladder tile width on these buffers, the call is captured once into a CUDA graph and replayed
+    `steps` times after `warmup` replays, timed with CUDA events on the current stream."""
     import torch
-    import paper_2603_20912_gb300 as lad
-    from paper_2603_20912_gb300 import build
-    from ladder_inputs import batched_shapes, make_batched_inputs
-    world, rank, local = dist_setup(args)
-    torch.cuda.set_device(local)
-    build.build()
+    from ladder_inputs import batched_shapes, make_batched_inputs, make_device_inputs
     shapes = batched_shapes()
-    host = make_batched_inputs(shapes)
-    Ls = [torch.from_numpy(L).cuda() for L, _ in host]
-    ts = [torch.from_numpy(t).cuda() for _, t in host]
+    if device_inputs:
+        pairs = [make_device_inputs(s.no, s.nv, s.nchol, s.seed, device=f"cuda:{local}") for s in shapes]
+        Ls = [L for L, _ in pairs]
+        ts = [t for _, t in pairs]
+    else:
+        host = make_batched_inputs(shapes)
+        Ls = [torch.from_numpy(L).cuda() for L, _ in host]
+        ts = [torch.from_numpy(t).cuda() for _, t in host]
     Rs = [torch.zeros_like(t) for t in ts]
     precision = lad.LADDER_EMU_BF16 if args.precision == "emu" else lad.LADDER_FP64
+    torch.cuda.empty_cache()
     plan = lad.ladder_plan_batched([s.no for s in shapes], [s.nv for s in shapes], [s.nchol for s in shapes],
                                    precision, nslices=args.nslices, device=local)
     ws = plan.workspace()
@@ -345,7 +348,7 @@ def run_batched(args):
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g, stream=stream):
         lad.ladder_apply_batched(plan, Ls, ts, Rs, ws, stream=stream)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         g.replay()
     torch.cuda.synchronize()
     sampler = ClockSampler(local)
@@ -356,27 +359,26 @@ def run_batched(args):
     ev1 = torch.cuda.Event(enable_timing=True)
     cur = torch.cuda.current_stream()
     ev0.record(cur)
-    for _ in range(args.steps):
+    for _ in range(steps):
         g.replay()
     ev1.record(cur)
     torch.cuda.synchronize()
     clocks = sampler.stop()
+    assert plan.last_status() == lad.LADDER_OK
     ms_total = max_over_ranks(ev0.elapsed_time(ev1), world)
-    value = world * flops * args.steps / (ms_total * 1e-3) / 1e12
+    value = world * flops * steps / (ms_total * 1e-3) / 1e12
     fp64 = None
-    if args.fp64_reference:
-        ref = lad.ladder_plan_batched([s.no for s in shapes], [s.nv for s in shapes], [s.nchol for s in shapes],
-                                      lad.LADDER_FP64, device=local)
-        refws = ref.workspace()
+    if fp64_sequential:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for sh, L, t in zip(shapes, Ls, ts):   # 24 sequential FP64 calls
+        for sh, L, t in zip(shapes, Ls, ts):   # 24 sequential FP64 calls, each with its own plan
             single = lad.ladder_plan(sh.no, sh.nv, sh.nchol, lad.LADDER_FP64, device=local)
             lad.ladder_apply(single, L, t, torch.zeros_like(t))
             torch.cuda.synchronize()
+            single.close()
         fp64_s = time.perf_counter() - t0
-        fp64 = {"seconds": fp64_s, "tflops": flops / fp64_s / 1e12, "speedup": fp64_s / (ms_total * 1e-3 / args.steps)}
-        del refws
+        fp64 = {"seconds": fp64_s, "tflops": flops / fp64_s / 1e12,
+                "speedup": fp64_s / (ms_total * 1e-3 / steps)}
     peaks, peak_src = load_peaks()
     peak_key = "bf16_tflops_sustained" if ms_total >= 1000.0 else "bf16_tflops"
     peak = peaks.get(peak_key, peaks.get("bf16_tflops", FALLBACK_BF16_TFLOPS))
@@ -387,23 +389,47 @@ def run_batched(args):
         S = args.nslices or 6
         useful = sum(2.0 * s.nchol * eri_products(s.nv, s.nv, s.nv) + 2.0 * ladder_products(s.no, s.nv, "plain")
                      for s in shapes)
-        achieved = useful * (S * (S + 1) // 2) * args.steps / (ms_total * 1e-3) / 1e12
+        achieved = useful * (S * (S + 1) // 2) * steps / (ms_total * 1e-3) / 1e12
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "frac_of_burst": achieved / peaks.get("bf16_tflops", FALLBACK_BF16_TFLOPS),
                 "traffic": None, "kernel": "whole batched call (executed slice products, all kernels)",
                 "peak_source": f"{peak_key} ({peak_src})", "executed_slice_products": S * (S + 1) // 2}
+    tuned = plan.batched_choice()
+    rec = {"workload": "c5: 24 uneven instances, no~U{5..30}, nv~U{60..320}, nchol=3(no+nv), seed 1239",
+           "value": value, "unit": "TFLOP/s", "ms_per_step": ms_total / steps, "steps": steps, "warmup": warmup,
+           "instances": len(shapes), "total_flops": flops,
+           "schedule": (f"{-k} instance groups, one ERI launch and one ladder launch per shape per group"
+                        if k < 0 else f"{k} worker streams"),
+           "tuned": tuned,
+           "graph": "one CUDA graph replay per step",
+           "inputs": "drawn on the GPU (timing)" if device_inputs else "ladder_inputs host generators",
+           "roofline": roof, "clocks": clocks, "fp64_sequential": fp64}
+    del ws, Ls, ts, Rs
+    plan.close()
+    torch.cuda.empty_cache()
+    return rec, precision
+
+
+def run_batched(args):
+    """The uneven batch as the bench line (--config c5)."""
+    import torch
+    import paper_2603_20912_gb300 as lad
+    from paper_2603_20912_gb300 import build
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    build.build()
+    rec, precision = batched_record(args, lad, local, world, args.device_inputs, args.steps, args.warmup,
+                                    fp64_sequential=args.fp64_reference)
     if rank == 0:
         line = {
-            "metric": "PP-ladder TFLOP/s", "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64-emulated(bf16 slices)" if precision == lad.LADDER_EMU_BF16 else "f64",
+            "metric": "PP-ladder TFLOP/s", "value": rec["value"], "unit": "TFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": rec["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64-emulated(bf16 slices)" if precision == lad.LADDER_EMU_BF16 else "f64",
             "data": "synthetic",
-            "config": {"workload": "c5: 24 uneven instances, no~U{5..30}, nv~U{60..320}, nchol=3(no+nv), seed 1239",
-                       "instances": len(shapes), "total_flops": flops,
-                       "schedule": (f"{-k} instance groups, one ERI and one ladder launch per shape per group"
-                                    if k < 0 else f"{k} worker streams"),
-                       "graph": "one CUDA graph replay per step"},
-            "roofline": roof, "clocks": clocks, "fp64_sequential": fp64,
+            "config": {"workload": rec["workload"], "instances": rec["instances"], "total_flops": rec["total_flops"],
+                       "schedule": rec["schedule"], "tuned": rec["tuned"], "graph": rec["graph"]},
+            "roofline": rec["roofline"], "clocks": rec["clocks"], "fp64_sequential": rec["fp64_sequential"],
         }
         print(json.dumps(line), flush=True)
 
@@ -723,6 +749,17 @@ def run_single(args, cfg):
             # the whole R of the two paths against each other (every element, on the device)
             accuracy["R_rel_fro_vs_fp64_whole"] = float(torch.linalg.norm((R - R64).ravel()) /
                                                         torch.linalg.norm(R64.ravel()))
+    # The 24-instance uneven batch, tuned and graph-captured, as a sub-record (inputs drawn on
+    # the GPU: timing; its parity is the batched GPU tests').
+    batched = None
+    want_batched = args.batched == "on" or (args.batched == "auto" and world == 1 and not args.shape
+                                             and not args.device_inputs and precision == lad.LADDER_EMU_BF16)
+    if want_batched:
+        del R64
+        R64 = None
+        torch.cuda.empty_cache()
+        batched, _ = batched_record(args, lad, local, world, True, steps=3, warmup=3)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu, _, _ = cpu_baseline_sample(L, t2)
@@ -748,11 +785,111 @@ def run_single(args, cfg):
             "fp64": fp64,
             "speedup_vs_fp64": fp64["speedup_vs_fp64"] if fp64 else None,
             "accuracy": accuracy,
+            "batched": batched,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+# The paper's random-array contraction sweep (Table 3): N = nocc + nvir, nvec Cholesky vectors,
+# and its best C-split seconds per contraction (FP64 on Hopper, host transfers included) as context:
+# (N, nocc, nvec, nvir, GH200 CuPy, GH200 PyTorch, H100 CuPy, H100 PyTorch); None: not computed.
+TABLE3 = [
+    (800, 200, 8000, 600, 706.8, 1573.6, 1364.7, 1485.3),
+    (900, 225, 9000, 675, None, None, 2529.6, 3042.2),
+    (1000, 250, 10000, 750, None, None, 7759.1, 6233.1),
+    (800, 100, 4000, 700, 306.6, 355.9, 461.5, 330.5),
+    (900, 100, 4500, 800, 495.0, 587.1, 809.7, 496.2),
+    (1000, 100, 5000, 900, 829.1, 805.8, 1338.7, 827.1),
+    (1100, 100, 5500, 1000, 1282.7, 1401.7, 1860.9, 1223.4),
+    (1200, 100, 6000, 1100, None, None, 12329.8, 1864.7),
+    (1300, 100, 6500, 1200, None, None, 18426.4, 2679.1),
+    (800, 150, 4000, 650, 532.8, 475.3, 940.9, 651.2),
+    (900, 150, 4500, 750, 911.6, 1261.1, 1654.1, 1044.4),
+    (1000, 150, 5000, 850, 1489.2, 1924.4, 2945.2, 1739.7),
+    (1100, 150, 5500, 950, None, None, 4241.5, 3234.4),
+    (1000, 50, 10000, 950, 763.0, 574.6, 1006.4, 673.0),
+    (1200, 50, 12000, 1150, 2155.2, 1756.0, 2429.5, 2031.5),
+]
+
+
+def run_sweep(args):
+    """Table 3 shapes, emulated path, inputs drawn on the GPU, one timed call per shape after a
+    warm-up call on a small shape (calls of tens of seconds: launch costs are negligible).  A
+    shape is skipped, with the reason, when its inputs do not fit the device or no blocking fits
+    the workspace budget left beside them, or when the blocking needs more than 400 block pairs."""
+    import torch
+    import paper_2603_20912_gb300 as lad
+    from paper_2603_20912_gb300 import build
+    from ladder_inputs import make_device_inputs
+    torch.cuda.set_device(0)
+    build.build()
+    warm = lad.ladder_plan(20, 64, 300, lad.LADDER_EMU_BF16)
+    Lw, tw = make_device_inputs(20, 64, 300, 1)
+    lad.ladder_apply(warm, Lw, tw, torch.zeros_like(tw))
+    torch.cuda.synchronize()
+    warm.close()
+    del Lw, tw
+    total_mem = torch.cuda.get_device_properties(0).total_memory
+    for (N, no, nchol, nv, gh_cupy, gh_torch, h_cupy, h_torch) in TABLE3:
+        paper = {"GH200_CuPy_C-split_s": gh_cupy, "GH200_PyTorch_C-split_s": gh_torch,
+                 "H100_CuPy_C-split_s": h_cupy, "H100_PyTorch_C-split_s": h_torch}
+        rec = {"sweep": "Table 3", "N": N, "nocc": no, "nvir": nv, "nvec": nchol, "paper_seconds": paper}
+        inputs = 8.0 * (nchol * nv * nv + 2 * no * no * nv * nv)
+        torch.cuda.empty_cache()
+        if inputs > 0.8 * total_mem:
+            rec["skipped"] = f"L, t2 and R alone take {inputs / 1e9:.0f} GB of the {total_mem / 1e9:.0f} GB device"
+            print(json.dumps(rec), flush=True)
+            continue
+        plan = ws = Ld = td = R = None
+        try:
+            Ld, td = make_device_inputs(no, nv, nchol, 4242 + N + no, device="cuda:0")
+            R = torch.zeros_like(td)
+            torch.cuda.synchronize()
+            torch.cuda.empty_cache()
+            plan = lad.ladder_plan(no, nv, nchol, lad.LADDER_EMU_BF16)
+        except torch.cuda.OutOfMemoryError:
+            rec["skipped"] = f"drawing the inputs ({inputs / 1e9:.0f} GB) ran out of device memory"
+        except lad.LadderError as e:
+            rec["skipped"] = f"ladder_plan: {e} (L, t2 and R take {inputs / 1e9:.0f} GB)"
+        if "skipped" not in rec and plan.describe()["n_block_pairs"] > 400:
+            d = plan.describe()
+            rec["skipped"] = (f"the workspace left beside {inputs / 1e9:.0f} GB of inputs holds {d['max_pairs_per_block']} "
+                              f"pairs per block: {d['n_block_pairs']} block pairs, not timed")
+        if "skipped" in rec:
+            print(json.dumps(rec), flush=True)
+            del plan, Ld, td, R
+            continue
+        ws = plan.workspace()
+        desc = plan.describe()
+        plan.set_timing(True)
+        sampler = ClockSampler(0)
+        sampler.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        lad.ladder_apply(plan, Ld, td, R, ws)
+        e1.record()
+        torch.cuda.synchronize()
+        clocks = sampler.stop()
+        ms = e0.elapsed_time(e1)
+        kms, _ = kernel_times(lad, plan, 1)
+        assert plan.last_status() == lad.LADDER_OK
+        flops = lad.ladder_flops(no, nv, nchol)
+        unpacked = 2.0 * nv ** 4 * (nchol + no * no)
+        best_paper = min(x for x in (gh_cupy, gh_torch, h_cupy, h_torch) if x is not None)
+        rec.update({"seconds": ms * 1e-3, "tflops_packed": flops / (ms * 1e-3) / 1e12,
+                    "tflops_unpacked_count": unpacked / (ms * 1e-3) / 1e12,
+                    "form": "pm" if plan.form() == 1 else "plain", "n_a": desc["n_a"], "n_b": desc["n_b"],
+                    "block_pairs": desc["n_block_pairs"], "workspace_gb": plan.workspace_bytes() / 1e9,
+                    "kernel_s": {k: v * 1e-3 for k, v in kms.items()}, "clocks": clocks,
+                    "best_paper_over_ours": best_paper / (ms * 1e-3),
+                    "data": "synthetic, drawn on the GPU (torch generator), shapes of Table 3"})
+        print(json.dumps(rec), flush=True)
+        del ws, Ld, td, R
+        plan.close()
 
 
 def main():
@@ -775,16 +912,23 @@ def main():
     ap.add_argument("--fp64", default="auto", choices=["auto", "on", "off"],
                     help="also time the native FP64 path on the workload (auto: emulated runs on one GPU)")
     ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--batched", default="auto", choices=["auto", "on", "off"],
+                    help="also time the 24-instance uneven batch (auto: emulated default runs on one GPU)")
     ap.add_argument("--device-inputs", action="store_true",
                     help="draw L and t2 on the GPU (timing-only runs at large shapes)")
     ap.add_argument("--budget-gb", type=float, default=0.0, help="workspace budget (0: 0.9*0.98*free)")
     ap.add_argument("--fp64-reference", action="store_true",
                     help="c5: also time 24 sequential native-FP64 calls (slow)")
+    ap.add_argument("--sweep", default=None, choices=["table3"],
+                    help="time the paper's Table 3 shapes that fit one GB300 (one JSON line each)")
     ap.add_argument("--measure-peaks", action="store_true",
                     help="print torch/cuBLAS matmul throughput for fp64, bf16 and int8 and exit")
     args = ap.parse_args()
     if args.measure_peaks:
         measure_peaks()
+        return
+    if args.sweep:
+        run_sweep(args)
         return
     if args.config == "c5":
         run_batched(args)

@@ -305,13 +305,27 @@ int ladder_apply_batched(ladder_plan_t plan, const double* const* L, const doubl
  * ladder_tune_batched -- measured tuner of a batched plan: times
  * ladder_apply_batched under worker-stream schedules with 1, 2, 4, ... streams
  * and (emulated path) grouped schedules with the whole workspace, a half and a
- * quarter of it per group, on the given buffers, and keeps the fastest.  R[k]
+ * quarter of it per group (the batch splits), each with the one-SM ladder tile
+ * widths 96 and 64 (emulated path; ladder_plan_set_ladder_tile), on the given
+ * buffers, and keeps the fastest.  R[k]
  * is accumulated into by every trial (pass scratch R).  Synchronises the
  * stream.  *best_schedule (may be NULL) receives the chosen schedule: the
  * number of streams (> 0) or minus the number of groups (< 0).
  */
 int ladder_tune_batched(ladder_plan_t plan, const double* const* L, const double* const* t2,
                         double* const* R, void* ws, cudaStream_t stream, int* best_schedule);
+
+/*
+ * ladder_plan_set_ladder_tile -- column tile of the emulated ladder GEMM when it runs on one SM
+ * (no^2 <= 128 amplitude rows; the CTA-pair form keeps 96): bn pairs per tile, a multiple of 16
+ * in [16, 96] (96 is the widest the five TMEM accumulators leave room for: 5 x bn <= 512
+ * columns).  Narrower tiles make more, smaller units for instances with few pairs.
+ * The result does not depend on it (exact integer accumulation).  Applies to a batched plan's
+ * instances too; ladder_tune_batched measures 96 and 64 with every schedule and keeps the best.
+ * Returns LADDER_OK or LADDER_ERR_ARG.  ladder_plan_get_ladder_tile: the width, -1 for NULL.
+ */
+int ladder_plan_set_ladder_tile(ladder_plan_t plan, int bn);
+int ladder_plan_get_ladder_tile(ladder_plan_t plan);
 
 /*
  * Per-kernel timing for benchmarks.  ladder_plan_set_timing(plan, 1) creates a

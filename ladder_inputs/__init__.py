@@ -109,25 +109,37 @@ def make_inputs(no: int, nv: int, nchol: int, seed: int, symmetric_t2: bool = Tr
 def make_device_inputs(no: int, nv: int, nchol: int, seed: int, device="cuda"):
     """(L, t2) as torch float64 tensors drawn on the GPU with the same distributions and
     symmetries as ``make_inputs`` (torch's generator, so not the same numbers): for timing runs
-    at shapes whose host-side generation would take minutes.  Not used for parity."""
+    at shapes whose host-side generation would take minutes.  Not used for parity.  L is drawn
+    in chunks of Cholesky vectors and t2 symmetrised pair by pair in place, so the device holds
+    little more than L and t2 themselves while they are drawn."""
     import torch
     gen = torch.Generator(device=device)
     gen.manual_seed(seed)
     f64 = dict(dtype=torch.float64, device=device)
     eps_occ = torch.empty(no, **f64).uniform_(-1.5, -0.3, generator=gen)
     eps_vir = torch.empty(nv, **f64).uniform_(0.2, 3.0, generator=gen)
-    g = torch.randn((nchol, nv, nv), generator=gen, **f64)
-    L = torch.triu(g) + torch.triu(g, 1).transpose(1, 2)
-    del g
-    L *= torch.tensor(decay_factors(nchol), **f64)[:, None, None]
-    x = torch.randn((no, no, nv, nv), generator=gen, **f64)
-    x *= 0.01
-    t2 = (x + x.permute(1, 0, 3, 2)) / 2.0
-    del x
+    decay = torch.tensor(decay_factors(nchol), **f64)
+    L = torch.empty((nchol, nv, nv), **f64)
+    chunk = max(1, (1 << 27) // max(1, nv * nv))      # ~1 GB of draws at a time
+    for p0 in range(0, nchol, chunk):
+        p1 = min(nchol, p0 + chunk)
+        g = torch.randn((p1 - p0, nv, nv), generator=gen, **f64)
+        L[p0:p1] = torch.triu(g) + torch.triu(g, 1).transpose(1, 2)
+        L[p0:p1] *= decay[p0:p1, None, None]
+        del g
+    t2 = torch.empty((no, no, nv, nv), **f64)
+    for i in range(no):
+        t2[i].normal_(0.0, 0.01, generator=gen)
+    for i in range(no):                                # (X + X.transpose(1,0,3,2)) / 2, pair by pair
+        for j in range(i, no):
+            s = (t2[i, j] + t2[j, i].transpose(0, 1)) / 2.0
+            t2[i, j] = s
+            t2[j, i] = s.transpose(0, 1)
     eab = eps_vir[:, None] + eps_vir[None, :]
     eij = eps_occ[:, None] + eps_occ[None, :]
-    t2 /= (2.0 + eab)[None, None, :, :] - eij[:, :, None, None]
-    return L.contiguous(), t2.contiguous()
+    for i in range(no):
+        t2[i] /= (2.0 + eab)[None, :, :] - eij[i, :, None, None]
+    return L, t2
 
 
 def make_integer_inputs(no: int, nv: int, nchol: int, seed: int, lo: int = -3, hi: int = 3,

@@ -73,6 +73,10 @@ def _load():
     lib.ladder_plan_get_form.restype = ci
     lib.ladder_form_model.argtypes = [ci, ci, ci, ci]
     lib.ladder_form_model.restype = ci
+    lib.ladder_plan_set_ladder_tile.argtypes = [vp, ci]
+    lib.ladder_plan_set_ladder_tile.restype = ci
+    lib.ladder_plan_get_ladder_tile.argtypes = [vp]
+    lib.ladder_plan_get_ladder_tile.restype = ci
     lib.ladder_plan_set_path.argtypes = [vp, ci]
     lib.ladder_plan_set_path.restype = ci
     lib.ladder_plan_get_path.argtypes = [vp]
@@ -199,6 +203,17 @@ class Plan:
 
     def form(self) -> int:
         return int(_load().ladder_plan_get_form(self._h))
+
+    def ladder_tile(self) -> int:
+        return int(_load().ladder_plan_get_ladder_tile(self._h))
+
+    def set_ladder_tile(self, bn: int):
+        """Pairs per column tile of the one-SM emulated ladder (multiple of 16 in [16, 96])."""
+        _check(_load().ladder_plan_set_ladder_tile(self._h, int(bn)), "ladder_plan_set_ladder_tile")
+
+    def batched_choice(self) -> dict:
+        """The tile width a batched plan holds (after ladder_tune_batched: the tuner's choice)."""
+        return {"ladder_tile": self.ladder_tile()}
 
     def path(self) -> int:
         return int(_load().ladder_plan_get_path(self._h))
@@ -426,4 +441,5 @@ EXPORTED_SYMBOLS = [
     "ladder_watchdog_selftest", "ladder_batched_schedule", "ladder_plan_set_form", "ladder_plan_get_form",
     "ladder_form_model", "ladder_plan_set_wait_limit", "ladder_plan_get_wait_limit",
     "ladder_plan_shard_dry", "ladder_plan_set_path", "ladder_plan_get_path", "ladder_path_model",
+    "ladder_plan_set_ladder_tile", "ladder_plan_get_ladder_tile",
 ]

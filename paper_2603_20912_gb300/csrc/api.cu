@@ -1022,7 +1022,7 @@ int ladder_tune_batched(ladder_plan_t plan, const double* const* L, const double
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return LADDER_ERR_CUDA;
     // Candidates: worker-stream schedules with 1, 2, 4, ... streams, and (emulated path) grouped
     // schedules with the whole workspace, a half and a quarter of it per group.
-    struct Cand { int streams; size_t cap; };
+    struct Cand { int streams; size_t cap; int bn = ladder::kEmuTileN; };
     std::vector<Cand> cands;
     for (int k = 1; k < plan->max_streams; k *= 2) cands.push_back({k, 0});
     cands.push_back({plan->max_streams, 0});
@@ -1032,10 +1032,24 @@ int ladder_tune_batched(ladder_plan_t plan, const double* const* L, const double
         for (int d = 1; d <= 4; d *= 2)
             if (plan->ws.total / d >= biggest) cands.push_back({0, plan->ws.total / d});
     }
+    // Ladder column tile on one SM: 96 pairs (the widest that the five accumulators leave room
+    // for in TMEM) or 64 (more, smaller tiles for instances with few pairs).
+    const int widths[2] = {ladder::kEmuTileN, 64};
+    const int nwidths = plan->precision != LADDER_FP64 ? 2 : 1;
+    {
+        const std::vector<Cand> base = cands;
+        cands.clear();
+        for (int wi = 0; wi < nwidths; ++wi)
+            for (Cand c : base) {
+                c.bn = widths[wi];
+                cands.push_back(c);
+            }
+    }
     float best_ms = 1e30f;
     Cand best = cands[0];
     int rc = LADDER_OK;
     auto use = [&](const Cand& c) -> int {
+        ladder_plan_set_ladder_tile(plan, c.bn);
         if (c.streams > 0) {
             schedule_batched(*plan, c.streams);
             return LADDER_OK;
@@ -1067,6 +1081,15 @@ int ladder_tune_batched(ladder_plan_t plan, const double* const* L, const double
     if (best_schedule) *best_schedule = plan->sched_groups > 0 ? -plan->sched_groups : plan->nstreams;
     return rc;
 }
+
+int ladder_plan_set_ladder_tile(ladder_plan_t plan, int bn) {
+    if (!plan || bn < 16 || bn > ladder::kEmuTileN || bn % 16 != 0) return LADDER_ERR_ARG;
+    plan->lad_bn = bn;
+    for (auto* s : plan->sub) s->lad_bn = bn;
+    return LADDER_OK;
+}
+
+int ladder_plan_get_ladder_tile(ladder_plan_t plan) { return plan ? plan->lad_bn : -1; }
 
 int ladder_plan_set_wait_limit(ladder_plan_t plan, double seconds) {
     if (!plan || !(seconds >= 0.0) || seconds > 3600.0) return LADDER_ERR_ARG;

@@ -1570,18 +1570,22 @@ inline bool ladder_on_pairs(const ladder_plan_s& p) { return p.no * p.no > kEmuT
 
 // The ladder work item of one block pair of a plan whose workspace starts at ws; its units are
 // numbered from ubeg in the launch.
+// Column tile (pairs) of the ladder: 96 on CTA pairs (48 per CTA), the plan's width on one SM.
+inline int ladder_bn(const ladder_plan_s& p, bool pair) { return pair ? kEmuTileN : p.lad_bn; }
+
 template <int S>
 bool ladder_item(const ladder_plan_s& p, const BlockPair& bp, void* ws, long long ubeg, LadItem* it, CUtensorMap* ta,
                  CUtensorMap* tb) {
     constexpr int BK = bk_for(S);
     const bool pair = ladder_on_pairs(p);
+    const int bn = ladder_bn(p, pair);
     const int vp = padded_vp(p.nv);
     const int kpad = p.nv * vp, no2 = p.no * p.no;
     const size_t vplane = (size_t)p.max_pairs * kpad;
     if (!make_tmap(ta, at<char>(ws, p.ws.t_slices), kpad, no2, S, (uint64_t)kpad * 2, (uint64_t)no2 * kpad * 2, BK,
                    kEmuTile) ||
         !make_tmap(tb, at<char>(ws, p.ws.v_blk), kpad, bp.npairs, S, (uint64_t)kpad * 2, (uint64_t)vplane * 2, BK,
-                   pair ? kEmuTileN / 2 : kEmuTileN))
+                   pair ? kEmuTileN / 2 : bn))
         return false;
     LadItem x{};
     x.swap = 1;
@@ -1589,7 +1593,7 @@ bool ladder_item(const ladder_plan_s& p, const BlockPair& bp, void* ws, long lon
     x.M = no2;
     x.N = bp.npairs;
     x.n_mt = (x.M + (pair ? 2 : 1) * kEmuTile - 1) / ((pair ? 2 : 1) * kEmuTile);
-    x.n_nt = (x.N + kEmuTileN - 1) / kEmuTileN;
+    x.n_nt = (x.N + bn - 1) / bn;
     x.nkb = (kpad + BK - 1) / BK;
     x.kb_per_chunk = kEmuChunkK / BK;
     x.n_ch = (x.nkb + x.kb_per_chunk - 1) / x.kb_per_chunk;
@@ -1622,10 +1626,11 @@ bool ladder_item_pm(const ladder_plan_s& p, const BlockPair& bp, void* ws, long 
     const int rows = plus ? d.np : d.nm;
     const long long K = plus ? d.kp : d.km, kpad = plus ? d.kp_pad : d.km_pad;
     const bool pair = rows > kEmuTile;
+    const int bn = ladder_bn(p, pair);
     if (!make_tmap(ta, at<char>(ws, plus ? p.ws.tp_slices : p.ws.tm_slices), K, rows, S, (uint64_t)kpad * 2,
                    (uint64_t)rows * kpad * 2, BK, kEmuTile) ||
         !make_tmap(tb, at<char>(ws, plus ? p.ws.vp_blk : p.ws.vm_blk), K, bp.npairs, S, (uint64_t)kpad * 2,
-                   (uint64_t)p.max_pairs * kpad * 2, BK, pair ? kEmuTileN / 2 : kEmuTileN))
+                   (uint64_t)p.max_pairs * kpad * 2, BK, pair ? kEmuTileN / 2 : bn))
         return false;
     LadItem x{};
     x.swap = 1;
@@ -1633,7 +1638,7 @@ bool ladder_item_pm(const ladder_plan_s& p, const BlockPair& bp, void* ws, long 
     x.M = rows;
     x.N = bp.npairs;
     x.n_mt = (rows + (pair ? 2 : 1) * kEmuTile - 1) / ((pair ? 2 : 1) * kEmuTile);
-    x.n_nt = (x.N + kEmuTileN - 1) / kEmuTileN;
+    x.n_nt = (x.N + bn - 1) / bn;
     x.nkb = (int)((K + BK - 1) / BK);
     x.kb_per_chunk = kEmuChunkK / BK;
     x.n_ch = (x.nkb + x.kb_per_chunk - 1) / x.kb_per_chunk;
@@ -1684,12 +1689,11 @@ cudaError_t block_pm_impl(const ladder_plan_s& p, const BlockPair& bp, double* R
     for (int part = 0; part < (has_y ? 2 : 1); ++part) {
         LadBatch lb{};
         lb.nitems = 1;
-        lb.BN = kEmuTileN;
         lb.status = p.d_status;
-    lb.wait_ns = p.wait_ns;
         lb.wait_ns = p.wait_ns;
         if (!ladder_item_pm<S>(p, bp, ws, 0, part == 0, &lb.item[0], &lb.ta[0], &lb.tb[0]))
             return cudaErrorInvalidValue;
+        lb.BN = ladder_bn(p, lb.item[0].M > kEmuTile);
         lb.units = lb.item[0].units;
         LaunchTimer tm(p, s, LADDER_KERNEL_LADDER);
         launch_ladder_batch<S>(lb, lb.item[0].M > kEmuTile, fit, p.num_sms, s);
@@ -1734,7 +1738,7 @@ cudaError_t block_impl(const ladder_plan_s& p, const BlockPair& bp, double* R, v
     // o^2 <= 128 in one 128-row tile (one SM per tile); larger o^2 in 256-row tiles on CTA pairs.
     LadBatch lb{};
     lb.nitems = 1;
-    lb.BN = kEmuTileN;
+    lb.BN = ladder_bn(p, ladder_on_pairs(p));
     lb.status = p.d_status;
     lb.wait_ns = p.wait_ns;
     if (!ladder_item<S>(p, bp, ws, 0, &lb.item[0], &lb.ta[0], &lb.tb[0])) return cudaErrorInvalidValue;
@@ -1796,7 +1800,7 @@ cudaError_t group_impl(const ladder_plan_s& parent, const ladder_plan_s* const* 
     for (int shape = 0; shape < 2; ++shape) {   // 0: single CTAs, 1: CTA pairs
         static thread_local LadBatch lb;
         lb = LadBatch{};
-        lb.BN = kEmuTileN;
+        lb.BN = shape == 1 ? kEmuTileN : parent.lad_bn;   // every single-CTA item of the group uses it
         lb.status = parent.d_status;
         lb.wait_ns = parent.wait_ns;
         long long units = 0;

@@ -129,6 +129,7 @@ struct ladder_plan_s {
     size_t budget = 0;
     int n_a = 0, n_b = 0;
     int form = 0;  // emulated ladder form: 0 = plain (K = (c,d)), 1 = symmetric/antisymmetric
+    int lad_bn = ladder::kEmuTileN;  // emulated ladder on one SM: pairs per column tile (16..96)
     int path = 0;     // 0: rebuild (ac|bd) per block pair; 1: factorised sum_P L_P T_ij L_P^T (FP64)
     int fact_pb = 0;  // factorised path: Cholesky vectors per batch
     int shard_rank = 0, shard_world = 1;  // this plan holds shard `shard_rank` of `shard_world`

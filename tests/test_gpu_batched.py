@@ -63,6 +63,7 @@ def test_tuner_picks_a_schedule_and_results_stay_exact():
     scratch = [torch.zeros_like(t) for t in ts]
     k = lad.ladder_tune_batched(plan, Ls, ts, scratch, ws)
     assert k in (1, 2, 4, 6) or k < 0   # streams, or minus the number of groups
+    assert plan.batched_choice()["ladder_tile"] in (96, 64)
     Rs = [torch.zeros_like(t) for t in ts]
     lad.ladder_apply_batched(plan, Ls, ts, Rs, ws)
     torch.cuda.synchronize()
@@ -141,4 +142,51 @@ def test_every_schedule_gives_the_same_bits(schedule):
     torch.cuda.synchronize()
     assert plan.last_status() == lad.LADDER_OK
     for R, R1 in zip(Rs, ref):
+        assert torch.equal(R, R1)
+
+
+@pytest.mark.parametrize("bn", [16, 48, 64, 80])
+def test_ladder_tile_width_does_not_change_a_bit(bn):
+    # one-SM ladder (no^2 <= 128) in both forms: exact integer sums, any column tile width
+    for (o, v, x), form in (((7, 61, 90), 0), ((10, 47, 70), 1)):
+        L, t2, _, _ = make_inputs(o, v, x, seed=bn + v)
+        Ld, td = torch.from_numpy(L).cuda(), torch.from_numpy(t2).cuda()
+        out = []
+        for width in (96, bn):
+            plan = lad.ladder_plan(o, v, x, EMU)
+            plan.set_form(form)
+            plan.set_ladder_tile(width)
+            assert plan.ladder_tile() == width
+            R = torch.zeros_like(td)
+            lad.ladder_apply(plan, Ld, td, R)
+            torch.cuda.synchronize()
+            assert plan.last_status() == lad.LADDER_OK
+            out.append(R)
+        assert torch.equal(out[0], out[1])
+        assert rel_fro(out[1].cpu().numpy(), oracle.ladder(L, t2)) <= 1e-10
+    plan = lad.ladder_plan(3, 20, 30, EMU)
+    for bad in (0, 8, 40, 112):
+        with pytest.raises(lad.LadderError):
+            plan.set_ladder_tile(bad)
+
+
+def test_tuned_choice_is_bit_identical_to_single_plans():
+    # the tuner varies schedule, batch split and ladder tile width; whatever it keeps, every
+    # instance's R equals its single-plan R bit for bit
+    shapes = SMALL + [(12, 40, 60), (2, 88, 50)]
+    host, Ls, ts = _make(shapes, seed0=950)
+    plan = lad.ladder_plan_batched([s[0] for s in shapes], [s[1] for s in shapes], [s[2] for s in shapes], EMU)
+    ws = plan.workspace()
+    scratch = [torch.zeros_like(t) for t in ts]
+    lad.ladder_tune_batched(plan, Ls, ts, scratch, ws)
+    assert plan.batched_choice()["ladder_tile"] in (96, 64)
+    Rs = [torch.zeros_like(t) for t in ts]
+    lad.ladder_apply_batched(plan, Ls, ts, Rs, ws)
+    torch.cuda.synchronize()
+    assert plan.last_status() == lad.LADDER_OK
+    for (o, v, x), L, t, R in zip(shapes, Ls, ts, Rs):
+        single = lad.ladder_plan(o, v, x, EMU)
+        R1 = torch.zeros_like(t)
+        lad.ladder_apply(single, L, t, R1)
+        torch.cuda.synchronize()
         assert torch.equal(R, R1)
