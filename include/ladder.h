@@ -316,6 +316,25 @@ int ladder_tune_batched(ladder_plan_t plan, const double* const* L, const double
                         double* const* R, void* ws, cudaStream_t stream, int* best_schedule);
 
 /*
+ * ladder_plan_set_eri_chunk -- longest exact K chunk of the emulated ERI, in blocks of 1024
+ * Cholesky vectors (1..4, default 4).  Each chunk ends with a drain of the tensor-memory
+ * accumulators into int64 registers that the next chunk's MMAs wait for.  With |digit| <= 64 a
+ * chunk of 1024 keeps every exact level sum an FP32 integer for any data; longer chunks are taken,
+ * per call and on the device, only when a bound from the operands' own digits proves the same:
+ * by Cauchy-Schwarz each level-l sum over a chunk is at most sum_{s+t=l-2} M_s M_t, M_s the
+ * largest 2-norm of slice s's digits over any L^T row within one chunk-aligned window, and the
+ * longest window (up to the limit) whose bounds stay within (l-1) 2^22 for l = 2..5 is used.  The
+ * result does not depend on the chunk (exact integer sums).  blocks = 1 keeps 1024.  Applies to a
+ * batched plan's instances too.  Returns LADDER_OK or LADDER_ERR_ARG.
+ *
+ * ladder_plan_eri_chunk -- the chunk length (Cholesky vectors) the last ladder_apply of an emulated
+ * plan with workspace `ws` chose; synchronises `stream` to read it.  -1 for a NULL, batched, FP64
+ * or factorised plan or a failed read.
+ */
+int ladder_plan_set_eri_chunk(ladder_plan_t plan, int blocks);
+int ladder_plan_eri_chunk(ladder_plan_t plan, const void* ws, cudaStream_t stream);
+
+/*
  * ladder_plan_set_ladder_tile -- column tile of the emulated ladder GEMM when it runs on one SM
  * (no^2 <= 128 amplitude rows; the CTA-pair form keeps 96): bn pairs per tile, a multiple of 16
  * in [16, 96] (96 is the widest the five TMEM accumulators leave room for: 5 x bn <= 512

@@ -73,6 +73,10 @@ def _load():
     lib.ladder_plan_get_form.restype = ci
     lib.ladder_form_model.argtypes = [ci, ci, ci, ci]
     lib.ladder_form_model.restype = ci
+    lib.ladder_plan_set_eri_chunk.argtypes = [vp, ci]
+    lib.ladder_plan_set_eri_chunk.restype = ci
+    lib.ladder_plan_eri_chunk.argtypes = [vp, vp, vp]
+    lib.ladder_plan_eri_chunk.restype = ci
     lib.ladder_plan_set_ladder_tile.argtypes = [vp, ci]
     lib.ladder_plan_set_ladder_tile.restype = ci
     lib.ladder_plan_get_ladder_tile.argtypes = [vp]
@@ -203,6 +207,14 @@ class Plan:
 
     def form(self) -> int:
         return int(_load().ladder_plan_get_form(self._h))
+
+    def set_eri_chunk(self, blocks: int):
+        """Longest exact K chunk of the emulated ERI in blocks of 1024 (1..4); see ladder_plan_set_eri_chunk."""
+        _check(_load().ladder_plan_set_eri_chunk(self._h, int(blocks)), "ladder_plan_set_eri_chunk")
+
+    def eri_chunk(self, ws, stream=None) -> int:
+        """Chunk length (Cholesky vectors) the last ladder_apply with this workspace chose."""
+        return int(_load().ladder_plan_eri_chunk(self._h, ctypes.c_void_p(ws.data_ptr()), _stream_handle(stream)))
 
     def ladder_tile(self) -> int:
         return int(_load().ladder_plan_get_ladder_tile(self._h))
@@ -441,5 +453,6 @@ EXPORTED_SYMBOLS = [
     "ladder_watchdog_selftest", "ladder_batched_schedule", "ladder_plan_set_form", "ladder_plan_get_form",
     "ladder_form_model", "ladder_plan_set_wait_limit", "ladder_plan_get_wait_limit",
     "ladder_plan_shard_dry", "ladder_plan_set_path", "ladder_plan_get_path", "ladder_path_model",
-    "ladder_plan_set_ladder_tile", "ladder_plan_get_ladder_tile",
+    "ladder_plan_set_ladder_tile", "ladder_plan_get_ladder_tile", "ladder_plan_set_eri_chunk",
+    "ladder_plan_eri_chunk",
 ]

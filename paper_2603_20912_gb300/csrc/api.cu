@@ -142,6 +142,10 @@ ladder::WsLayout layout_for(const ladder_plan_s& p, long long max_pairs) {
         w.v_exp = take(nv2 * 4);
         w.lnorm = take((size_t)p.nv * 8);
         w.lsq = take(nv2 * 8);
+        const size_t nblk = (xpad + ladder::kEmuChunkK - 1) / ladder::kEmuChunkK;
+        w.lt_norm2 = take(S * nvp * nblk * 4);
+        w.eri_cand = take(S * 3 * 4);
+        w.eri_kbc = take(4);
     }
     w.total = std::max<size_t>(off, kAlign);
     return w;
@@ -1080,6 +1084,24 @@ int ladder_tune_batched(ladder_plan_t plan, const double* const* L, const double
     if (rc == LADDER_OK) rc = rc2;
     if (best_schedule) *best_schedule = plan->sched_groups > 0 ? -plan->sched_groups : plan->nstreams;
     return rc;
+}
+
+int ladder_plan_set_eri_chunk(ladder_plan_t plan, int blocks) {
+    if (!plan || blocks < 1 || blocks > 4) return LADDER_ERR_ARG;
+    plan->eri_chunk_max = blocks;
+    for (auto* s : plan->sub) s->eri_chunk_max = blocks;
+    return LADDER_OK;
+}
+
+int ladder_plan_eri_chunk(ladder_plan_t plan, const void* ws, cudaStream_t stream) {
+    if (!plan || plan->batched || !ws || plan->precision == LADDER_FP64 || plan->path != 0) return -1;
+    DeviceGuard guard(plan->device);
+    int kbc = 0;
+    if (cudaMemcpyAsync(&kbc, static_cast<const char*>(ws) + plan->ws.eri_kbc, sizeof(int), cudaMemcpyDeviceToHost,
+                        stream) != cudaSuccess ||
+        cudaStreamSynchronize(stream) != cudaSuccess)
+        return -1;
+    return kbc * ladder::emu_eri_stage_k(plan->nslices);
 }
 
 int ladder_plan_set_ladder_tile(ladder_plan_t plan, int bn) {

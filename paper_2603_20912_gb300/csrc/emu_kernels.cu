@@ -287,7 +287,8 @@ __global__ void f_table_kernel(const unsigned long long* __restrict__ lnorm_bits
 template <int S>
 __global__ void __launch_bounds__(256) lt_slice_kernel(const double* __restrict__ L, int nchol, int nv, int vp,
                                                        int xpad, const int* __restrict__ lt_exp,
-                                                       __nv_bfloat16* __restrict__ planes, unsigned* status) {
+                                                       __nv_bfloat16* __restrict__ planes,
+                                                       unsigned* __restrict__ norm2, int nblk, unsigned* status) {
     __shared__ double tile[64][65];
     const long long nv2 = (long long)nv * nv, rows = (long long)nv * vp;
     const int P0 = blockIdx.x * 64;
@@ -303,19 +304,39 @@ __global__ void __launch_bounds__(256) lt_slice_kernel(const double* __restrict_
     __syncthreads();
     const int rr = threadIdx.x >> 2, pseg = (threadIdx.x & 3) * 16;
     const long long r = r0 + rr;
-    if (r >= rows) return;
-    const int e = lt_exp[r0 / kG];
+    const int e = r < rows ? lt_exp[r0 / kG] : 0;
     const size_t plane = (size_t)rows * xpad;
     const int P0t = P0 + pseg;
-    if (P0t >= nchol) return;
     __align__(16) __nv_bfloat16 out[S][16];
+    unsigned sq[S];
+#pragma unroll
+    for (int s2 = 0; s2 < S; ++s2) sq[s2] = 0;
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
         __nv_bfloat16 d[S];
         digits_of<S>(scaled_rint(tile[pseg + k][rr], 7 * S - e), d);
 #pragma unroll
-        for (int s2 = 0; s2 < S; ++s2) out[s2][k] = d[s2];
+        for (int s2 = 0; s2 < S; ++s2) {
+            out[s2][k] = d[s2];
+            const int di = __float2int_rn(__bfloat162float(d[s2]) * pow2f(7 * (s2 + 1)));   // the digit
+            sq[s2] += (unsigned)(di * di);
+        }
     }
+    // Squared digit norms of this row over the block's 64 P (the four threads of a row are
+    // adjacent lanes), added into the row's 1024-wide block of K: the exact-chunk bound.
+#pragma unroll
+    for (int s2 = 0; s2 < S; ++s2) {
+        sq[s2] += __shfl_xor_sync(0xffffffffu, sq[s2], 1);
+        sq[s2] += __shfl_xor_sync(0xffffffffu, sq[s2], 2);
+    }
+    if (r >= rows) return;
+    if ((threadIdx.x & 3) == 0) {
+        const int blk = P0 / kEmuChunkK;
+#pragma unroll
+        for (int s2 = 0; s2 < S; ++s2)
+            if (sq[s2] != 0) atomicAdd(norm2 + ((size_t)s2 * rows + r) * nblk + blk, sq[s2]);
+    }
+    if (P0t >= nchol) return;
     if (P0t + 16 <= xpad) {
         // 16 consecutive P of one row: two 16-byte stores per plane (xpad % 8 == 0, P0t % 16 == 0)
 #pragma unroll
@@ -332,6 +353,59 @@ __global__ void __launch_bounds__(256) lt_slice_kernel(const double* __restrict_
                 if (LADDER_IN_BOUNDS((size_t)r * xpad + P0t + k < plane, status))
                     planes[s2 * plane + (size_t)r * xpad + P0t + k] = out[s2][k];
     }
+}
+
+// Exact chunk length of the ERI (K = nchol) from the digit norms.  A level-l accumulator sums, over
+// the chunk, the products d_s d_t (s + t = l - 2, 0-based planes) of a row and a column of L^T; by
+// Cauchy-Schwarz every partial sum of it is at most sum_{s+t} |d_s| |d_t| <= sum_{s+t} M_s M_t,
+// where M_s is the largest 2-norm over rows of plane s's digits in one chunk-aligned window of K.
+// Chunks of 1024 meet the limits (l - 1) 2^22 of levels 2..5 for any digits (|d| <= 64); a window
+// of c blocks of 1024 (c = 2, 3, 4) is taken when its norms meet the same limits, so that every level
+// sum stays an exact FP32 integer and the 32-bit pairings of the epilogue cannot overflow.
+// cand[(c-2) S + s] = max over rows and aligned windows of c blocks of the squared norm of plane s.
+constexpr int kEriMaxChunkBlocks = 4;
+
+__global__ void __launch_bounds__(256) eri_chunk_norms_kernel(const unsigned* __restrict__ norm2, long long rows,
+                                                              int S, int nblk, unsigned* __restrict__ cand) {
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int s2 = 0; s2 < S; ++s2) {
+        unsigned best[kEriMaxChunkBlocks - 1] = {0, 0, 0};
+        if (r < rows) {
+            const unsigned* row = norm2 + ((size_t)s2 * rows + r) * nblk;
+            for (int c = 2; c <= kEriMaxChunkBlocks; ++c)
+                for (int w0 = 0; w0 < nblk; w0 += c) {
+                    unsigned sum = 0;
+                    for (int b = w0; b < w0 + c && b < nblk; ++b) sum += row[b];
+                    best[c - 2] = max(best[c - 2], sum);
+                }
+        }
+        for (int c = 0; c < kEriMaxChunkBlocks - 1; ++c) {
+            unsigned v = best[c];
+            for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+            if ((threadIdx.x & 31) == 0 && v != 0) atomicMax(cand + c * S + s2, v);
+        }
+    }
+}
+
+// One thread: the largest window (in blocks of 1024, at most max_blocks) that meets the limits,
+// as K blocks of the ERI's stage width per chunk.
+__global__ void eri_chunk_select_kernel(const unsigned* __restrict__ cand, int S, int max_blocks, int bk,
+                                        int* __restrict__ kb_per_chunk) {
+    int chosen = 1;
+    for (int c = min(max_blocks, kEriMaxChunkBlocks); c >= 2 && chosen == 1; --c) {
+        bool ok = true;
+        for (int j = 0; j < 4 && ok; ++j) {   // accumulator j: level j + 2, planes s + t = j
+            double bound = 0.0;
+            for (int s2 = 0; s2 <= j && s2 < S; ++s2) {
+                const int t = j - s2;
+                if (t >= S) continue;
+                bound += sqrt((double)cand[(c - 2) * S + s2]) * sqrt((double)cand[(c - 2) * S + t]);
+            }
+            ok = bound * (1.0 + 1e-9) + 1.0 <= (double)(j + 1) * 4194304.0;   // (l - 1) 2^22
+        }
+        if (ok) chosen = c;
+    }
+    *kb_per_chunk = chosen * kEmuChunkK / bk;
 }
 
 // max |T| per group of 64 T rows, via atomic max on the IEEE bits (T viewed [no^2][nv^2]).
@@ -732,6 +806,7 @@ struct EriItem {
     const int* f_tab;
     __nv_bfloat16* vplanes;
     long long* vint;      // non-null: V as int64 N (row stride kpad) instead of digit planes
+    const int* kbc;       // K blocks (of the stage width) per exact chunk, chosen on the device
 };
 
 struct EriBatch {
@@ -791,7 +866,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsEri, 1)
     cluster_sync();
     tc_fence_after();
     const uint32_t tmem = tmem_base;
-    const int kb_per_chunk = kEmuChunkK / BK;
     bool failed = false;
 
     if (warp == 0 && lane == 0) {
@@ -829,7 +903,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsEri, 1)
         bool ok = true;
         int it = 0;
         for (int e = cluster; e < B.nentries && ok; e += nclusters) {
-            const int nkb = (B.item[B.entries[e].z].nchol + BK - 1) / BK;
+            const EriItem& p = B.item[B.entries[e].z];
+            const int nkb = (p.nchol + BK - 1) / BK;
+            const int kb_per_chunk = *p.kbc;
             const int nch = (nkb + kb_per_chunk - 1) / kb_per_chunk;
             for (int ch = 0; ch < nch && ok; ++ch, ++it) {
                 if (!(ok = mbar_wait(&acc_empty, (uint32_t)(it & 1) ^ 1u, B.status, kStatusTimeout, B.wait_ns))) break;
@@ -868,6 +944,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsEri, 1)
             const int Ncols = p.nb * p.vp;
             const bool few_tables = p.vp >= 8 * kEriRuns;
             const int nkb = (p.nchol + BK - 1) / BK;
+            const int kb_per_chunk = *p.kbc;
             const int nch = (nkb + kb_per_chunk - 1) / kb_per_chunk;
             const int qt = en.y;
             // this thread's tile row: chunk (first L^T row, rows) and the row (x, y) in it
@@ -1477,7 +1554,10 @@ cudaError_t prep_impl(const ladder_plan_s& p, const double* L, const double* t2,
     const int xpad = (int)align_up((size_t)p.nchol, 8);
     const int kpad = (int)rows;
     const int ngt = (no2 + kG - 1) / kG;
-    LaunchTimer tm(p, s, LADDER_KERNEL_PREP, 6);
+    // kernels: L^T statistics, pair exponents, L^T slices, chunk norms and choice, then the T side
+    // (row maxima, exponents, slices; the split form has two exponent passes when rows i < j exist)
+    const int t_kernels = p.form == 0 ? 3 : (p.no > 1 ? 4 : 3);
+    LaunchTimer tm(p, s, LADDER_KERNEL_PREP, 5 + t_kernels);
     cudaError_t e;
     if ((e = cudaMemsetAsync(at<char>(ws, p.ws.lnorm), 0, (size_t)p.nv * 8, s)) != cudaSuccess) return e;
     if (p.form == 0 && (e = cudaMemsetAsync(at<char>(ws, p.ws.t_gmax), 0, (size_t)ngt * 8, s)) != cudaSuccess)
@@ -1487,8 +1567,16 @@ cudaError_t prep_impl(const ladder_plan_s& p, const double* L, const double* t2,
                                                                         at<double>(ws, p.ws.lsq));
     f_table_kernel<<<(unsigned)((nv2 + 255) / 256), 256, 0, s>>>(at<unsigned long long>(ws, p.ws.lnorm), p.nv,
                                                                    at<int>(ws, p.ws.v_exp));
+    const int nblk = (xpad + kEmuChunkK - 1) / kEmuChunkK;
+    if ((e = cudaMemsetAsync(at<char>(ws, p.ws.lt_norm2), 0, (size_t)S * rows * nblk * 4, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(at<char>(ws, p.ws.eri_cand), 0, (size_t)S * 3 * 4, s)) != cudaSuccess) return e;
     lt_slice_kernel<S><<<dim3((p.nchol + 63) / 64, (unsigned)((rows + 63) / 64)), 256, 0, s>>>(
-        L, p.nchol, p.nv, vp, xpad, at<int>(ws, p.ws.lt_exp), at<__nv_bfloat16>(ws, p.ws.lt_slices), p.d_status);
+        L, p.nchol, p.nv, vp, xpad, at<int>(ws, p.ws.lt_exp), at<__nv_bfloat16>(ws, p.ws.lt_slices),
+        at<unsigned>(ws, p.ws.lt_norm2), nblk, p.d_status);
+    eri_chunk_norms_kernel<<<(unsigned)((rows + 255) / 256), 256, 0, s>>>(at<unsigned>(ws, p.ws.lt_norm2), rows, S,
+                                                                         nblk, at<unsigned>(ws, p.ws.eri_cand));
+    eri_chunk_select_kernel<<<1, 1, 0, s>>>(at<unsigned>(ws, p.ws.eri_cand), S, p.eri_chunk_max, eri_bk_for(S),
+                                            at<int>(ws, p.ws.eri_kbc));
     if (p.form == 0) {
         t_rowmax_kernel<<<dim3((unsigned)((nv2 + 8191) / 8192), no2), 256, 0, s>>>(
             t2, nv2, no2, at<unsigned long long>(ws, p.ws.t_gmax));
@@ -1536,7 +1624,8 @@ bool eri_item(const ladder_plan_s& p, const BlockPair& bp, void* ws, EriItem* it
     const int2* chunks = reinterpret_cast<const int2*>(p.d_tables) + bp.chunks_off;
     *it = EriItem{p.nv, vp, p.nchol, bp.a0, bp.a1 - bp.a0, bp.b0, bp.b1 - bp.b0, (int)rows,
                   (size_t)p.max_pairs * (size_t)rows, chunks, row_start, at<int>(ws, p.ws.lt_exp), at<int>(ws, p.ws.v_exp),
-                  at<__nv_bfloat16>(ws, p.ws.v_blk), p.form == 1 ? at<long long>(ws, p.ws.v_blk) : nullptr};
+                  at<__nv_bfloat16>(ws, p.ws.v_blk), p.form == 1 ? at<long long>(ws, p.ws.v_blk) : nullptr,
+                  at<int>(ws, p.ws.eri_kbc)};
     return true;
 }
 
@@ -1913,6 +2002,8 @@ cudaError_t launch_emu_group(const ladder_plan_s& parent, const ladder_plan_s* c
 }
 
 int emu_max_group() { return kMaxItems; }
+
+int emu_eri_stage_k(int nslices) { return eri_bk_for(nslices); }
 
 cudaError_t launch_emu_block(const ladder_plan_s& p, const BlockPair& bp, double* R, void* ws, cudaStream_t s) {
     switch (p.nslices) {

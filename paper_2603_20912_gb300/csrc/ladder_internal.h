@@ -64,6 +64,9 @@ struct WsLayout {
     size_t v_exp = 0;      // EMU: exponent bound per (a, b) pair [nv][nv] (int)
     size_t lnorm = 0;      // EMU: max_c ||L[:, a, c]||_2 per a (IEEE bits, u64)
     size_t lsq = 0;        // EMU: ||L[:, a, c]||_2^2 per (a, c) [nv][nv] (f64)
+    size_t lt_norm2 = 0;   // EMU: squared digit norms of L^T [S][nv*vp][nblk] (u32), 1024-wide blocks of K
+    size_t eri_cand = 0;   // EMU: largest windowed squared norms per (window length, plane) (u32)
+    size_t eri_kbc = 0;    // EMU: K blocks per exact ERI chunk, chosen on the device (int)
     // EMU, symmetric/antisymmetric ladder form (instead of t_slices, t_gmax, t_exp, rp_int):
     size_t vp_blk = 0;     // V' planes [S][max_pairs][kp] bf16, K' = (c <= d) packed
     size_t vm_blk = 0;     // V'' planes [S][max_pairs][km] bf16, K'' = (c < d) packed
@@ -130,6 +133,7 @@ struct ladder_plan_s {
     int n_a = 0, n_b = 0;
     int form = 0;  // emulated ladder form: 0 = plain (K = (c,d)), 1 = symmetric/antisymmetric
     int lad_bn = ladder::kEmuTileN;  // emulated ladder on one SM: pairs per column tile (16..96)
+    int eri_chunk_max = 4;           // emulated ERI: longest exact K chunk, in blocks of 1024 (1..4)
     int path = 0;     // 0: rebuild (ac|bd) per block pair; 1: factorised sum_P L_P T_ij L_P^T (FP64)
     int fact_pb = 0;  // factorised path: Cholesky vectors per batch
     int shard_rank = 0, shard_world = 1;  // this plan holds shard `shard_rank` of `shard_world`
@@ -215,6 +219,7 @@ cudaError_t launch_emu_group(const ladder_plan_s& parent, const ladder_plan_s* c
                              const double* const* L, const double* const* t2, double* const* R, const int4* entries,
                              int nentries, cudaStream_t s);
 int emu_max_group();  // most instances in one group
+int emu_eri_stage_k(int nslices);  // K columns per pipeline stage of the emulated ERI
 bool emu_supported(int no, int nv, int nchol, int nslices);
 cudaError_t emu_set_attributes(int nslices);  // per device, before the first launch
 // Co-resident clusters of the emulated CTA-pair kernels on the current device: kind 0 = ERI,

@@ -186,3 +186,54 @@ def test_c3_planner_split_is_bitwise_identical():
     d = planb.describe()
     assert d["n_block_pairs"] > 1 and planb.workspace_bytes() <= budget
     assert np.array_equal(Rb, R1)
+
+
+def _emu_run(L, t2, chunk_blocks=None, form=None):
+    nchol, nv, _ = L.shape
+    no = t2.shape[0]
+    torch.cuda.empty_cache()
+    plan = lad.ladder_plan(no, nv, nchol, EMU)
+    if form is not None:
+        plan.set_form(form)
+    if chunk_blocks is not None:
+        plan.set_eri_chunk(chunk_blocks)
+    ws = plan.workspace()
+    R = torch.zeros(t2.shape, dtype=torch.float64, device="cuda")
+    lad.ladder_apply(plan, dev(L), dev(t2), R, ws)
+    torch.cuda.synchronize()
+    assert plan.last_status() == lad.LADDER_OK
+    return R.cpu().numpy(), plan.eri_chunk(ws)
+
+
+@pytest.mark.parametrize("form", [0, 1])
+def test_exact_chunk_from_digit_norms_is_bit_identical(form):
+    # nchol = 1500 spans two blocks of 1024: the digit-norm bound admits one chunk for the whole
+    # K; forcing chunks of 1024 gives the same bits (every level sum is exact either way)
+    L, t2, _, _ = make_inputs(4, 40, 1500, seed=61)
+    R_long, chunk = _emu_run(L, t2, form=form)
+    assert chunk >= 1500
+    R_1024, chunk1 = _emu_run(L, t2, chunk_blocks=1, form=form)
+    assert chunk1 == 1024
+    assert np.array_equal(R_long, R_1024)
+    assert rel_fro(R_long, oracle.ladder(L, t2)) <= TOL_R
+
+
+def test_worst_case_digits_keep_chunks_of_1024():
+    # L = 3 everywhere: the top digit of every entry is 48, so two blocks of 1024 would reach
+    # 48^2 * 2048 > 2^22 at level 2: the bound must refuse the longer chunk; integer inputs make
+    # the result exact, so it must equal the oracle bit for bit
+    no, nv, nchol = 2, 9, 2100
+    L = np.full((nchol, nv, nv), 3.0)
+    rng = np.random.default_rng(9)
+    x = rng.integers(-3, 4, size=(no, no, nv, nv)).astype(np.float64)
+    t2 = np.ascontiguousarray(x + x.transpose(1, 0, 3, 2))
+    R, chunk = _emu_run(L, t2)
+    assert chunk == 1024
+    assert np.array_equal(R, oracle.ladder(L, t2))
+
+
+def test_eri_chunk_rejects_bad_limits():
+    plan = lad.ladder_plan(3, 20, 30, EMU)
+    for bad in (0, 5, -1):
+        with pytest.raises(lad.LadderError):
+            plan.set_eri_chunk(bad)
