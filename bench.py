@@ -706,9 +706,23 @@ def run_single(args, cfg):
         e1.record(stream)
         torch.cuda.synchronize()
         ms_e2e = max_over_ranks(e0.elapsed_time(e1), world)
+        # the copies alone, one step's worth, on the same stream (context for the difference)
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        c2 = torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        Ld.copy_(Lh, non_blocking=True)
+        td.copy_(th, non_blocking=True)
+        c1.record(stream)
+        Rh.copy_(R, non_blocking=True)
+        c2.record(stream)
+        torch.cuda.synchronize()
+        h2d_ms, d2h_ms = c0.elapsed_time(c1), c1.elapsed_time(c2)
         e2e = {"value": (1 if shard else world) * flops * args.steps / (ms_e2e * 1e-3) / 1e12, "unit": "TFLOP/s",
                "ms_per_step": ms_e2e / args.steps,
-               "h2d_bytes_per_step": int(L.nbytes + t2.nbytes), "d2h_bytes_per_step": int(t2.nbytes)}
+               "h2d_bytes_per_step": int(L.nbytes + t2.nbytes), "d2h_bytes_per_step": int(t2.nbytes),
+               "copies_alone_ms": {"h2d": h2d_ms, "d2h": d2h_ms},
+               "host_buffers_pinned": bool(Lh.is_pinned() and th.is_pinned() and Rh.is_pinned())}
     elif L is not None:
         R.zero_()
         lad.ladder_apply(plan, Ld, td, R, ws)
