@@ -20,10 +20,10 @@ workload (``speedup_vs_fp64`` = its ms/call over the emulated one) and
 ``accuracy`` states both results' error against the CPU oracle: sampled
 (a, b) pairs against the oracle's pair mode, E_L against the stored oracle
 value, and the whole R of one path against the other.  Multi-GPU runs
-(torchrun): ``--mode replicas`` (default) gives each rank its own independent
-instance (weak scaling, no collective on the data path); ``--mode shard``
-splits one contraction's block pairs over the ranks (ladder_plan_shard) and
-sums E_L with one scalar all-reduce (strong scaling).
+(torchrun): ``--mode shard`` (default) splits one contraction's block pairs
+over the ranks (ladder_plan_shard) and sums E_L with one scalar all-reduce
+(strong scaling); ``--mode replicas`` gives each rank its own independent
+instance (weak scaling, no collective on the data path).
 """
 from __future__ import annotations
 
@@ -383,12 +383,14 @@ def batched_record(args, lad, local, world, device_inputs, steps, warmup, fp64_s
     peak_key = "bf16_tflops_sustained" if ms_total >= 1000.0 else "bf16_tflops"
     peak = peaks.get(peak_key, peaks.get("bf16_tflops", FALLBACK_BF16_TFLOPS))
     roof = None
+    forms = []
     if precision == lad.LADDER_EMU_BF16:
         # executed slice products of the work each instance needs (one block pair per instance:
-        # every instance's V fits the budget; plain ladder form, as batched instances use)
+        # every instance's V fits the budget; each instance's ladder form from the planner's model)
         S = args.nslices or 6
-        useful = sum(2.0 * s.nchol * eri_products(s.nv, s.nv, s.nv) + 2.0 * ladder_products(s.no, s.nv, "plain")
-                     for s in shapes)
+        forms = ["pm" if lad.ladder_form_model(s.no, s.nv, s.nchol, args.nslices) == 1 else "plain" for s in shapes]
+        useful = sum(2.0 * s.nchol * eri_products(s.nv, s.nv, s.nv) + 2.0 * ladder_products(s.no, s.nv, f)
+                     for s, f in zip(shapes, forms))
         achieved = useful * (S * (S + 1) // 2) * steps / (ms_total * 1e-3) / 1e12
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "frac_of_burst": achieved / peaks.get("bf16_tflops", FALLBACK_BF16_TFLOPS),
@@ -401,6 +403,7 @@ def batched_record(args, lad, local, world, device_inputs, steps, warmup, fp64_s
            "schedule": (f"{-k} instance groups, one ERI launch and one ladder launch per shape per group"
                         if k < 0 else f"{k} worker streams"),
            "tuned": tuned,
+           "split_form_instances": sum(1 for f in forms if f == "pm"),
            "graph": "one CUDA graph replay per step",
            "inputs": "drawn on the GPU (timing)" if device_inputs else "ladder_inputs host generators",
            "roofline": roof, "clocks": clocks, "fp64_sequential": fp64}
@@ -918,8 +921,8 @@ def main():
     ap.add_argument("--form", default="auto", choices=["auto", "plain", "pm"],
                     help="emulated ladder form: the planner's choice, plain, or the symmetric/antisymmetric split")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="replicas", choices=["replicas", "shard"],
-                    help="N>1: an independent instance per GPU, or one contraction sharded over the GPUs")
+    ap.add_argument("--mode", default="shard", choices=["replicas", "shard"],
+                    help="N>1: one contraction sharded over the GPUs (default), or an independent instance per GPU")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true", help="skip the error report against the oracle")

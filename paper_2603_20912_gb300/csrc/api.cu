@@ -518,8 +518,7 @@ int auto_form(int no, int nv, int nchol, int nslices) {
     return pm < 0.95 * plain ? 1 : 0;
 }
 
-// split_ok = false keeps the plain form (instances of a batched plan, whose grouped launches
-// run the plain form).
+// split_ok = false keeps the plain form.
 int make_plan(ladder_plan_s** out, int no, int nv, int nchol, int precision, int nslices, size_t budget,
               int device, bool split_ok = true) {
     *out = nullptr;
@@ -890,7 +889,7 @@ int ladder_plan_batched(ladder_plan_t* out, int n, const int* no, const int* nv,
     // ERI fits), and the plan's workspace holds as many instances at once as the budget allows.
     for (int k = 0; k < n; ++k) {
         ladder_plan_s* s = nullptr;
-        const int rc = make_plan(&s, no[k], nv[k], nchol[k], precision, nslices, budget, device, false);
+        const int rc = make_plan(&s, no[k], nv[k], nchol[k], precision, nslices, budget, device, true);
         if (rc != LADDER_OK) {
             destroy_plan(p);
             return rc;
