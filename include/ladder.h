@@ -327,8 +327,11 @@ int ladder_tune_batched(ladder_plan_t plan, const double* const* L, const double
  * by Cauchy-Schwarz each level-l sum over a chunk is at most sum_{s+t=l-2} M_s M_t, M_s the
  * largest 2-norm of slice s's digits over any L^T row within one chunk-aligned window, and the
  * longest window (up to the limit) whose bounds stay within (l-1) 2^22 for l = 2..5 is used.  The
- * result does not depend on the chunk (exact integer sums).  blocks = 1 keeps 1024.  Applies to a
- * batched plan's instances too.  Returns LADDER_OK or LADDER_ERR_ARG.
+ * exact levels do not depend on the chunk; the shared accumulator of the levels >= 6 (weight
+ * <= 2^-28 of the leading level) is rounded once per chunk, which can move the int64 sum of an
+ * ERI element by a few units of 2^-49 of its scale before it is rounded to the V grid (2^-42), so
+ * results agree to that level (bit for bit in the tested cases).  blocks = 1 keeps 1024.  Applies
+ * to a batched plan's instances too.  Returns LADDER_OK or LADDER_ERR_ARG.
  *
  * ladder_plan_eri_chunk -- the chunk length (Cholesky vectors) the last ladder_apply of an emulated
  * plan with workspace `ws` chose; synchronises `stream` to read it.  -1 for a NULL, batched, FP64
