@@ -319,6 +319,25 @@ int ladder_tune_batched(ladder_plan_t plan, const double* const* L, const double
                         double* const* R, void* ws, cudaStream_t stream, int* best_schedule);
 
 /*
+ * ladder_plan_set_pbatch -- slice the Cholesky vectors a batch of pb at a time (emulated path;
+ * the P-split of a blocked Cholesky contraction).  The L^T digit planes of all nchol vectors take
+ * 2 nslices bytes per element of L for the whole call; with batches only pb vectors' planes are
+ * resident, sliced again for every (A,B) block pair, and the ERI of each batch adds its exact int64
+ * sums into V (every batch uses the exponents of all the vectors, so the sums share one fixed-point
+ * unit); the last batch rounds V onto the pair's grid.  This needs the symmetric/antisymmetric
+ * form's int64 V, so a plan with batches uses form 1.  ladder_plan picks batches of 8192, 4096,
+ * 2048 or 1024 vectors when a cost model (larger blocks against re-slicing L per block pair)
+ * prefers them or when nothing else fits the budget.  pb = 0 (or >= nchol) slices all vectors at
+ * once; otherwise pb must be a multiple of 64.  The exact levels of the ERI do not depend on the
+ * batches (see ladder_plan_set_eri_chunk for the shared tail level).  Returns LADDER_OK,
+ * LADDER_ERR_ARG (batched or sharded plan, bad pb), LADDER_ERR_UNSUPPORTED (pb > 0 on the FP64
+ * path), LADDER_ERR_BUDGET or LADDER_ERR_CUDA.  ladder_plan_get_pbatch: the batch, 0 for none,
+ * -1 for NULL.  ladder_plan_set_form(plan, 0) is refused (LADDER_ERR_ARG) while batches are set.
+ */
+int ladder_plan_set_pbatch(ladder_plan_t plan, int pb);
+int ladder_plan_get_pbatch(ladder_plan_t plan);
+
+/*
  * ladder_plan_set_eri_chunk -- longest exact K chunk of the emulated ERI, in blocks of 1024
  * Cholesky vectors (1..4, default 4).  Each chunk ends with a drain of the tensor-memory
  * accumulators into int64 registers that the next chunk's MMAs wait for.  With |digit| <= 64 a

@@ -73,6 +73,10 @@ def _load():
     lib.ladder_plan_get_form.restype = ci
     lib.ladder_form_model.argtypes = [ci, ci, ci, ci]
     lib.ladder_form_model.restype = ci
+    lib.ladder_plan_set_pbatch.argtypes = [vp, ci]
+    lib.ladder_plan_set_pbatch.restype = ci
+    lib.ladder_plan_get_pbatch.argtypes = [vp]
+    lib.ladder_plan_get_pbatch.restype = ci
     lib.ladder_plan_set_eri_chunk.argtypes = [vp, ci]
     lib.ladder_plan_set_eri_chunk.restype = ci
     lib.ladder_plan_eri_chunk.argtypes = [vp, vp, vp]
@@ -207,6 +211,13 @@ class Plan:
 
     def form(self) -> int:
         return int(_load().ladder_plan_get_form(self._h))
+
+    def pbatch(self) -> int:
+        return int(_load().ladder_plan_get_pbatch(self._h))
+
+    def set_pbatch(self, pb: int):
+        """Slice the Cholesky vectors pb at a time (0: all at once); see ladder_plan_set_pbatch."""
+        _check(_load().ladder_plan_set_pbatch(self._h, int(pb)), "ladder_plan_set_pbatch")
 
     def set_eri_chunk(self, blocks: int):
         """Longest exact K chunk of the emulated ERI in blocks of 1024 (1..4); see ladder_plan_set_eri_chunk."""
@@ -454,5 +465,5 @@ EXPORTED_SYMBOLS = [
     "ladder_form_model", "ladder_plan_set_wait_limit", "ladder_plan_get_wait_limit",
     "ladder_plan_shard_dry", "ladder_plan_set_path", "ladder_plan_get_path", "ladder_path_model",
     "ladder_plan_set_ladder_tile", "ladder_plan_get_ladder_tile", "ladder_plan_set_eri_chunk",
-    "ladder_plan_eri_chunk",
+    "ladder_plan_eri_chunk", "ladder_plan_set_pbatch", "ladder_plan_get_pbatch",
 ]

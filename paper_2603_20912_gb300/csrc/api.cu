@@ -115,7 +115,8 @@ ladder::WsLayout layout_for(const ladder_plan_s& p, long long max_pairs) {
         // (c, d) rows padded to vp (ladder::emu_vp): K index c*vp + d, zero for d >= nv.
         const size_t S = p.nslices;
         const size_t vp = (size_t)ladder::emu_vp(p.nv), nvp = (size_t)p.nv * vp;
-        const size_t kpad = nvp, xpad = align_up((size_t)p.nchol, 8);
+        const size_t batch = p.pb > 0 && p.pb < p.nchol ? (size_t)p.pb : (size_t)p.nchol;
+        const size_t kpad = nvp, xpad = align_up(batch, 8);
         const size_t G = ladder::kExpGroupRows;
         // V digit planes, or V as int64 for the symmetric/antisymmetric form (combined first)
         w.v_blk = take((p.form == 0 ? S * 2 : 8) * (size_t)max_pairs * kpad);
@@ -454,6 +455,52 @@ int choose_blocking(ladder_plan_s& p) {
     return apply_blocking(p, na, nb);
 }
 
+// Modelled extra time of slicing the Cholesky vectors in batches: every block pair re-slices all
+// of L (reads 8 and writes 2S bytes per element at ~3 TB/s) and launches three more kernels per
+// batch, and every ERI tile drains its accumulators once more per batch.
+double pbatch_overhead(const ladder_plan_s& p, const std::vector<BlockPair>& bps) {
+    if (p.pb <= 0 || p.pb >= p.nchol) return 0.0;
+    const double rows = (double)p.nv * ladder::emu_vp(p.nv);
+    const int nbat = (p.nchol + p.pb - 1) / p.pb;
+    const double slice = rows * p.nchol * (8.0 + 2.0 * p.nslices) / 3.0e12;
+    double tiles = 0.0;
+    for (auto& bp : bps) tiles += (double)eri_tile_count(bp, p.nv, ladder::kEmuTileN);
+    const double clusters = std::max(1, p.num_sms / 2);
+    return bps.size() * (slice + nbat * 30e-6) + tiles / clusters * (nbat - 1) * 4e-6;
+}
+
+// Emulated path: whether to slice the Cholesky vectors a batch at a time (the L^T digit planes of
+// all vectors take 2S bytes per element of L, which at large nchol leaves little of the budget
+// for V blocks).  Batches need the split form's int64 V, which adds the exact sums of the batches.
+// Candidates: all vectors at once (the blocking the plan holds, if `have`) and batches of 8192,
+// 4096, 2048 and 1024 vectors; the lowest modelled time wins (a batch must win by 3 %).  Host only:
+// returns the chosen batch (0: none) and, for a batch, its blocking; leaves the plan as it was.
+int select_pbatch(ladder_plan_s& p, bool have, int* out_na, int* out_nb) {
+    if (p.precision == LADDER_FP64 || p.nchol <= 1024) return 0;
+    double best = have ? model_time(p, p.bps) : 1e300;
+    int best_pb = 0;
+    const int pb0 = p.pb, form0 = p.form;
+    for (int pb : {8192, 4096, 2048, 1024}) {
+        if (pb >= p.nchol) continue;
+        p.pb = pb;
+        p.form = 1;
+        int na = 0, nb = 0;
+        if (select_blocking(p, &na, &nb) == LADDER_OK) {
+            const std::vector<BlockPair> bps = enumerate_blocks(p.nv, na, nb);
+            const double t = model_time(p, bps) + pbatch_overhead(p, bps);
+            if (t < best * 0.97) {
+                best = t;
+                best_pb = pb;
+                *out_na = na;
+                *out_nb = nb;
+            }
+        }
+    }
+    p.pb = pb0;
+    p.form = form0;
+    return best_pb;
+}
+
 bool aligned256(const void* ptr) { return (reinterpret_cast<uintptr_t>(ptr) & 255u) == 0; }
 
 void free_events(ladder_plan_s* p) {
@@ -520,7 +567,7 @@ int auto_form(int no, int nv, int nchol, int nslices) {
 
 // split_ok = false keeps the plain form.
 int make_plan(ladder_plan_s** out, int no, int nv, int nchol, int precision, int nslices, size_t budget,
-              int device, bool split_ok = true) {
+              int device, bool split_ok = true, bool pbatch_ok = true) {
     *out = nullptr;
     if (no < 1 || nv < 1 || nchol < 1) return LADDER_ERR_ARG;
     if ((long long)no * no > (1 << 20) || nv > 4096) return LADDER_ERR_ARG;
@@ -570,6 +617,16 @@ int make_plan(ladder_plan_s** out, int no, int nv, int nchol, int precision, int
     if (rc == LADDER_ERR_BUDGET && p->form == 1) {   // the split needs more workspace: fall back
         p->form = 0;
         rc = choose_blocking(*p);
+    }
+    // Emulated: slicing the Cholesky vectors in batches when that lets larger blocks fit (or any).
+    if ((rc == LADDER_OK || rc == LADDER_ERR_BUDGET) && precision != LADDER_FP64 && pbatch_ok) {
+        int na = 0, nb = 0;
+        const int pb = select_pbatch(*p, rc == LADDER_OK, &na, &nb);
+        if (pb > 0) {
+            p->pb = pb;
+            p->form = 1;
+            rc = apply_blocking(*p, na, nb);
+        }
     }
     // FP64: the factorised order when the model prefers it and its batch fits (also when no
     // blocking of the rebuild order fits the budget).
@@ -748,6 +805,7 @@ int ladder_plan_shard(ladder_plan_t plan, int rank, int world) {
 
 int ladder_plan_set_form(ladder_plan_t plan, int form) {
     if (!plan || plan->batched || (form != 0 && form != 1)) return LADDER_ERR_ARG;
+    if (form == 0 && plan->pb > 0 && plan->pb < plan->nchol) return LADDER_ERR_ARG;   // batches need form 1
     if (form == 1 && plan->precision == LADDER_FP64) return LADDER_ERR_UNSUPPORTED;
     if (form == plan->form) return LADDER_OK;
     DeviceGuard guard(plan->device);
@@ -840,7 +898,7 @@ int ladder_apply(ladder_plan_t plan, const double* L, const double* t2, double* 
         e = ladder::launch_emu_prep(*plan, L, t2, ws, stream);
         if (e == cudaSuccess) {
             for (const auto& bp : plan->bps) {
-                e = ladder::launch_emu_block(*plan, bp, R, ws, stream);
+                e = ladder::launch_emu_block(*plan, bp, L, R, ws, stream);
                 if (e != cudaSuccess) break;
             }
         }
@@ -889,7 +947,7 @@ int ladder_plan_batched(ladder_plan_t* out, int n, const int* no, const int* nv,
     // ERI fits), and the plan's workspace holds as many instances at once as the budget allows.
     for (int k = 0; k < n; ++k) {
         ladder_plan_s* s = nullptr;
-        const int rc = make_plan(&s, no[k], nv[k], nchol[k], precision, nslices, budget, device, true);
+        const int rc = make_plan(&s, no[k], nv[k], nchol[k], precision, nslices, budget, device, true, false);
         if (rc != LADDER_OK) {
             destroy_plan(p);
             return rc;
@@ -1085,6 +1143,26 @@ int ladder_tune_batched(ladder_plan_t plan, const double* const* L, const double
     return rc;
 }
 
+int ladder_plan_set_pbatch(ladder_plan_t plan, int pb) {
+    if (!plan || plan->batched || plan->shard_world > 1 || pb < 0 || pb % 64 != 0) return LADDER_ERR_ARG;
+    if (plan->precision == LADDER_FP64) return pb == 0 ? LADDER_OK : LADDER_ERR_UNSUPPORTED;
+    DeviceGuard guard(plan->device);
+    if (!guard.ok) return LADDER_ERR_CUDA;
+    const int old_pb = plan->pb, old_form = plan->form;
+    plan->pb = pb >= plan->nchol ? 0 : pb;
+    if (plan->pb > 0) plan->form = 1;   // batches add into the split form's int64 V
+    int rc = apply_blocking(*plan, plan->n_a, plan->n_b);
+    if (rc == LADDER_ERR_BUDGET) rc = choose_blocking(*plan);
+    if (rc != LADDER_OK) {
+        plan->pb = old_pb;
+        plan->form = old_form;
+        apply_blocking(*plan, plan->n_a, plan->n_b);
+    }
+    return rc;
+}
+
+int ladder_plan_get_pbatch(ladder_plan_t plan) { return plan ? (plan->pb > 0 && plan->pb < plan->nchol ? plan->pb : 0) : -1; }
+
 int ladder_plan_set_eri_chunk(ladder_plan_t plan, int blocks) {
     if (!plan || blocks < 1 || blocks > 4) return LADDER_ERR_ARG;
     plan->eri_chunk_max = blocks;
@@ -1220,6 +1298,18 @@ int dry_plan(ladder_plan_s& p, int no, int nv, int nchol, int precision, int nsl
         if (rc == LADDER_ERR_BUDGET && p.form == 1) {
             p.form = 0;
             rc = select_blocking(p, &na, &nb);
+        }
+        if (rc == LADDER_OK || rc == LADDER_ERR_BUDGET) {   // batches of Cholesky vectors, as ladder_plan
+            if (rc == LADDER_OK) p.bps = enumerate_blocks(nv, na, nb);
+            int bna = 0, bnb = 0;
+            const int pb = select_pbatch(p, rc == LADDER_OK, &bna, &bnb);
+            if (pb > 0) {
+                p.pb = pb;
+                p.form = 1;
+                na = bna;
+                nb = bnb;
+                rc = LADDER_OK;
+            }
         }
         if (rc != LADDER_OK) return rc;
     } else if (na > nv || nb > nv) {

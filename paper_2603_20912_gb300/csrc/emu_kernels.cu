@@ -283,10 +283,11 @@ __global__ void f_table_kernel(const unsigned long long* __restrict__ lnorm_bits
     f[k] = exponent_above(na * nb * (1.0 + 0x1p-20));
 }
 
-// L^T slices: tile of 64 P x 64 rows through shared memory; writes planes[s][r][P].
+// L^T slices of the Cholesky vectors [pbase, pbase + nchol): tile of 64 P x 64 rows through shared
+// memory; writes planes[s][r][P - pbase] (row stride xpad).
 template <int S>
-__global__ void __launch_bounds__(256) lt_slice_kernel(const double* __restrict__ L, int nchol, int nv, int vp,
-                                                       int xpad, const int* __restrict__ lt_exp,
+__global__ void __launch_bounds__(256) lt_slice_kernel(const double* __restrict__ L, int pbase, int nchol, int nv,
+                                                       int vp, int xpad, const int* __restrict__ lt_exp,
                                                        __nv_bfloat16* __restrict__ planes,
                                                        unsigned* __restrict__ norm2, int nblk, unsigned* status) {
     __shared__ double tile[64][65];
@@ -298,7 +299,7 @@ __global__ void __launch_bounds__(256) lt_slice_kernel(const double* __restrict_
         const long long r = r0 + rr;
         const int c = (int)(r % vp);
         tile[p][rr] = (P0 + p < nchol && r < rows && c < nv)
-                          ? __ldg(L + (size_t)(P0 + p) * nv2 + (size_t)(r / vp) * nv + c)
+                          ? __ldg(L + (size_t)(pbase + P0 + p) * nv2 + (size_t)(r / vp) * nv + c)
                           : 0.0;
     }
     __syncthreads();
@@ -807,6 +808,8 @@ struct EriItem {
     __nv_bfloat16* vplanes;
     long long* vint;      // non-null: V as int64 N (row stride kpad) instead of digit planes
     const int* kbc;       // K blocks (of the stage width) per exact chunk, chosen on the device
+    int acc_mode;         // int64 V over batches of Cholesky vectors: 3 one batch (round), 0 first
+                          // (store the raw sums), 1 middle (add), 2 last (add, then round)
 };
 
 struct EriBatch {
@@ -1031,7 +1034,21 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsEri, 1)
                 const size_t off = (size_t)(rs + (b - max(a, p.b0))) * p.kpad + (size_t)c * p.vp + d;
                 if (p.vint != nullptr) {   // 64 bytes: two whole sectors
                     __align__(16) long long N[8];
-                    round_run<S>(run[g], sh, N, B.status);
+                    if ((p.acc_mode == 1 || p.acc_mode == 2) && off + 8 <= p.plane_stride) {   // earlier batches
+                        const longlong2* src = reinterpret_cast<const longlong2*>(p.vint + off);
+#pragma unroll
+                        for (int k2 = 0; k2 < 4; ++k2) {
+                            const longlong2 v2 = __ldcs(src + k2);
+                            run[g][2 * k2] += v2.x;
+                            run[g][2 * k2 + 1] += v2.y;
+                        }
+                    }
+                    if (p.acc_mode >= 2) {
+                        round_run<S>(run[g], sh, N, B.status);
+                    } else {
+#pragma unroll
+                        for (int k2 = 0; k2 < 8; ++k2) N[k2] = run[g][k2];
+                    }
                     const uint4* w4 = reinterpret_cast<const uint4*>(N);
                     if (LADDER_IN_BOUNDS(off + 8 <= p.plane_stride, B.status)) {
                         st_cs_32B(p.vint + off, w4[0], w4[1]);
@@ -1545,19 +1562,44 @@ T* at(void* ws, size_t off) {
 // Padded (c, d) layout of the emulated path: vp = nv rounded up to 16 (emu_vp), K = nv * vp.
 inline int padded_vp(int nv) { return emu_vp(nv); }
 
+// Cholesky vectors sliced at a time: all of them, or the plan's batch.
+inline int lt_batch(const ladder_plan_s& p) { return p.pb > 0 && p.pb < p.nchol ? p.pb : p.nchol; }
+
+// L^T digit planes of the Cholesky vectors [pbase, pbase + count), their digit norms and the ERI's
+// exact chunk for them (three kernels, memsets of the norm accumulators).
+template <int S>
+cudaError_t slice_lt(const ladder_plan_s& p, const double* L, void* ws, int pbase, int count, cudaStream_t s) {
+    const int vp = padded_vp(p.nv);
+    const long long rows = (long long)p.nv * vp;
+    const int xpad = (int)align_up((size_t)lt_batch(p), 8);
+    const int nblk = (xpad + kEmuChunkK - 1) / kEmuChunkK;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(at<char>(ws, p.ws.lt_norm2), 0, (size_t)S * rows * nblk * 4, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(at<char>(ws, p.ws.eri_cand), 0, (size_t)S * 3 * 4, s)) != cudaSuccess) return e;
+    lt_slice_kernel<S><<<dim3((count + 63) / 64, (unsigned)((rows + 63) / 64)), 256, 0, s>>>(
+        L, pbase, count, p.nv, vp, xpad, at<int>(ws, p.ws.lt_exp), at<__nv_bfloat16>(ws, p.ws.lt_slices),
+        at<unsigned>(ws, p.ws.lt_norm2), nblk, p.d_status);
+    eri_chunk_norms_kernel<<<(unsigned)((rows + 255) / 256), 256, 0, s>>>(at<unsigned>(ws, p.ws.lt_norm2), rows, S,
+                                                                         nblk, at<unsigned>(ws, p.ws.eri_cand));
+    eri_chunk_select_kernel<<<1, 1, 0, s>>>(at<unsigned>(ws, p.ws.eri_cand), S, p.eri_chunk_max, eri_bk_for(S),
+                                            at<int>(ws, p.ws.eri_kbc));
+    return cudaGetLastError();
+}
+
 template <int S>
 cudaError_t prep_impl(const ladder_plan_s& p, const double* L, const double* t2, void* ws, cudaStream_t s) {
     const long long nv2 = (long long)p.nv * p.nv;
     const int vp = padded_vp(p.nv);
     const long long rows = (long long)p.nv * vp;
     const int no2 = p.no * p.no;
-    const int xpad = (int)align_up((size_t)p.nchol, 8);
     const int kpad = (int)rows;
     const int ngt = (no2 + kG - 1) / kG;
-    // kernels: L^T statistics, pair exponents, L^T slices, chunk norms and choice, then the T side
-    // (row maxima, exponents, slices; the split form has two exponent passes when rows i < j exist)
+    // kernels: L^T statistics, pair exponents, L^T slices, chunk norms and choice (here unless the
+    // Cholesky vectors are sliced batch by batch with the blocks), then the T side (row maxima,
+    // exponents, slices; the split form has two exponent passes when rows i < j exist)
+    const bool batched_p = lt_batch(p) < p.nchol;
     const int t_kernels = p.form == 0 ? 3 : (p.no > 1 ? 4 : 3);
-    LaunchTimer tm(p, s, LADDER_KERNEL_PREP, 5 + t_kernels);
+    LaunchTimer tm(p, s, LADDER_KERNEL_PREP, (batched_p ? 2 : 5) + t_kernels);
     cudaError_t e;
     if ((e = cudaMemsetAsync(at<char>(ws, p.ws.lnorm), 0, (size_t)p.nv * 8, s)) != cudaSuccess) return e;
     if (p.form == 0 && (e = cudaMemsetAsync(at<char>(ws, p.ws.t_gmax), 0, (size_t)ngt * 8, s)) != cudaSuccess)
@@ -1567,16 +1609,7 @@ cudaError_t prep_impl(const ladder_plan_s& p, const double* L, const double* t2,
                                                                         at<double>(ws, p.ws.lsq));
     f_table_kernel<<<(unsigned)((nv2 + 255) / 256), 256, 0, s>>>(at<unsigned long long>(ws, p.ws.lnorm), p.nv,
                                                                    at<int>(ws, p.ws.v_exp));
-    const int nblk = (xpad + kEmuChunkK - 1) / kEmuChunkK;
-    if ((e = cudaMemsetAsync(at<char>(ws, p.ws.lt_norm2), 0, (size_t)S * rows * nblk * 4, s)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(at<char>(ws, p.ws.eri_cand), 0, (size_t)S * 3 * 4, s)) != cudaSuccess) return e;
-    lt_slice_kernel<S><<<dim3((p.nchol + 63) / 64, (unsigned)((rows + 63) / 64)), 256, 0, s>>>(
-        L, p.nchol, p.nv, vp, xpad, at<int>(ws, p.ws.lt_exp), at<__nv_bfloat16>(ws, p.ws.lt_slices),
-        at<unsigned>(ws, p.ws.lt_norm2), nblk, p.d_status);
-    eri_chunk_norms_kernel<<<(unsigned)((rows + 255) / 256), 256, 0, s>>>(at<unsigned>(ws, p.ws.lt_norm2), rows, S,
-                                                                         nblk, at<unsigned>(ws, p.ws.eri_cand));
-    eri_chunk_select_kernel<<<1, 1, 0, s>>>(at<unsigned>(ws, p.ws.eri_cand), S, p.eri_chunk_max, eri_bk_for(S),
-                                            at<int>(ws, p.ws.eri_kbc));
+    if (!batched_p && (e = slice_lt<S>(p, L, ws, 0, p.nchol, s)) != cudaSuccess) return e;
     if (p.form == 0) {
         t_rowmax_kernel<<<dim3((unsigned)((nv2 + 8191) / 8192), no2), 256, 0, s>>>(
             t2, nv2, no2, at<unsigned long long>(ws, p.ws.t_gmax));
@@ -1608,24 +1641,27 @@ cudaError_t prep_impl(const ladder_plan_s& p, const double* L, const double* t2,
 
 // The ERI work item of one block pair of a plan whose workspace starts at ws: its tables and
 // its two L^T tensor maps.
+// count: Cholesky vectors in the L^T planes (the batch); acc_mode as in EriItem.
 template <int S>
-bool eri_item(const ladder_plan_s& p, const BlockPair& bp, void* ws, EriItem* it, CUtensorMap* ta, CUtensorMap* tb) {
+bool eri_item(const ladder_plan_s& p, const BlockPair& bp, void* ws, EriItem* it, CUtensorMap* ta, CUtensorMap* tb,
+              int count = 0, int acc_mode = 3) {
     constexpr int EBK = eri_bk_for(S);
     const int vp = padded_vp(p.nv);
     if (vp % 16 != 0) return false;   // the epilogue stores whole 32-byte sectors
+    if (count <= 0) count = p.nchol;
     const long long rows = (long long)p.nv * vp;
-    const int xpad = (int)align_up((size_t)p.nchol, 8);
-    if (!make_tmap(ta, at<char>(ws, p.ws.lt_slices), p.nchol, rows, S, (uint64_t)xpad * 2, (uint64_t)rows * xpad * 2,
+    const int xpad = (int)align_up((size_t)lt_batch(p), 8);
+    if (!make_tmap(ta, at<char>(ws, p.ws.lt_slices), count, rows, S, (uint64_t)xpad * 2, (uint64_t)rows * xpad * 2,
                    EBK, kEriChunkRows) ||
-        !make_tmap(tb, at<char>(ws, p.ws.lt_slices), p.nchol, rows, S, (uint64_t)xpad * 2, (uint64_t)rows * xpad * 2,
+        !make_tmap(tb, at<char>(ws, p.ws.lt_slices), count, rows, S, (uint64_t)xpad * 2, (uint64_t)rows * xpad * 2,
                    EBK, kEmuTileN / 2))
         return false;
     const int* row_start = reinterpret_cast<const int*>(p.d_tables) + bp.rows_off;
     const int2* chunks = reinterpret_cast<const int2*>(p.d_tables) + bp.chunks_off;
-    *it = EriItem{p.nv, vp, p.nchol, bp.a0, bp.a1 - bp.a0, bp.b0, bp.b1 - bp.b0, (int)rows,
+    *it = EriItem{p.nv, vp, count, bp.a0, bp.a1 - bp.a0, bp.b0, bp.b1 - bp.b0, (int)rows,
                   (size_t)p.max_pairs * (size_t)rows, chunks, row_start, at<int>(ws, p.ws.lt_exp), at<int>(ws, p.ws.v_exp),
                   at<__nv_bfloat16>(ws, p.ws.v_blk), p.form == 1 ? at<long long>(ws, p.ws.v_blk) : nullptr,
-                  at<int>(ws, p.ws.eri_kbc)};
+                  at<int>(ws, p.ws.eri_kbc), acc_mode};
     return true;
 }
 
@@ -1741,7 +1777,8 @@ bool ladder_item_pm(const ladder_plan_s& p, const BlockPair& bp, void* ws, long 
 // One block pair in the symmetric/antisymmetric form: ERI and self-product entries as in the
 // plain form, V -> V', V'', the X and Y ladders, and the four-way finalisation.
 template <int S>
-cudaError_t block_pm_impl(const ladder_plan_s& p, const BlockPair& bp, double* R, void* ws, cudaStream_t s) {
+cudaError_t block_pm_impl(const ladder_plan_s& p, const BlockPair& bp, const double* L, double* R, void* ws,
+                          cudaStream_t s) {
     const PmDims d = pm_dims(p.no, p.nv);
     const bool has_y = d.nm > 0 && d.km > 0;
     cudaError_t e;
@@ -1757,12 +1794,30 @@ cudaError_t block_pm_impl(const ladder_plan_s& p, const BlockPair& bp, double* R
     eb.entries = reinterpret_cast<const int4*>(table + bp.tiles_off);
     eb.status = p.d_status;
     eb.wait_ns = p.wait_ns;
-    if (!eri_item<S>(p, bp, ws, &eb.item[0], &eb.ta[0], &eb.tb[0])) return cudaErrorInvalidValue;
     const int vp = padded_vp(p.nv);
-    {
+    const int pb = lt_batch(p);
+    if (pb >= p.nchol) {
+        if (!eri_item<S>(p, bp, ws, &eb.item[0], &eb.ta[0], &eb.tb[0])) return cudaErrorInvalidValue;
         LaunchTimer tm(p, s, LADDER_KERNEL_ERI, 2);
         launch_eri_batch<S>(eb, p.eri_clusters > 0 ? p.eri_clusters : p.num_sms / 2, s);
         launch_self<S>(p, bp, ws, s);
+    } else {
+        // Cholesky vectors in batches: each batch's L^T planes are sliced into the workspace and its
+        // ERI adds its exact int64 sums into V (same fixed-point unit for every batch: the exponents
+        // are those of all the vectors); the last batch rounds V onto the pair's grid.
+        for (int P0 = 0; P0 < p.nchol; P0 += pb) {
+            const int count = std::min(pb, p.nchol - P0);
+            const bool first = P0 == 0, last = P0 + pb >= p.nchol;
+            {
+                LaunchTimer tm(p, s, LADDER_KERNEL_PREP, 3);
+                if ((e = slice_lt<S>(p, L, ws, P0, count, s)) != cudaSuccess) return e;
+            }
+            if (!eri_item<S>(p, bp, ws, &eb.item[0], &eb.ta[0], &eb.tb[0], count, first ? 0 : (last ? 2 : 1)))
+                return cudaErrorInvalidValue;
+            LaunchTimer tm(p, s, LADDER_KERNEL_ERI, last ? 2 : 1);
+            launch_eri_batch<S>(eb, p.eri_clusters > 0 ? p.eri_clusters : p.num_sms / 2, s);
+            if (last) launch_self<S>(p, bp, ws, s);
+        }
     }
     {
         LaunchTimer tm(p, s, LADDER_KERNEL_COMBINE);
@@ -1801,8 +1856,10 @@ cudaError_t block_pm_impl(const ladder_plan_s& p, const BlockPair& bp, double* R
 }
 
 template <int S>
-cudaError_t block_impl(const ladder_plan_s& p, const BlockPair& bp, double* R, void* ws, cudaStream_t s) {
-    if (p.form == 1) return block_pm_impl<S>(p, bp, R, ws, s);
+cudaError_t block_impl(const ladder_plan_s& p, const BlockPair& bp, const double* L, double* R, void* ws,
+                       cudaStream_t s) {
+    if (p.form == 1) return block_pm_impl<S>(p, bp, L, R, ws, s);
+    if (lt_batch(p) < p.nchol) return cudaErrorInvalidValue;   // batches of vectors need the split form's int64 V
     const int no2 = p.no * p.no;
     cudaError_t e;
     // int64 ladder accumulator of this block pair starts at zero
@@ -2005,12 +2062,13 @@ int emu_max_group() { return kMaxItems; }
 
 int emu_eri_stage_k(int nslices) { return eri_bk_for(nslices); }
 
-cudaError_t launch_emu_block(const ladder_plan_s& p, const BlockPair& bp, double* R, void* ws, cudaStream_t s) {
+cudaError_t launch_emu_block(const ladder_plan_s& p, const BlockPair& bp, const double* L, double* R, void* ws,
+                             cudaStream_t s) {
     switch (p.nslices) {
-        case 5: return block_impl<5>(p, bp, R, ws, s);
-        case 6: return block_impl<6>(p, bp, R, ws, s);
-        case 7: return block_impl<7>(p, bp, R, ws, s);
-        case 8: return block_impl<8>(p, bp, R, ws, s);
+        case 5: return block_impl<5>(p, bp, L, R, ws, s);
+        case 6: return block_impl<6>(p, bp, L, R, ws, s);
+        case 7: return block_impl<7>(p, bp, L, R, ws, s);
+        case 8: return block_impl<8>(p, bp, L, R, ws, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -134,6 +134,7 @@ struct ladder_plan_s {
     int form = 0;  // emulated ladder form: 0 = plain (K = (c,d)), 1 = symmetric/antisymmetric
     int lad_bn = ladder::kEmuTileN;  // emulated ladder on one SM: pairs per column tile (16..96)
     int eri_chunk_max = 4;           // emulated ERI: longest exact K chunk, in blocks of 1024 (1..4)
+    int pb = 0;                      // emulated: Cholesky vectors per slicing batch (0: all at once)
     int path = 0;     // 0: rebuild (ac|bd) per block pair; 1: factorised sum_P L_P T_ij L_P^T (FP64)
     int fact_pb = 0;  // factorised path: Cholesky vectors per batch
     int shard_rank = 0, shard_world = 1;  // this plan holds shard `shard_rank` of `shard_world`
@@ -210,7 +211,7 @@ cudaError_t launch_energy(const ladder_plan_s& p, const double* t2, const double
 // emu_kernels.cu
 cudaError_t launch_emu_prep(const ladder_plan_s& p, const double* L, const double* t2, void* ws,
                             cudaStream_t s);
-cudaError_t launch_emu_block(const ladder_plan_s& p, const BlockPair& bp, double* R, void* ws,
+cudaError_t launch_emu_block(const ladder_plan_s& p, const BlockPair& bp, const double* L, double* R, void* ws,
                              cudaStream_t s);
 // A group of emulated instances planned as one block pair each, run with one ERI launch and
 // one ladder launch per ladder shape over all of them (ws[k]: instance k's workspace; entries:

@@ -178,3 +178,18 @@ def test_path_model_decisions(lib):
                 assert lad.ladder_path_model(no, nv, nchol, lad.LADDER_EMU_BF16) == 0
     with pytest.raises(lad.LadderError):
         lad.ladder_path_model(0, 5, 5)
+
+
+def test_dry_planner_batches_cholesky_vectors_when_their_planes_do_not_fit(lib):
+    # L^T digit planes of all 20000 vectors: 12 x 64 x 64 x 20000 bytes = 983 MB > the budget;
+    # sliced in batches they fit, and the workspace respects the budget
+    no, nv, nchol = 2, 64, 20000
+    budget = 700 * 10 ** 6
+    d = lad.ladder_plan_dry(no, nv, nchol, lad.LADDER_EMU_BF16, ws_budget_bytes=budget)
+    assert d["ws_bytes"] <= budget
+    covered = sum(b[4] for b in d["blocks"])
+    assert covered == nv * (nv + 1) // 2
+    # at the default workload the planes fit with room to spare: no batches, the same blocking
+    s = CONFIGS["c3"]
+    d3 = lad.ladder_plan_dry(s.no, s.nv, s.nchol, lad.LADDER_EMU_BF16, ws_budget_bytes=int(0.88 * 280e9))
+    assert (d3["n_a"], d3["n_b"]) == (400, 200)
