@@ -817,7 +817,8 @@ struct EriBatch {
     CUtensorMap tb[kMaxItems];  // L^T slices, 48-row boxes (B)
     EriItem item[kMaxItems];
     const int4* entries;        // (row tile, column tile, item, 0)
-    int nentries, nitems;
+    const int* ustart;          // first entry of every unit (a column tile's run of row tiles), then nentries
+    int nentries, nitems, nunits;
     unsigned* status;
     unsigned long long wait_ns; // limit of every bounded mbarrier wait (ns of the global timer)
 };
@@ -834,7 +835,9 @@ struct EriBatch {
 // whose 8-row groups lie S*8*BK*2 bytes apart.  Both CTAs' TMA loads complete on the leader's
 // (rank 0) full barrier; the leader issues the MMAs and its commits release the stage and
 // publish the accumulators in both CTAs; the epilogue warps of both CTAs release the
-// accumulators to the leader.  K = nchol runs in exact chunks of kEmuChunkK.
+// accumulators to the leader.  K = nchol runs in exact chunks (kbc stages each).  CTA pair c runs
+// the units c, c + pairs, ...: a unit is the run of entries (row tiles of one band) sharing one
+// column tile, so that tile's operand is reused from L2 by one CTA pair.
 template <int S>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsEri, 1)
     eri_emu_kernel(const __grid_constant__ EriBatch B) {
@@ -877,7 +880,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsEri, 1)
         Ring ring;
         bool ok = true;
         const uint64_t keep = policy_evict_last();
-        for (int e = cluster; e < B.nentries && ok; e += nclusters) {
+        for (int u = cluster; u < B.nunits && ok; u += nclusters)
+        for (int e = B.ustart[u]; e < B.ustart[u + 1] && ok; ++e) {
             const int4 en = B.entries[e];
             const EriItem& p = B.item[en.z];
             const int nkb = (p.nchol + BK - 1) / BK;
@@ -905,7 +909,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsEri, 1)
         const uint32_t idesc = idesc_bf16_f32(2 * kEmuTile, kEmuTileN);
         bool ok = true;
         int it = 0;
-        for (int e = cluster; e < B.nentries && ok; e += nclusters) {
+        for (int u = cluster; u < B.nunits && ok; u += nclusters)
+        for (int e = B.ustart[u]; e < B.ustart[u + 1] && ok; ++e) {
             const EriItem& p = B.item[B.entries[e].z];
             const int nkb = (p.nchol + BK - 1) / BK;
             const int kb_per_chunk = *p.kbc;
@@ -941,7 +946,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsEri, 1)
         // With vp >= 48 the warp's 48 columns touch at most two b and two exponent groups, so
         // the exponent tables of a tile come down to ten loads per thread, issued before the
         // accumulators are waited for so that their latency hides behind the MMAs.
-        for (int e = cluster; e < B.nentries && ok; e += nclusters) {
+        for (int u = cluster; u < B.nunits && ok; u += nclusters)
+        for (int e = B.ustart[u]; e < B.ustart[u + 1] && ok; ++e) {
             const int4 en = B.entries[e];
             const EriItem& p = B.item[en.z];
             const int Ncols = p.nb * p.vp;
@@ -1034,20 +1040,25 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsEri, 1)
                 const size_t off = (size_t)(rs + (b - max(a, p.b0))) * p.kpad + (size_t)c * p.vp + d;
                 if (p.vint != nullptr) {   // 64 bytes: two whole sectors
                     __align__(16) long long N[8];
-                    if ((p.acc_mode == 1 || p.acc_mode == 2) && off + 8 <= p.plane_stride) {   // earlier batches
+                    // this target's exact sum: the product, plus (Cholesky batches) the sums the
+                    // earlier batches left in this V element (the other target has its own)
+                    long long I[8];
+#pragma unroll
+                    for (int k2 = 0; k2 < 8; ++k2) I[k2] = run[g][k2];
+                    if ((p.acc_mode == 1 || p.acc_mode == 2) && off + 8 <= p.plane_stride) {
                         const longlong2* src = reinterpret_cast<const longlong2*>(p.vint + off);
 #pragma unroll
                         for (int k2 = 0; k2 < 4; ++k2) {
                             const longlong2 v2 = __ldcs(src + k2);
-                            run[g][2 * k2] += v2.x;
-                            run[g][2 * k2 + 1] += v2.y;
+                            I[2 * k2] += v2.x;
+                            I[2 * k2 + 1] += v2.y;
                         }
                     }
                     if (p.acc_mode >= 2) {
-                        round_run<S>(run[g], sh, N, B.status);
+                        round_run<S>(I, sh, N, B.status);
                     } else {
 #pragma unroll
-                        for (int k2 = 0; k2 < 8; ++k2) N[k2] = run[g][k2];
+                        for (int k2 = 0; k2 < 8; ++k2) N[k2] = I[k2];
                     }
                     const uint4* w4 = reinterpret_cast<const uint4*>(N);
                     if (LADDER_IN_BOUNDS(off + 8 <= p.plane_stride, B.status)) {
@@ -1670,7 +1681,7 @@ bool eri_item(const ladder_plan_s& p, const BlockPair& bp, void* ws, EriItem* it
 // others).
 template <int S>
 void launch_eri_batch(const EriBatch& eb, int max_clusters, cudaStream_t s) {
-    const int clusters = std::max(1, std::min(eb.nentries, max_clusters));
+    const int clusters = std::max(1, std::min(eb.nunits, max_clusters));
     eri_emu_kernel<S><<<2 * clusters, kThreadsEri, eri_smem_bytes_for(S), s>>>(eb);
 }
 
@@ -1792,6 +1803,8 @@ cudaError_t block_pm_impl(const ladder_plan_s& p, const BlockPair& bp, const dou
     eb.nitems = 1;
     eb.nentries = bp.ntiles;
     eb.entries = reinterpret_cast<const int4*>(table + bp.tiles_off);
+    eb.nunits = bp.nunits;
+    eb.ustart = reinterpret_cast<const int*>(p.d_tables) + bp.units_off;
     eb.status = p.d_status;
     eb.wait_ns = p.wait_ns;
     const int vp = padded_vp(p.nv);
@@ -1870,6 +1883,8 @@ cudaError_t block_impl(const ladder_plan_s& p, const BlockPair& bp, const double
     eb.nitems = 1;
     eb.nentries = bp.ntiles;
     eb.entries = reinterpret_cast<const int4*>(table + bp.tiles_off);
+    eb.nunits = bp.nunits;
+    eb.ustart = reinterpret_cast<const int*>(p.d_tables) + bp.units_off;
     eb.status = p.d_status;
     eb.wait_ns = p.wait_ns;
     if (!eri_item<S>(p, bp, ws, &eb.item[0], &eb.ta[0], &eb.tb[0])) return cudaErrorInvalidValue;
@@ -1914,7 +1929,7 @@ cudaError_t block_impl(const ladder_plan_s& p, const BlockPair& bp, const double
 template <int S>
 cudaError_t group_impl(const ladder_plan_s& parent, const ladder_plan_s* const* subs, int n, void* const* ws,
                        const double* const* L, const double* const* t2, double* const* R, const int4* entries,
-                       int nentries, cudaStream_t s) {
+                       int nentries, const int* ustart, int nunits, cudaStream_t s) {
     if (n < 1 || n > kMaxItems) return cudaErrorInvalidValue;
     cudaError_t e;
     for (int k = 0; k < n; ++k) {
@@ -1930,6 +1945,8 @@ cudaError_t group_impl(const ladder_plan_s& parent, const ladder_plan_s* const* 
     eb.nitems = n;
     eb.nentries = nentries;
     eb.entries = entries;
+    eb.nunits = nunits;
+    eb.ustart = ustart;
     eb.status = parent.d_status;
     eb.wait_ns = parent.wait_ns;
     for (int k = 0; k < n; ++k)
@@ -2048,12 +2065,12 @@ cudaError_t launch_emu_prep(const ladder_plan_s& p, const double* L, const doubl
 
 cudaError_t launch_emu_group(const ladder_plan_s& parent, const ladder_plan_s* const* subs, int n, void* const* ws,
                              const double* const* L, const double* const* t2, double* const* R, const int4* entries,
-                             int nentries, cudaStream_t s) {
+                             int nentries, const int* ustart, int nunits, cudaStream_t s) {
     switch (parent.nslices) {
-        case 5: return group_impl<5>(parent, subs, n, ws, L, t2, R, entries, nentries, s);
-        case 6: return group_impl<6>(parent, subs, n, ws, L, t2, R, entries, nentries, s);
-        case 7: return group_impl<7>(parent, subs, n, ws, L, t2, R, entries, nentries, s);
-        case 8: return group_impl<8>(parent, subs, n, ws, L, t2, R, entries, nentries, s);
+        case 5: return group_impl<5>(parent, subs, n, ws, L, t2, R, entries, nentries, ustart, nunits, s);
+        case 6: return group_impl<6>(parent, subs, n, ws, L, t2, R, entries, nentries, ustart, nunits, s);
+        case 7: return group_impl<7>(parent, subs, n, ws, L, t2, R, entries, nentries, ustart, nunits, s);
+        case 8: return group_impl<8>(parent, subs, n, ws, L, t2, R, entries, nentries, ustart, nunits, s);
         default: return cudaErrorInvalidValue;
     }
 }
