@@ -290,22 +290,16 @@ EriRowTiles eri_row_tiles(const BlockPair& bp, int nv) {
 // ERI work entries of one block pair, (rt, qt, 0, 0): a 256-row tile rt (computed by a CTA pair,
 // 128 rows each) and a 96-column tile qt of (b,d), kept when one of its rows stores to one of
 // its b.  Order: a band of row tiles whose operand slices take ~40 MB of L2 stays resident while
-// every column tile of the band streams past it.  The entries of one (band, column tile) form a
-// unit, which one CTA pair runs from start to end, so that the column tile's operand is read
-// from DRAM once per band and its row tiles' operands stay shared by all CTA pairs; `units`
-// receives the first entry of every unit and, last, the number of entries.
-std::vector<int> eri_entries(const BlockPair& bp, int nv, int tile_n, size_t row_bytes,
-                             std::vector<int>* units = nullptr) {
+// every column tile of the band streams past it.
+std::vector<int> eri_entries(const BlockPair& bp, int nv, int tile_n, size_t row_bytes) {
     const EriRowTiles rt = eri_row_tiles(bp, nv);
     nv = ladder::emu_vp(nv);  // columns run over the padded (b, d) range
     std::vector<int> out;
     const long long N = (long long)(bp.b1 - bp.b0) * nv;
     const int nrt = (int)rt.key.size(), nqt = (int)((N + tile_n - 1) / tile_n);
     const int band = (int)std::max<size_t>(4, std::min<size_t>(32, (40u << 20) / std::max<size_t>(1, row_bytes * 256)));
-    if (units) units->clear();
     for (int r0 = 0; r0 < nrt; r0 += band)
-        for (int qt = 0; qt < nqt; ++qt) {
-            const size_t start = out.size() / 4;
+        for (int qt = 0; qt < nqt; ++qt)
             for (int r = r0; r < std::min(nrt, r0 + band); ++r) {
                 const long long last = std::min((long long)(qt + 1) * tile_n, N) - 1;
                 if (rt.key[r] > bp.b0 + (int)(last / nv)) continue;
@@ -314,22 +308,17 @@ std::vector<int> eri_entries(const BlockPair& bp, int nv, int tile_n, size_t row
                 out.push_back(0);
                 out.push_back(0);
             }
-            if (units && out.size() / 4 > start) units->push_back((int)start);
-        }
-    if (units) units->push_back((int)(out.size() / 4));
     return out;
 }
 
 int build_tables(ladder_plan_s& p) {
     size_t n_int2 = 0, n_int = 0;
-    std::vector<std::vector<int>> tiles, chunks, units;
+    std::vector<std::vector<int>> tiles, chunks;
     for (auto& bp : p.bps) n_int2 += bp.npairs;
     if (p.precision != LADDER_FP64)
         for (auto& bp : p.bps) {
-            units.emplace_back();
             tiles.push_back(eri_entries(bp, p.nv, ladder::kEmuTileN,
-                                        (size_t)p.nslices * 2 * ladder::align_up((size_t)p.nchol, 8), &units.back()));
-            n_int += units.back().size();
+                                        (size_t)p.nslices * 2 * ladder::align_up((size_t)p.nchol, 8)));
             chunks.push_back(eri_row_tiles(bp, p.nv).chunks);
             n_int2 += tiles.back().size() / 2 + chunks.back().size() / 2;
         }
@@ -361,9 +350,6 @@ int build_tables(ladder_plan_s& p) {
         p.bps[k].chunks_off = o2;
         for (size_t t = 0; t < chunks[k].size(); ++t) host[2 * o2 + t] = chunks[k][t];
         o2 += chunks[k].size() / 2;
-        p.bps[k].units_off = oi;                       // in int units
-        p.bps[k].nunits = (int)units[k].size() - 1;
-        for (int u : units[k]) host[oi++] = u;
     }
     if (p.d_tables) {
         cudaFree(p.d_tables);
@@ -539,7 +525,6 @@ void destroy_plan(ladder_plan_s* p) {
     if (p->d_status) cudaFree(p->d_status);
     if (p->d_partials) cudaFree(p->d_partials);
     if (p->d_group_entries) cudaFree(p->d_group_entries);
-    if (p->d_group_units) cudaFree(p->d_group_units);
     if (cur >= 0 && cur != p->device) cudaSetDevice(cur);
     delete p;
 }
@@ -720,23 +705,17 @@ int schedule_groups(ladder_plan_s& p, size_t cap) {
         used[g] += need;
         groups[g].push_back(k);
     }
-    std::vector<int> host, hostu;
+    std::vector<int> host;
     p.group_eoff.clear();
     p.group_ecnt.clear();
-    p.group_uoff.clear();
-    p.group_ucnt.clear();
     for (auto& grp : groups) {
         p.group_eoff.push_back(host.size() / 4);
-        p.group_uoff.push_back(hostu.size());
         int cnt = 0;
         if (grp.size() > 1 || groupable(*p.sub[grp[0]]))
             for (int i = 0; i < (int)grp.size(); ++i) {
                 const ladder_plan_s& q = *p.sub[grp[i]];
-                std::vector<int> u;
                 const std::vector<int> t = eri_entries(q.bps[0], q.nv, ladder::kEmuTileN,
-                                                       (size_t)q.nslices * 2 * ladder::align_up((size_t)q.nchol, 8),
-                                                       &u);
-                for (size_t j = 0; j + 1 < u.size(); ++j) hostu.push_back(cnt + u[j]);   // unit starts in the group
+                                                       (size_t)q.nslices * 2 * ladder::align_up((size_t)q.nchol, 8));
                 for (size_t j = 0; j < t.size(); j += 4) {
                     host.push_back(t[j]);
                     host.push_back(t[j + 1]);
@@ -745,8 +724,6 @@ int schedule_groups(ladder_plan_s& p, size_t cap) {
                     ++cnt;
                 }
             }
-        hostu.push_back(cnt);
-        p.group_ucnt.push_back((int)(hostu.size() - p.group_uoff.back()) - 1);
         p.group_ecnt.push_back(cnt);
     }
     if (p.d_group_entries) {
@@ -757,13 +734,6 @@ int schedule_groups(ladder_plan_s& p, size_t cap) {
         return LADDER_ERR_CUDA;
     if (!host.empty() &&
         cudaMemcpy(p.d_group_entries, host.data(), host.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
-        return LADDER_ERR_CUDA;
-    if (p.d_group_units) {
-        cudaFree(p.d_group_units);
-        p.d_group_units = nullptr;
-    }
-    if (cudaMalloc(&p.d_group_units, std::max<size_t>(16, hostu.size() * sizeof(int))) != cudaSuccess ||
-        cudaMemcpy(p.d_group_units, hostu.data(), hostu.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
         return LADDER_ERR_CUDA;
     p.groups = std::move(groups);
     p.sched_groups = (int)p.groups.size();
@@ -1077,10 +1047,9 @@ int ladder_apply_batched(ladder_plan_t plan, const double* const* L, const doubl
                 Rv.push_back(R[k]);
             }
             const int4* entries = static_cast<const int4*>(plan->d_group_entries) + plan->group_eoff[g];
-            const int* ustart = static_cast<const int*>(plan->d_group_units) + plan->group_uoff[g];
             const cudaError_t e = ladder::launch_emu_group(*plan, subs.data(), (int)subs.size(), wsv.data(),
                                                            Lv.data(), tv.data(), Rv.data(), entries,
-                                                           plan->group_ecnt[g], ustart, plan->group_ucnt[g], stream);
+                                                           plan->group_ecnt[g], stream);
             if (e != cudaSuccess) return LADDER_ERR_CUDA;
         }
         return LADDER_OK;

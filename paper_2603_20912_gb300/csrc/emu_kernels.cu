@@ -817,8 +817,7 @@ struct EriBatch {
     CUtensorMap tb[kMaxItems];  // L^T slices, 48-row boxes (B)
     EriItem item[kMaxItems];
     const int4* entries;        // (row tile, column tile, item, 0)
-    const int* ustart;          // first entry of every unit (a column tile's run of row tiles), then nentries
-    int nentries, nitems, nunits;
+    int nentries, nitems;
     unsigned* status;
     unsigned long long wait_ns; // limit of every bounded mbarrier wait (ns of the global timer)
 };
@@ -836,8 +835,8 @@ struct EriBatch {
 // (rank 0) full barrier; the leader issues the MMAs and its commits release the stage and
 // publish the accumulators in both CTAs; the epilogue warps of both CTAs release the
 // accumulators to the leader.  K = nchol runs in exact chunks (kbc stages each).  CTA pair c runs
-// the units c, c + pairs, ...: a unit is the run of entries (row tiles of one band) sharing one
-// column tile, so that tile's operand is reused from L2 by one CTA pair.
+// the entries c, c + pairs, ...: at any time the pairs work on neighbouring entries, which share
+// the band's row tiles and a few column tiles in L2.
 template <int S>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsEri, 1)
     eri_emu_kernel(const __grid_constant__ EriBatch B) {
@@ -880,8 +879,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsEri, 1)
         Ring ring;
         bool ok = true;
         const uint64_t keep = policy_evict_last();
-        for (int u = cluster; u < B.nunits && ok; u += nclusters)
-        for (int e = B.ustart[u]; e < B.ustart[u + 1] && ok; ++e) {
+        for (int e = cluster; e < B.nentries && ok; e += nclusters) {
             const int4 en = B.entries[e];
             const EriItem& p = B.item[en.z];
             const int nkb = (p.nchol + BK - 1) / BK;
@@ -909,8 +907,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsEri, 1)
         const uint32_t idesc = idesc_bf16_f32(2 * kEmuTile, kEmuTileN);
         bool ok = true;
         int it = 0;
-        for (int u = cluster; u < B.nunits && ok; u += nclusters)
-        for (int e = B.ustart[u]; e < B.ustart[u + 1] && ok; ++e) {
+        for (int e = cluster; e < B.nentries && ok; e += nclusters) {
             const EriItem& p = B.item[B.entries[e].z];
             const int nkb = (p.nchol + BK - 1) / BK;
             const int kb_per_chunk = *p.kbc;
@@ -946,8 +943,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsEri, 1)
         // With vp >= 48 the warp's 48 columns touch at most two b and two exponent groups, so
         // the exponent tables of a tile come down to ten loads per thread, issued before the
         // accumulators are waited for so that their latency hides behind the MMAs.
-        for (int u = cluster; u < B.nunits && ok; u += nclusters)
-        for (int e = B.ustart[u]; e < B.ustart[u + 1] && ok; ++e) {
+        for (int e = cluster; e < B.nentries && ok; e += nclusters) {
             const int4 en = B.entries[e];
             const EriItem& p = B.item[en.z];
             const int Ncols = p.nb * p.vp;
@@ -1165,7 +1161,9 @@ struct LadItem {
     int M, N, n_mt, n_nt, n_ch, kb_per_chunk, nkb;
     int swap;                // 0: rows m = pairs, columns n = (i,j); 1: rows m = (i,j), columns n = pairs
     int no2;
+    int gm;                  // row tiles per group of the tile order (see tile_coords)
     long long ubeg, units;   // first unit of this item in the launch, and its unit count
+    long long tbeg, ntiles;  // first tile of this item in the launch, and its tile count
     unsigned long long* rp;  // int64 fixed-point accumulator [npairs][no2]
 };
 
@@ -1174,6 +1172,7 @@ struct LadBatch {
     CUtensorMap tb[kMaxItems];  // B: V planes of the item
     LadItem item[kMaxItems];
     long long units;            // all items' units
+    long long tiles;            // all items' tiles
     int nitems, BN;
     unsigned* status;
     unsigned long long wait_ns; // limit of every bounded mbarrier wait (ns of the global timer)
@@ -1185,6 +1184,69 @@ struct ItemCursor {
     __device__ __forceinline__ int seek(const LadBatch& B, long long u) {
         while (k + 1 < B.nitems && u >= B.item[k + 1].ubeg) ++k;
         return k;
+    }
+};
+
+// (row tile, column tile) of tile `tile` of an item.  Tiles run in groups of gm row tiles: within
+// a group, down the gm row tiles of a column tile, then to the next column tile, so that the tiles
+// one wave of workers takes at the same time share gm row tiles' A chunks and P / gm column tiles'
+// B chunks in L2.
+__device__ __forceinline__ void tile_coords(const LadItem& p, long long tile, int& mt, int& nt) {
+    if (p.gm <= 1) {
+        nt = (int)(tile % p.n_nt);
+        mt = (int)(tile / p.n_nt);
+        return;
+    }
+    const long long per = (long long)p.gm * p.n_nt;
+    const long long g = tile / per;
+    const int first = (int)(g * p.gm);
+    const int rows = min(p.gm, p.n_mt - first);
+    const long long local = tile - g * per;
+    mt = first + (int)(local % rows);
+    nt = (int)(local / rows);
+}
+
+// The units one worker (a CTA, or a CTA pair) of P runs, in increasing order: first whole tiles,
+// tile w, w + P, w + 2P, ... up to the last full wave of P tiles, every K chunk of a tile in turn,
+// so that the P workers of a wave move through K together and share each chunk of their operands
+// in L2; then an even share of the units of the tiles left over (stream-K), which keeps the load
+// balanced.  `last` marks the last unit of the worker's stream-K share (its sums are flushed).
+struct UnitSeq {
+    long long t = 0, full = 0, P = 1, tail_u = 0, tail_end = 0;
+    int k = 0, ch = 0;
+    bool in_tail = false;
+    __device__ __forceinline__ void init(const LadBatch& B, long long w, long long workers) {
+        P = workers;
+        full = B.tiles / P * P;
+        t = w;
+        in_tail = t >= full;
+        long long tu0 = B.units;   // first unit of tile `full`
+        for (int i = 0; i < B.nitems; ++i)
+            if (full < B.item[i].tbeg + B.item[i].ntiles) {
+                tu0 = B.item[i].ubeg + (full - B.item[i].tbeg) * B.item[i].n_ch;
+                break;
+            }
+        const long long n = B.units - tu0;
+        tail_u = tu0 + n * w / P;
+        tail_end = tu0 + n * (w + 1) / P;
+    }
+    __device__ __forceinline__ bool next(const LadBatch& B, long long& u, bool& last) {
+        if (!in_tail) {
+            while (t >= B.item[k].tbeg + B.item[k].ntiles) ++k;
+            const LadItem& it = B.item[k];
+            u = it.ubeg + (t - it.tbeg) * it.n_ch + ch;
+            last = false;
+            if (++ch == it.n_ch) {
+                ch = 0;
+                t += P;
+                in_tail = t >= full;
+            }
+            return true;
+        }
+        if (tail_u >= tail_end) return false;
+        u = tail_u++;
+        last = tail_u == tail_end;
+        return true;
     }
 };
 
@@ -1227,7 +1289,6 @@ __global__ void __launch_bounds__(kThreadsTC, 1) ladder_emu_kernel(const __grid_
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_base;
-    const long long u0 = B.units * blockIdx.x / gridDim.x, u1 = B.units * (blockIdx.x + 1) / gridDim.x;
 
     if (warp == 0 && lane == 0) {
         // T slices (A) are re-read for every pair tile and stay in L2; the V planes (B) stream.
@@ -1237,13 +1298,18 @@ __global__ void __launch_bounds__(kThreadsTC, 1) ladder_emu_kernel(const __grid_
         bool ok = true;
         const uint32_t bytes = (uint32_t)S * (kEmuTile + B.BN) * BK * 2;
         ItemCursor cur;
-        for (long long u = u0; u < u1 && ok; ++u) {
+        UnitSeq seq;
+        seq.init(B, blockIdx.x, gridDim.x);
+        long long u;
+        bool last_u;
+        while (ok && seq.next(B, u, last_u)) {
             const int ik = cur.seek(B, u);
             const LadItem& p = B.item[ik];
             const long long ul = u - p.ubeg;
             const int ch = (int)(ul % p.n_ch);
             const long long tile = ul / p.n_ch;
-            const int nt = (int)(tile % p.n_nt), mt = (int)(tile / p.n_nt);
+            int mt, nt;
+                tile_coords(p, tile, mt, nt);
             const int kb1 = min((ch + 1) * p.kb_per_chunk, p.nkb);
             for (int kb = ch * p.kb_per_chunk; kb < kb1 && ok; ++kb) {
                 if (!(ok = mbar_wait(&empty[ring.stage], ring.phase ^ 1u, B.status, kStatusTimeout, B.wait_ns))) break;
@@ -1263,7 +1329,11 @@ __global__ void __launch_bounds__(kThreadsTC, 1) ladder_emu_kernel(const __grid_
         bool ok = true;
         int it = 0;
         ItemCursor cur;
-        for (long long u = u0; u < u1 && ok; ++u, ++it) {
+        UnitSeq seq;
+        seq.init(B, blockIdx.x, gridDim.x);
+        long long u;
+        bool last_u;
+        for (; ok && seq.next(B, u, last_u); ++it) {
             const LadItem& p = B.item[cur.seek(B, u)];
             const int ch = (int)((u - p.ubeg) % p.n_ch);
             if (!(ok = mbar_wait(&acc_empty, (uint32_t)(it & 1) ^ 1u, B.status, kStatusTimeout, B.wait_ns))) break;
@@ -1293,7 +1363,11 @@ __global__ void __launch_bounds__(kThreadsTC, 1) ladder_emu_kernel(const __grid_
             for (int k = 0; k < 16; ++k) run[i][k] = 0;
         int it = 0;
         ItemCursor cur;
-        for (long long u = u0; u < u1; ++u, ++it) {
+        UnitSeq seq;
+        seq.init(B, blockIdx.x, gridDim.x);
+        long long u;
+        bool last_u;
+        for (; seq.next(B, u, last_u); ++it) {
             if (!mbar_wait(&acc_full, (uint32_t)(it & 1), B.status, kStatusTimeout, B.wait_ns)) break;
             tc_fence_after();
 #pragma unroll
@@ -1326,8 +1400,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1) ladder_emu_kernel(const __grid_
             const int ik = cur.seek(B, u);
             const LadItem& p = B.item[ik];
             const long long tile = (u - p.ubeg) / p.n_ch;
-            if (u + 1 == u1 || tile_ends(B, ik, u)) {
-                const int nt = (int)(tile % p.n_nt), mt = (int)(tile / p.n_nt);
+            if (last_u || tile_ends(B, ik, u)) {
+                int mt, nt;
+                tile_coords(p, tile, mt, nt);
                 const int m = mt * kEmuTile + 32 * q + lane;
 #pragma unroll
                 for (int i = 0; i < 3; ++i) {
@@ -1373,7 +1448,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t rank = cluster_ctarank();
     const long long cluster = blockIdx.x >> 1, nclusters = gridDim.x >> 1;
-    const long long u0 = B.units * cluster / nclusters, u1 = B.units * (cluster + 1) / nclusters;
     if (threadIdx.x == 0) {
         for (int i = 0; i < STAGES; ++i) {
             mbar_init(&full[i], 1);
@@ -1401,13 +1475,18 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
         bool ok = true;
         const uint64_t keep = policy_evict_last(), stream = policy_evict_first();
         ItemCursor cur;
-        for (long long u = u0; u < u1 && ok; ++u) {
+        UnitSeq seq;
+        seq.init(B, cluster, nclusters);
+        long long u;
+        bool last_u;
+        while (ok && seq.next(B, u, last_u)) {
             const int ik = cur.seek(B, u);
             const LadItem& p = B.item[ik];
             const long long ul = u - p.ubeg;
             const int ch = (int)(ul % p.n_ch);
             const long long tile = ul / p.n_ch;
-            const int nt = (int)(tile % p.n_nt), mt = (int)(tile / p.n_nt);
+            int mt, nt;
+                tile_coords(p, tile, mt, nt);
             const int arow = mt * 2 * kEmuTile + kEmuTile * (int)rank;
             const int brow = nt * kEmuTileN + (kEmuTileN / 2) * (int)rank;
             const int kb1 = min((ch + 1) * p.kb_per_chunk, p.nkb);
@@ -1428,7 +1507,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
         bool ok = true;
         int it = 0;
         ItemCursor cur;
-        for (long long u = u0; u < u1 && ok; ++u, ++it) {
+        UnitSeq seq;
+        seq.init(B, cluster, nclusters);
+        long long u;
+        bool last_u;
+        for (; ok && seq.next(B, u, last_u); ++it) {
             const LadItem& p = B.item[cur.seek(B, u)];
             const int ch = (int)((u - p.ubeg) % p.n_ch);
             if (!(ok = mbar_wait(&acc_empty, (uint32_t)(it & 1) ^ 1u, B.status, kStatusTimeout, B.wait_ns))) break;
@@ -1458,7 +1541,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
         int it = 0;
         bool ok = true;
         ItemCursor cur;
-        for (long long u = u0; u < u1; ++u, ++it) {
+        UnitSeq seq;
+        seq.init(B, cluster, nclusters);
+        long long u;
+        bool last_u;
+        for (; seq.next(B, u, last_u); ++it) {
             if (!(ok = mbar_wait(&acc_full, (uint32_t)(it & 1), B.status, kStatusTimeout, B.wait_ns))) break;
             tc_fence_after();
 #pragma unroll
@@ -1487,8 +1574,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
             const int ik = cur.seek(B, u);
             const LadItem& p = B.item[ik];
             const long long tile = (u - p.ubeg) / p.n_ch;
-            if (u + 1 == u1 || tile_ends(B, ik, u)) {
-                const int nt = (int)(tile % p.n_nt), mt = (int)(tile / p.n_nt);
+            if (last_u || tile_ends(B, ik, u)) {
+                int mt, nt;
+                tile_coords(p, tile, mt, nt);
                 const int m = mt * 2 * kEmuTile + kEmuTile * (int)rank + 32 * q + lane;  // (i,j)
 #pragma unroll
                 for (int cc = 0; cc < 3; ++cc)
@@ -1681,7 +1769,7 @@ bool eri_item(const ladder_plan_s& p, const BlockPair& bp, void* ws, EriItem* it
 // others).
 template <int S>
 void launch_eri_batch(const EriBatch& eb, int max_clusters, cudaStream_t s) {
-    const int clusters = std::max(1, std::min(eb.nunits, max_clusters));
+    const int clusters = std::max(1, std::min(eb.nentries, max_clusters));
     eri_emu_kernel<S><<<2 * clusters, kThreadsEri, eri_smem_bytes_for(S), s>>>(eb);
 }
 
@@ -1711,7 +1799,7 @@ inline int ladder_bn(const ladder_plan_s& p, bool pair) { return pair ? kEmuTile
 
 template <int S>
 bool ladder_item(const ladder_plan_s& p, const BlockPair& bp, void* ws, long long ubeg, LadItem* it, CUtensorMap* ta,
-                 CUtensorMap* tb) {
+                 CUtensorMap* tb, long long tbeg = 0) {
     constexpr int BK = bk_for(S);
     const bool pair = ladder_on_pairs(p);
     const int bn = ladder_bn(p, pair);
@@ -1735,6 +1823,9 @@ bool ladder_item(const ladder_plan_s& p, const BlockPair& bp, void* ws, long lon
     x.n_ch = (x.nkb + x.kb_per_chunk - 1) / x.kb_per_chunk;
     x.units = (long long)x.n_mt * x.n_nt * x.n_ch;
     x.ubeg = ubeg;
+    x.ntiles = (long long)x.n_mt * x.n_nt;
+    x.tbeg = tbeg;
+    x.gm = x.n_mt < 4 ? x.n_mt : 4;   // waves of P tiles: 4 row tiles x P/4 column tiles
     x.rp = at<unsigned long long>(ws, p.ws.rp_int);
     *it = x;
     return true;
@@ -1756,7 +1847,7 @@ void launch_ladder_batch(const LadBatch& lb, bool on_pairs, int max_pair_cluster
 // Ladder work item X (plus) or Y (minus) of the symmetric/antisymmetric form of one block pair.
 template <int S>
 bool ladder_item_pm(const ladder_plan_s& p, const BlockPair& bp, void* ws, long long ubeg, bool plus, LadItem* it,
-                    CUtensorMap* ta, CUtensorMap* tb) {
+                    CUtensorMap* ta, CUtensorMap* tb, long long tbeg = 0) {
     constexpr int BK = bk_for(S);
     const PmDims d = pm_dims(p.no, p.nv);
     const int rows = plus ? d.np : d.nm;
@@ -1780,6 +1871,9 @@ bool ladder_item_pm(const ladder_plan_s& p, const BlockPair& bp, void* ws, long 
     x.n_ch = (x.nkb + x.kb_per_chunk - 1) / x.kb_per_chunk;
     x.units = (long long)x.n_mt * x.n_nt * x.n_ch;
     x.ubeg = ubeg;
+    x.ntiles = (long long)x.n_mt * x.n_nt;
+    x.tbeg = tbeg;
+    x.gm = x.n_mt < 4 ? x.n_mt : 4;   // waves of P tiles: 4 row tiles x P/4 column tiles
     x.rp = at<unsigned long long>(ws, plus ? p.ws.rpx : p.ws.rpy);
     *it = x;
     return true;
@@ -1803,8 +1897,6 @@ cudaError_t block_pm_impl(const ladder_plan_s& p, const BlockPair& bp, const dou
     eb.nitems = 1;
     eb.nentries = bp.ntiles;
     eb.entries = reinterpret_cast<const int4*>(table + bp.tiles_off);
-    eb.nunits = bp.nunits;
-    eb.ustart = reinterpret_cast<const int*>(p.d_tables) + bp.units_off;
     eb.status = p.d_status;
     eb.wait_ns = p.wait_ns;
     const int vp = padded_vp(p.nv);
@@ -1852,6 +1944,7 @@ cudaError_t block_pm_impl(const ladder_plan_s& p, const BlockPair& bp, const dou
             return cudaErrorInvalidValue;
         lb.BN = ladder_bn(p, lb.item[0].M > kEmuTile);
         lb.units = lb.item[0].units;
+        lb.tiles = lb.item[0].ntiles;
         LaunchTimer tm(p, s, LADDER_KERNEL_LADDER);
         launch_ladder_batch<S>(lb, lb.item[0].M > kEmuTile, fit, p.num_sms, s);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -1883,8 +1976,6 @@ cudaError_t block_impl(const ladder_plan_s& p, const BlockPair& bp, const double
     eb.nitems = 1;
     eb.nentries = bp.ntiles;
     eb.entries = reinterpret_cast<const int4*>(table + bp.tiles_off);
-    eb.nunits = bp.nunits;
-    eb.ustart = reinterpret_cast<const int*>(p.d_tables) + bp.units_off;
     eb.status = p.d_status;
     eb.wait_ns = p.wait_ns;
     if (!eri_item<S>(p, bp, ws, &eb.item[0], &eb.ta[0], &eb.tb[0])) return cudaErrorInvalidValue;
@@ -1904,6 +1995,7 @@ cudaError_t block_impl(const ladder_plan_s& p, const BlockPair& bp, const double
     lb.wait_ns = p.wait_ns;
     if (!ladder_item<S>(p, bp, ws, 0, &lb.item[0], &lb.ta[0], &lb.tb[0])) return cudaErrorInvalidValue;
     lb.units = lb.item[0].units;
+    lb.tiles = lb.item[0].ntiles;
     {
         LaunchTimer tm(p, s, LADDER_KERNEL_LADDER);
         launch_ladder_batch<S>(lb, ladder_on_pairs(p), p.pair_clusters > 0 ? p.pair_clusters : p.num_sms / 2,
@@ -1929,7 +2021,7 @@ cudaError_t block_impl(const ladder_plan_s& p, const BlockPair& bp, const double
 template <int S>
 cudaError_t group_impl(const ladder_plan_s& parent, const ladder_plan_s* const* subs, int n, void* const* ws,
                        const double* const* L, const double* const* t2, double* const* R, const int4* entries,
-                       int nentries, const int* ustart, int nunits, cudaStream_t s) {
+                       int nentries, cudaStream_t s) {
     if (n < 1 || n > kMaxItems) return cudaErrorInvalidValue;
     cudaError_t e;
     for (int k = 0; k < n; ++k) {
@@ -1945,8 +2037,6 @@ cudaError_t group_impl(const ladder_plan_s& parent, const ladder_plan_s* const* 
     eb.nitems = n;
     eb.nentries = nentries;
     eb.entries = entries;
-    eb.nunits = nunits;
-    eb.ustart = ustart;
     eb.status = parent.d_status;
     eb.wait_ns = parent.wait_ns;
     for (int k = 0; k < n; ++k)
@@ -1966,17 +2056,20 @@ cudaError_t group_impl(const ladder_plan_s& parent, const ladder_plan_s* const* 
         lb.BN = shape == 1 ? kEmuTileN : parent.lad_bn;   // every single-CTA item of the group uses it
         lb.status = parent.d_status;
         lb.wait_ns = parent.wait_ns;
-        long long units = 0;
+        long long units = 0, tiles = 0;
         for (int k = 0; k < n; ++k) {
             if ((int)ladder_on_pairs(*subs[k]) != shape) continue;
             LadItem* it = &lb.item[lb.nitems];
-            if (!ladder_item<S>(*subs[k], subs[k]->bps[0], ws[k], units, it, &lb.ta[lb.nitems], &lb.tb[lb.nitems]))
+            if (!ladder_item<S>(*subs[k], subs[k]->bps[0], ws[k], units, it, &lb.ta[lb.nitems], &lb.tb[lb.nitems],
+                                tiles))
                 return cudaErrorInvalidValue;
             units += it->units;
+            tiles += it->ntiles;
             ++lb.nitems;
         }
         if (lb.nitems == 0) continue;
         lb.units = units;
+        lb.tiles = tiles;
         LaunchTimer tm(parent, s, LADDER_KERNEL_LADDER);
         launch_ladder_batch<S>(lb, shape == 1, pair_fit, subs[0]->num_sms, s);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -2065,12 +2158,12 @@ cudaError_t launch_emu_prep(const ladder_plan_s& p, const double* L, const doubl
 
 cudaError_t launch_emu_group(const ladder_plan_s& parent, const ladder_plan_s* const* subs, int n, void* const* ws,
                              const double* const* L, const double* const* t2, double* const* R, const int4* entries,
-                             int nentries, const int* ustart, int nunits, cudaStream_t s) {
+                             int nentries, cudaStream_t s) {
     switch (parent.nslices) {
-        case 5: return group_impl<5>(parent, subs, n, ws, L, t2, R, entries, nentries, ustart, nunits, s);
-        case 6: return group_impl<6>(parent, subs, n, ws, L, t2, R, entries, nentries, ustart, nunits, s);
-        case 7: return group_impl<7>(parent, subs, n, ws, L, t2, R, entries, nentries, ustart, nunits, s);
-        case 8: return group_impl<8>(parent, subs, n, ws, L, t2, R, entries, nentries, ustart, nunits, s);
+        case 5: return group_impl<5>(parent, subs, n, ws, L, t2, R, entries, nentries, s);
+        case 6: return group_impl<6>(parent, subs, n, ws, L, t2, R, entries, nentries, s);
+        case 7: return group_impl<7>(parent, subs, n, ws, L, t2, R, entries, nentries, s);
+        case 8: return group_impl<8>(parent, subs, n, ws, L, t2, R, entries, nentries, s);
         default: return cudaErrorInvalidValue;
     }
 }

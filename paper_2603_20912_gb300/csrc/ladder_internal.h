@@ -50,8 +50,6 @@ struct BlockPair {
     size_t tiles_off = 0;  // emulated path: offset (in int2) of the ERI entries (int4: rt, qt, 0, 0)
     int ntiles = 0;        // emulated path: number of ERI entries (one 2-CTA cluster each)
     size_t chunks_off = 0; // emulated path: offset (in int2) of the ERI row chunks (first L^T row, rows)
-    size_t units_off = 0;  // emulated path: offset (in int) of the first entries of the ERI units (+ count)
-    int nunits = 0;        // emulated path: number of ERI units (runs of entries sharing a column tile)
 };
 
 // Workspace layout of one plan (byte offsets from the workspace base).
@@ -176,10 +174,7 @@ struct ladder_plan_s {
     std::vector<size_t> inst_off;             // workspace offset of each instance in the grouped schedule
     std::vector<size_t> group_eoff;           // first ERI entry (int4) of each group in d_group_entries
     std::vector<int> group_ecnt;              // ERI entries of each group
-    std::vector<size_t> group_uoff;           // first unit start (int) of each group in d_group_units
-    std::vector<int> group_ucnt;              // ERI units of each group
     void* d_group_entries = nullptr;
-    void* d_group_units = nullptr;            // per group: unit starts (entry index in the group), then the count
 };
 
 namespace ladder {
@@ -223,7 +218,7 @@ cudaError_t launch_emu_block(const ladder_plan_s& p, const BlockPair& bp, const 
 // the group's ERI tiles with z = position of the instance in the group).
 cudaError_t launch_emu_group(const ladder_plan_s& parent, const ladder_plan_s* const* subs, int n, void* const* ws,
                              const double* const* L, const double* const* t2, double* const* R, const int4* entries,
-                             int nentries, const int* ustart, int nunits, cudaStream_t s);
+                             int nentries, cudaStream_t s);
 int emu_max_group();  // most instances in one group
 int emu_eri_stage_k(int nslices);  // K columns per pipeline stage of the emulated ERI
 bool emu_supported(int no, int nv, int nchol, int nslices);
