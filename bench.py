@@ -496,11 +496,36 @@ def kernel_times(lad, plan, steps):
     kms, counts = {}, {}
     for kind, name in [(lad.LADDER_KERNEL_PREP, "prep"), (lad.LADDER_KERNEL_ERI, "eri"),
                        (lad.LADDER_KERNEL_LADDER, "ladder"), (lad.LADDER_KERNEL_FINISH, "finish"),
-                       (lad.LADDER_KERNEL_COMBINE, "combine")]:
+                       (lad.LADDER_KERNEL_COMBINE, "combine"), (lad.LADDER_KERNEL_FACT_W, "fact_w"),
+                       (lad.LADDER_KERNEL_FACT_R, "fact_r"), (lad.LADDER_KERNEL_FUSED, "fused")]:
         ms, n = plan.timing(kind)
         kms[name] = ms
         counts[name] = n
     return kms, counts
+
+
+FP64_PATHS = {"eri": 0, "fused": 2}
+
+
+def set_fp64_path(lad, plan, args):
+    """Hold an FP64 plan to the path --fp64-path names (auto: the planner's choice)."""
+    if args.fp64_path != "auto":
+        plan.set_path(FP64_PATHS[args.fp64_path])
+
+
+def fp64_roofline(lad, plan, cfg, kms, steps, dgemm):
+    """DMMA roofline of the kernel that carries an FP64 call's flops: the ERI GEMM of the
+    rebuild order (its 2 X v^2 p flops), or the fused kernel (all of the call's packed flops)."""
+    src = "torch float64 matmul 8192^3 measured in this run (cuBLAS DGEMM)"
+    if plan.path() == lad.LADDER_PATH_FUSED:
+        flops, ms, kernel = lad.ladder_flops(cfg.no, cfg.nv, cfg.nchol), kms.get("fused", 0.0), \
+            "ladder_fused_fp64_kernel (DMMA m8n8k4 f64, ERI chunks contracted on chip)"
+    else:
+        flops, ms, kernel = 2.0 * cfg.nchol * cfg.nv * cfg.nv * (cfg.nv * (cfg.nv + 1) // 2), kms.get("eri", 0.0), \
+            "eri_fp64_kernel (DMMA m8n8k4 f64)"
+    tf = flops * steps / (ms * 1e-3) / 1e12 if ms > 0 else None
+    return {"bound": "tensor", "kernel": kernel, "achieved": tf, "peak": dgemm, "unit": "TFLOP/s",
+            "frac": tf / dgemm if tf else None, "peak_source": src}
 
 
 def run_fp64_compare(args, cfg, lad, Ld, td, local, stream):
@@ -517,6 +542,7 @@ def run_fp64_compare(args, cfg, lad, Ld, td, local, stream):
     warm.close()
     torch.cuda.empty_cache()
     plan = lad.ladder_plan(cfg.no, cfg.nv, cfg.nchol, lad.LADDER_FP64, device=local)
+    set_fp64_path(lad, plan, args)
     ws = plan.workspace()
     desc = plan.describe()
     R = torch.zeros_like(td)
@@ -538,16 +564,12 @@ def run_fp64_compare(args, cfg, lad, Ld, td, local, stream):
     plan.set_timing(False)
     assert plan.last_status() == lad.LADDER_OK
     E = lad.ladder_energy(plan, td, R)
-    eri_flops = 2.0 * cfg.nchol * cfg.nv * cfg.nv * (cfg.nv * (cfg.nv + 1) // 2)
-    eri_tf = eri_flops * args.fp64_steps / (kms["eri"] * 1e-3) / 1e12 if kms["eri"] > 0 else None
-    rec = {"ms_per_call": ms, "tflops": lad.ladder_flops(cfg.no, cfg.nv, cfg.nchol) / (ms * 1e-3) / 1e12,
+    rec = {"ms_per_call": ms, "path": {0: "eri", 1: "factorised", 2: "fused"}[plan.path()], "tflops": lad.ladder_flops(cfg.no, cfg.nv, cfg.nchol) / (ms * 1e-3) / 1e12,
            "steps": args.fp64_steps, "warmup": "one call on a no=5 nv=19 nchol=72 shape (loads the kernels)",
            "kernel_ms_per_call": {k: v / args.fp64_steps for k, v in kms.items()},
            "gpu_launches": sum(counts.values()), "n_a": desc["n_a"], "n_b": desc["n_b"],
            "block_pairs": desc["n_block_pairs"], "E_L": E,
-           "roofline": {"bound": "tensor", "kernel": "eri_fp64_kernel (DMMA m8n8k4 f64)", "achieved": eri_tf,
-                        "peak": dgemm, "unit": "TFLOP/s", "frac": eri_tf / dgemm if eri_tf else None,
-                        "peak_source": "torch float64 matmul 8192^3 measured in this run (cuBLAS DGEMM)"},
+           "roofline": fp64_roofline(lad, plan, cfg, kms, args.fp64_steps, dgemm),
            "clocks": clocks}
     del ws
     plan.close()
@@ -593,6 +615,8 @@ def run_single(args, cfg):
                            ws_budget_bytes=budget, device=local)
     if args.form != "auto":
         plan.set_form(1 if args.form == "pm" else 0)
+    if precision == lad.LADDER_FP64:
+        set_fp64_path(lad, plan, args)
     if shard:
         plan.shard(rank, world)
     form_used = "pm" if plan.form() == 1 else "plain"
@@ -658,13 +682,11 @@ def run_single(args, cfg):
                 "executed_slice_products": slice_products}
         dtype = "f64-emulated(bf16 slices)"
     else:
-        achieved = (eri_flops_call * args.steps / (kms["eri"] * 1e-3) / 1e12
-                    if kms["eri"] > 0 and eri_flops_call else None)
         dgemm = measure_dgemm_tflops()
-        roof = {"bound": "tensor", "achieved": achieved, "peak": dgemm, "unit": "TFLOP/s",
-                "frac": (achieved / dgemm) if achieved else None, "traffic": traffic,
-                "kernel": "eri_fp64_kernel (DMMA)",
-                "peak_source": "torch float64 matmul 8192^3 measured in this run (cuBLAS DGEMM)"}
+        roof = fp64_roofline(lad, plan, cfg, kms, args.steps, dgemm)
+        if shard:
+            roof["achieved"] = roof["frac"] = None   # a shard's share: no per-call flop count here
+        roof["traffic"] = traffic if plan.path() == lad.LADDER_PATH_ERI else None
         dtype = "f64"
     if traffic_src:
         roof["traffic_source"] = traffic_src
@@ -929,6 +951,8 @@ def main():
     ap.add_argument("--fp64", default="auto", choices=["auto", "on", "off"],
                     help="also time the native FP64 path on the workload (auto: emulated runs on one GPU)")
     ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--fp64-path", default="auto", choices=["auto", "eri", "fused"],
+                    help="FP64 evaluation order (auto: the planner's choice)")
     ap.add_argument("--batched", default="auto", choices=["auto", "on", "off"],
                     help="also time the 24-instance uneven batch (auto: emulated default runs on one GPU)")
     ap.add_argument("--device-inputs", action="store_true",

@@ -140,15 +140,28 @@ int ladder_form_model(int no, int nv, int nchol, int nslices);
  *     (R_ji = R_ij^T from t_ji^cd = t_ij^dc), as two FP64 DMMA GEMMs per batch of Cholesky
  *     vectors through a workspace W[o(o+1)/2][nv][batch][nv]: 4 nchol o(o+1)/2 nv^3 flops.
  *     Native FP64 plans only (LADDER_ERR_UNSUPPORTED for the emulated path).
- * ladder_plan picks, for an FP64 plan, the path with the fewer modelled flops (the factorised one
- * must be 1.25x cheaper) when its workspace fits; emulated plans use path 0.  Forcing a blocking
- * (ladder_plan_set_blocks) or sharding (ladder_plan_shard) returns a plan to path 0.
- * Returns LADDER_OK, LADDER_ERR_ARG, LADDER_ERR_UNSUPPORTED, LADDER_ERR_BUDGET (the batch of one
- * Cholesky vector does not fit) or LADDER_ERR_CUDA.  ladder_plan_get_path: the plan's path, -1 for
- * NULL.  ladder_path_model: host only, the path ladder_plan would pick for this shape and
- * precision before the workspace check (0 or 1; -1 for invalid arguments).
+ *   LADDER_PATH_FUSED (2): the rebuild order with the two C-split steps of a batch kept on the
+ *     chip (Sec. "An Asymmetric and Dynamic Splitting Protocol", Table 1, steps 0 and 1): one
+ *     kernel per block pair builds (ac|bd) for a tile of 4 x 4 pairs (a, b) one 16 x 16 chunk of
+ *     (c, d) at a time into shared memory and contracts each chunk with t2 at once into
+ *     accumulators for all no^2 amplitude rows held in registers; V is never written.  Same
+ *     flops as path 0 (plus the pairs a > b of the tiles that straddle the diagonal), no
+ *     workspace beyond the minimum (ladder_workspace_bytes returns 256), one block pair of all
+ *     pairs unless the plan is a shard.  Native FP64 plans with no^2 <= 1024 only
+ *     (LADDER_ERR_UNSUPPORTED otherwise).
+ * ladder_plan picks, for an FP64 plan, the factorised path when it needs 1.25x fewer flops and its
+ * workspace fits, else the fused path when no^2 <= 1024 (same flops as path 0 without the V round
+ * trip), else path 0; and the fused path whenever no workspace of the others fits.  Emulated
+ * plans use path 0.  Forcing a blocking (ladder_plan_set_blocks) returns a
+ * plan to path 0; sharding (ladder_plan_shard) returns a factorised plan to path 0 and splits the
+ * block pairs of a fused plan.
+ * Returns LADDER_OK, LADDER_ERR_ARG, LADDER_ERR_UNSUPPORTED, LADDER_ERR_BUDGET (path 1: the batch
+ * of one Cholesky vector does not fit; path 0: no blocking fits) or LADDER_ERR_CUDA; on an error
+ * the plan keeps its path.  ladder_plan_get_path: the plan's path, -1 for NULL.
+ * ladder_path_model: host only, the path ladder_plan would pick for this shape and precision
+ * before the workspace check (0, 1 or 2; -1 for invalid arguments).
  */
-enum { LADDER_PATH_ERI = 0, LADDER_PATH_FACTORISED = 1 };
+enum { LADDER_PATH_ERI = 0, LADDER_PATH_FACTORISED = 1, LADDER_PATH_FUSED = 2 };
 int ladder_plan_set_path(ladder_plan_t plan, int path);
 int ladder_plan_get_path(ladder_plan_t plan);
 int ladder_path_model(int no, int nv, int nchol, int precision);
@@ -388,7 +401,8 @@ enum {
     LADDER_KERNEL_COMBINE = 4,  /* V' and V'' from V (symmetric/antisymmetric form)   */
     LADDER_KERNEL_FACT_W = 5,   /* factorised path: W = L_P T_ij                      */
     LADDER_KERNEL_FACT_R = 6,   /* factorised path: R_ij += W L_P^T                   */
-    LADDER_KERNEL_CLASSES = 7
+    LADDER_KERNEL_FUSED = 7,    /* fused path: ERI chunks contracted on chip          */
+    LADDER_KERNEL_CLASSES = 8
 };
 int ladder_plan_set_timing(ladder_plan_t plan, int enable);
 int ladder_plan_timing(ladder_plan_t plan, int kernel_class, float* total_ms, int* launches, int reset);

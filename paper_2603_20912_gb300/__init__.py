@@ -39,9 +39,11 @@ LADDER_KERNEL_FINISH = 3
 LADDER_KERNEL_COMBINE = 4
 LADDER_KERNEL_FACT_W = 5
 LADDER_KERNEL_FACT_R = 6
+LADDER_KERNEL_FUSED = 7
 
 LADDER_PATH_ERI = 0
 LADDER_PATH_FACTORISED = 1
+LADDER_PATH_FUSED = 2
 
 # LADDER_CHECKED_LIBRARY=1 loads the index-checked build (build.build(check=True)) instead.
 LIB_PATH = _build_mod.LIB_CHECK if os.environ.get("LADDER_CHECKED_LIBRARY") == "1" else _build_mod.LIB

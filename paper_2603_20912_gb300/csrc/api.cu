@@ -99,6 +99,8 @@ std::vector<BlockPair> enumerate_blocks(int nv, int na, int nb) {
     return out;
 }
 
+int apply_blocking(ladder_plan_s& p, int na, int nb);
+
 ladder::WsLayout layout_for(const ladder_plan_s& p, long long max_pairs) {
     using ladder::align_up;
     using ladder::kAlign;
@@ -109,6 +111,8 @@ ladder::WsLayout layout_for(const ladder_plan_s& p, long long max_pairs) {
     if (p.path == 1) {
         const size_t npij = (size_t)p.no * (p.no + 1) / 2;
         w.w_blk = take(npij * nv2 * (size_t)p.fact_pb * sizeof(double));
+    } else if (p.path == 2) {
+        // fused path: (ac|bd) stays on the chip, no workspace
     } else if (p.precision == LADDER_FP64) {
         w.v_blk = take((size_t)max_pairs * nv2 * sizeof(double));
     } else {
@@ -211,7 +215,10 @@ double model_time(const ladder_plan_s& p, const std::vector<BlockPair>& bps) {
 // R_ij = sum_P L_P T_ij L_P^T costs 4 X v^3 per amplitude pair, o(o+1)/2 pairs with i <= j.
 // Both run on the same FP64 DMMA tiles, so the flop counts compare directly; the factorised
 // order is taken when it needs 1.25x fewer flops (it streams a W batch through HBM per
-// Cholesky batch).  The emulated path has only the rebuild order.
+// Cholesky batch).  Otherwise an FP64 plan takes the rebuild order fused on the chip (path 2:
+// the same flops, no V round trip through HBM and no workspace, measured faster than the
+// unfused rebuild at every shape it was timed on) when its accumulators hold the no^2
+// amplitude rows.  The emulated path has only the rebuild order through HBM.
 double eri_path_flops(int no, int nv, int nchol) {
     const double p = 0.5 * (double)nv * (nv + 1), v2 = (double)nv * nv;
     return 2.0 * nchol * v2 * p + 2.0 * (double)no * no * v2 * p;
@@ -221,7 +228,8 @@ double fact_path_flops(int no, int nv, int nchol) {
 }
 int auto_path(int no, int nv, int nchol, int precision) {
     if (precision != LADDER_FP64) return 0;
-    return 1.25 * fact_path_flops(no, nv, nchol) < eri_path_flops(no, nv, nchol) ? 1 : 0;
+    if (1.25 * fact_path_flops(no, nv, nchol) < eri_path_flops(no, nv, nchol)) return 1;
+    return (long long)no * no <= ladder::fused_fp64_max_rows() ? 2 : 0;
 }
 
 // Cholesky vectors per batch of the factorised path: as many as the budget holds (W is
@@ -245,6 +253,26 @@ int use_factorised(ladder_plan_s& p) {
     }
     p.ws = w;
     return LADDER_OK;
+}
+
+// Fused path (FP64): the plan's block pairs -- one block pair of all pairs unless the plan is a
+// shard -- walked by the fused ERI -> ladder kernel, which needs no workspace; its accumulators
+// hold no^2 <= fused_fp64_max_rows() amplitude rows (LADDER_ERR_UNSUPPORTED otherwise).
+int use_fused(ladder_plan_s& p) {
+    if (p.precision != LADDER_FP64 || (long long)p.no * p.no > ladder::fused_fp64_max_rows())
+        return LADDER_ERR_UNSUPPORTED;
+    const int old_path = p.path;
+    p.path = 2;
+    if (p.shard_world > 1) {
+        p.ws = layout_for(p, p.max_pairs);
+        return LADDER_OK;
+    }
+    const int rc = apply_blocking(p, p.nv, p.nv);
+    if (rc != LADDER_OK) {
+        p.path = old_path;
+        p.ws = layout_for(p, old_path == 1 ? 0 : p.max_pairs);
+    }
+    return rc;
 }
 
 // Modelled seconds of one call (scheduling of batched plans).
@@ -634,6 +662,12 @@ int make_plan(ladder_plan_s** out, int no, int nv, int nchol, int precision, int
         (auto_path(no, nv, nchol, precision) == 1 || rc == LADDER_ERR_BUDGET)) {
         if (use_factorised(*p) == LADDER_OK) rc = LADDER_OK;
     }
+    // FP64: the fused path when the model prefers it, or when nothing else fits (it needs no
+    // workspace).
+    if ((rc == LADDER_OK || rc == LADDER_ERR_BUDGET) && precision == LADDER_FP64 &&
+        (auto_path(no, nv, nchol, precision) == 2 || rc == LADDER_ERR_BUDGET)) {
+        if (use_fused(*p) == LADDER_OK) rc = LADDER_OK;
+    }
     if (rc == LADDER_OK) {
         if (cudaMalloc(&p->d_status, sizeof(unsigned)) != cudaSuccess ||
             cudaMemset(p->d_status, 0, sizeof(unsigned)) != cudaSuccess)
@@ -832,8 +866,8 @@ int ladder_form_model(int no, int nv, int nchol, int nslices) {
 }
 
 int ladder_plan_set_path(ladder_plan_t plan, int path) {
-    if (!plan || plan->batched || (path != 0 && path != 1)) return LADDER_ERR_ARG;
-    if (path == 1 && plan->precision != LADDER_FP64) return LADDER_ERR_UNSUPPORTED;
+    if (!plan || plan->batched || path < 0 || path > 2) return LADDER_ERR_ARG;
+    if (path != 0 && plan->precision != LADDER_FP64) return LADDER_ERR_UNSUPPORTED;
     if (path == plan->path) return LADDER_OK;
     DeviceGuard guard(plan->device);
     if (!guard.ok) return LADDER_ERR_CUDA;
@@ -841,6 +875,8 @@ int ladder_plan_set_path(ladder_plan_t plan, int path) {
         if (plan->shard_world > 1) return LADDER_ERR_ARG;   // a shard holds block pairs only
         return use_factorised(*plan);
     }
+    if (path == 2) return use_fused(*plan);
+    const int old_path = plan->path;
     plan->path = 0;
     int rc = plan->bps.empty() ? LADDER_ERR_BUDGET : LADDER_OK;
     if (rc == LADDER_OK) {
@@ -849,8 +885,8 @@ int ladder_plan_set_path(ladder_plan_t plan, int path) {
     }
     if (rc == LADDER_ERR_BUDGET) rc = choose_blocking(*plan);
     if (rc != LADDER_OK) {
-        plan->path = 1;
-        plan->ws = layout_for(*plan, 0);
+        plan->path = old_path;
+        plan->ws = layout_for(*plan, old_path == 1 ? 0 : plan->max_pairs);
     }
     return rc;
 }
@@ -889,6 +925,11 @@ int ladder_apply(ladder_plan_t plan, const double* L, const double* t2, double* 
     cudaError_t e = cudaSuccess;
     if (plan->path == 1) {
         e = ladder::launch_fp64_factorised(*plan, L, t2, R, ws, stream);
+    } else if (plan->path == 2) {
+        for (const auto& bp : plan->bps) {
+            e = ladder::launch_fp64_fused(*plan, bp, L, t2, R, stream);
+            if (e != cudaSuccess) break;
+        }
     } else if (plan->precision == LADDER_FP64) {
         for (const auto& bp : plan->bps) {
             e = ladder::launch_fp64_block(*plan, bp, L, t2, R, ws, stream);

@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 
 #include "ladder_internal.h"
 
@@ -302,7 +303,279 @@ __global__ void __launch_bounds__(THREADS) fact_r_kernel(const double* __restric
     }
 }
 
+// ---------------------------------------------------------------- fused path
+// The two C-split steps of one batch (Sec. "An Asymmetric and Dynamic Splitting Protocol",
+// Table 1: step 0 'xac,xbd->acbd', step 1 'acbd,ecfd->efab') kept on the chip: (ac|bd) never
+// reaches HBM.  A CTA owns a tile of FA x FBT pairs (a, b) and all no^2 amplitude rows (i, j); it
+// walks the (c, d) plane in FC x FD chunks.  For each chunk it builds
+//   V[(a,c),(b,d)] = sum_P L[P,a,c] L[P,b,d]            (64 x 16 FBT DMMA GEMM, K = nchol)
+// into shared memory and contracts it at once with the amplitudes,
+//   acc[(i,j),(a,b)] += sum_{c,d in chunk} t2[i,j,c,d] V[(a,c),(b,d)],
+// the accumulators staying in registers for the whole walk (warp w owns the 8-row (i,j) tiles
+// w, w + 8, ..., so no^2 <= 64 MT).  The epilogue adds them into R[i,j,a,b] and, for a < b, into
+// R[j,i,b,a]: the same ownership as the ladder epilogue above, so no atomics.  FP64 DMMA is the
+// bound (about 3.5 flop per clock per SM on this GPU), so the simple staging below keeps it busy;
+// what matters is issuing no DMMA without use: an 8 x 8 ERI sub-tile has one a and one b, so the
+// sub-tiles of pairs a > b, of rows c >= nv or columns d >= nv (the ragged last chunk) and of a
+// or b past the block are skipped, as are the ladder's K steps whose (c, d) lie past nv.
+constexpr int FA = 4, FC = 16, FD = 16;
+constexpr int FM = FA * FC;                 // ERI chunk rows (a,c): 64
+constexpr int FK = 16;                      // Cholesky vectors per staging step
+constexpr int FTHREADS = 256;
+
+template <int FBT>
+struct FusedShape {
+    static constexpr int FN = FBT * FD;             // ERI chunk columns (b,d)
+    static constexpr int WN = FN / 16;              // warps along the columns (16 each)
+    static constexpr int WM = 8 / WN;               // warps along the rows
+    static constexpr int MI = FM / WM / 8;          // 8-row sub-tiles per warp
+    static constexpr int NPAIR = FA * FBT;          // pairs of the tile
+    static constexpr int NT = NPAIR / 8;            // 8-pair ladder column tiles
+    static constexpr int VLD = FN + 1;              // V chunk row length (doubles)
+    static constexpr int BPT = FN * FK / FTHREADS;  // B staging values per thread
+    static constexpr int STAGE = 2 * FK * (FM + FN);
+    static constexpr int SMEM = STAGE > FM * VLD ? STAGE : FM * VLD;
+    static_assert(WN * WM == 8 && MI >= 1 && NT >= 1 && BPT >= 1, "warp layout");
+};
+
+template <int MT, int FBT>
+__global__ void __launch_bounds__(FTHREADS) ladder_fused_fp64_kernel(const double* __restrict__ L,
+                                                                     const double* __restrict__ t2, int no, int nv,
+                                                                     int nchol, int a0, int a1, int b0, int b1,
+                                                                     double* __restrict__ R) {
+    using Sh = FusedShape<FBT>;
+    constexpr int FN = Sh::FN, MI = Sh::MI, NT = Sh::NT;
+    // Staging buffers sA[2][FK][FM], sB[2][FK][FN] during a chunk's ERI; the V chunk Vs[FM][VLD]
+    // during its ladder step (the two phases are separated by barriers).
+    __shared__ __align__(16) double smem[Sh::SMEM];
+    double(*sA)[FK][FM] = reinterpret_cast<double(*)[FK][FM]>(smem);
+    double(*sB)[FK][FN] = reinterpret_cast<double(*)[FK][FN]>(smem + 2 * FK * FM);
+    double(*Vs)[Sh::VLD] = reinterpret_cast<double(*)[Sh::VLD]>(smem);
+
+    const int nta = (a1 - a0 + FA - 1) / FA;
+    const int at = a0 + (int)(blockIdx.x % nta) * FA, bt = b0 + (int)(blockIdx.x / nta) * FBT;
+    if (at > min(bt + FBT, b1) - 1) return;   // no pair a <= b in the tile
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int wm = warp / Sh::WN, wn = warp % Sh::WN;   // ERI: warp rows of 8 MI, columns of 16
+    const int no2 = no * no, mtiles = (no2 + 7) / 8;
+    const size_t nv2 = (size_t)nv * nv;
+
+    double acc[MT][NT][2];
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) acc[mt][nt][0] = acc[mt][nt][1] = 0.0;
+
+    // Staging map: A row m = t % 64 at the vectors t / 64 + 4i; B row n = t % FN at the vectors
+    // t / FN + (256 / FN) i.
+    const int am = threadIdx.x & 63, ak = threadIdx.x >> 6;
+    const int bn = threadIdx.x % FN, bk = threadIdx.x / FN;
+    const int arow = at + am / FC, brow = bt + bn / FD;
+    // The warp's ERI sub-tiles: a of row sub-tile mi, b of its 16 columns.
+    const int b_w = bt + wn;
+    // Ladder column tile nt holds pairs nt*8 .. nt*8+7 (a_i = n / FBT, b_i = n % FBT): in use when
+    // its smallest a is inside the block.
+    bool nt_on[NT];
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) nt_on[nt] = at + (nt * 8) / FBT < a1;
+
+    for (int c0 = 0; c0 < nv; c0 += FC) {
+        const int ac = c0 + am % FC;
+        const bool a_ok = arow < a1 && ac < nv;
+        const double* pa = L + (size_t)arow * nv + ac;
+        // row sub-tile mi: a = at + (wm*8MI + 8mi) / 16, first c = c0 + (8mi) % 16 (wm*8MI is a
+        // multiple of 16 whenever MI >= 2)
+        bool m_on[MI];
+        int a_of[MI];
+#pragma unroll
+        for (int mi = 0; mi < MI; ++mi) {
+            const int r0 = wm * 8 * MI + mi * 8;
+            a_of[mi] = at + r0 / FC;
+            m_on[mi] = a_of[mi] < a1 && c0 + r0 % FC < nv;
+        }
+        for (int d0 = 0; d0 < nv; d0 += FD) {
+            const int bd = d0 + bn % FD;
+            const bool b_ok = brow < b1 && bd < nv;
+            const double* pb = L + (size_t)brow * nv + bd;
+            bool on[MI][2];
+#pragma unroll
+            for (int mi = 0; mi < MI; ++mi)
+#pragma unroll
+                for (int ni = 0; ni < 2; ++ni)
+                    on[mi][ni] = m_on[mi] && b_w < b1 && d0 + ni * 8 < nv && a_of[mi] <= b_w;
+            // ---- ERI chunk: e[mi][ni][.] = rows wm*8MI + mi*8 + lane/4, columns wn*16 + ni*8 + 2(lane%4) + .
+            double e[MI][2][2];
+#pragma unroll
+            for (int mi = 0; mi < MI; ++mi)
+#pragma unroll
+                for (int ni = 0; ni < 2; ++ni) e[mi][ni][0] = e[mi][ni][1] = 0.0;
+            double ra[4], rb[Sh::BPT];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int P = ak + 4 * i;
+                ra[i] = a_ok && P < nchol ? __ldg(pa + (size_t)P * nv2) : 0.0;
+            }
+#pragma unroll
+            for (int i = 0; i < Sh::BPT; ++i) {
+                const int P = bk + (FTHREADS / FN) * i;
+                rb[i] = b_ok && P < nchol ? __ldg(pb + (size_t)P * nv2) : 0.0;
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) sA[0][ak + 4 * i][am] = ra[i];
+#pragma unroll
+            for (int i = 0; i < Sh::BPT; ++i) sB[0][bk + (FTHREADS / FN) * i][bn] = rb[i];
+            __syncthreads();
+            const int nk = (nchol + FK - 1) / FK;
+            for (int kt = 0; kt < nk; ++kt) {
+                const int cur = kt & 1;
+                const bool more = kt + 1 < nk;
+                if (more) {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int P = (kt + 1) * FK + ak + 4 * i;
+                        ra[i] = a_ok && P < nchol ? __ldg(pa + (size_t)P * nv2) : 0.0;
+                    }
+#pragma unroll
+                    for (int i = 0; i < Sh::BPT; ++i) {
+                        const int P = (kt + 1) * FK + bk + (FTHREADS / FN) * i;
+                        rb[i] = b_ok && P < nchol ? __ldg(pb + (size_t)P * nv2) : 0.0;
+                    }
+                }
+#pragma unroll
+                for (int kk = 0; kk < FK; kk += 4) {
+                    double af[MI], bf[2];
+#pragma unroll
+                    for (int mi = 0; mi < MI; ++mi)
+                        af[mi] = sA[cur][kk + (lane & 3)][wm * 8 * MI + mi * 8 + (lane >> 2)];
+#pragma unroll
+                    for (int ni = 0; ni < 2; ++ni) bf[ni] = sB[cur][kk + (lane & 3)][wn * 16 + ni * 8 + (lane >> 2)];
+#pragma unroll
+                    for (int mi = 0; mi < MI; ++mi)
+#pragma unroll
+                        for (int ni = 0; ni < 2; ++ni)
+                            if (on[mi][ni]) dmma_8x8x4(e[mi][ni], af[mi], bf[ni]);   // warp-uniform
+                }
+                if (more) {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) sA[cur ^ 1][ak + 4 * i][am] = ra[i];
+#pragma unroll
+                    for (int i = 0; i < Sh::BPT; ++i) sB[cur ^ 1][bk + (FTHREADS / FN) * i][bn] = rb[i];
+                }
+                __syncthreads();
+            }
+            // The staging buffers are dead now: the V chunk takes their place (zero where skipped).
+#pragma unroll
+            for (int mi = 0; mi < MI; ++mi)
+#pragma unroll
+                for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+                    for (int x = 0; x < 2; ++x)
+                        Vs[wm * 8 * MI + mi * 8 + (lane >> 2)][wn * 16 + ni * 8 + 2 * (lane & 3) + x] = e[mi][ni][x];
+            __syncthreads();
+            // ---- ladder step over the chunk's K = (c, d), c = k / FD, d = k % FD.
+            // B operand of pair n = (a_i, b_i) = (n / FBT, n % FBT): V[(a_i, c), (b_i, d)].
+            int vr[NT], vc[NT];
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt) {
+                const int n = nt * 8 + (lane >> 2);
+                vr[nt] = (n / FBT) * FC;
+                vc[nt] = (n % FBT) * FD;
+            }
+            const int c_end = min(FC, nv - c0), d_end = min(FD, nv - d0);
+            for (int c = 0; c < c_end; ++c) {
+#pragma unroll
+                for (int dd = 0; dd < FD; dd += 4) {
+                    if (dd >= d_end) break;   // warp-uniform: the K steps past nv
+                    const int d = dd + (lane & 3);
+                    const bool cd_ok = d < d_end;
+                    double v[NT];
+#pragma unroll
+                    for (int nt = 0; nt < NT; ++nt) v[nt] = Vs[vr[nt] + c][vc[nt] + d];
+                    const double* tk = t2 + (size_t)(c0 + c) * nv + (d0 + d);
+#pragma unroll
+                    for (int mt = 0; mt < MT; ++mt) {
+                        const int tile = warp + 8 * mt;
+                        if (tile < mtiles) {   // warp-uniform
+                            const int ij = tile * 8 + (lane >> 2);
+                            const double tv = cd_ok && ij < no2 ? __ldg(tk + (size_t)ij * nv2) : 0.0;
+#pragma unroll
+                            for (int nt = 0; nt < NT; ++nt)
+                                if (nt_on[nt]) dmma_8x8x4(acc[mt][nt], tv, v[nt]);
+                        }
+                    }
+                }
+            }
+            __syncthreads();   // Vs is read by every warp before the next chunk stages into it
+        }
+    }
+    // ---- epilogue: acc[mt][nt][x] is row (i,j) = (warp + 8 mt) * 8 + lane/4, pair n = nt*8 + 2(lane%4) + x.
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt) {
+        const int ij = (warp + 8 * mt) * 8 + (lane >> 2);
+        if (warp + 8 * mt >= mtiles || ij >= no2) continue;
+        const int i = ij / no, j = ij % no;
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+            for (int x = 0; x < 2; ++x) {
+                const int n = nt * 8 + 2 * (lane & 3) + x;
+                const int a = at + n / FBT, b = bt + n % FBT;
+                if (a >= a1 || b >= b1 || a > b) continue;
+                const double v = acc[mt][nt][x];
+                R[(((size_t)i * no + j) * nv + a) * nv + b] += v;
+                if (a < b) R[(((size_t)j * no + i) * nv + b) * nv + a] += v;
+            }
+    }
+}
+
+// Pair tiles of a block pair that hold a pair a <= b, for FA x fb tiles.
+long long fused_tiles(const BlockPair& bp, int fb) {
+    long long n = 0;
+    for (int at = bp.a0; at < bp.a1; at += FA)
+        for (int bt = bp.b0; bt < bp.b1; bt += fb)
+            if (at <= std::min(bt + fb, bp.b1) - 1) ++n;
+    return n;
+}
+
+template <int FBT>
+cudaError_t launch_fused_fbt(const ladder_plan_s& p, const BlockPair& bp, const double* L, const double* t2,
+                             double* R, cudaStream_t s) {
+    const int mtiles = (p.no * p.no + 7) / 8, per_warp = (mtiles + 7) / 8;
+    const long long nta = (bp.a1 - bp.a0 + FA - 1) / FA, ntb = (bp.b1 - bp.b0 + FBT - 1) / FBT;
+    if (per_warp > 16 || nta * ntb > 0x7fffffffLL) return cudaErrorInvalidValue;
+    const unsigned grid = (unsigned)(nta * ntb);
+#define LADDER_FUSED_LAUNCH(MT)                                                                           \
+    ladder_fused_fp64_kernel<MT, FBT><<<grid, FTHREADS, 0, s>>>(L, t2, p.no, p.nv, p.nchol, bp.a0, bp.a1, \
+                                                                bp.b0, bp.b1, R)
+    if (per_warp <= 1) LADDER_FUSED_LAUNCH(1);
+    else if (per_warp <= 2) LADDER_FUSED_LAUNCH(2);
+    else if (per_warp <= 4) LADDER_FUSED_LAUNCH(4);
+    else if (per_warp <= 8) LADDER_FUSED_LAUNCH(8);
+    else LADDER_FUSED_LAUNCH(16);
+#undef LADDER_FUSED_LAUNCH
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+int fused_fp64_max_rows() { return 8 * 8 * 16; }
+
+int fused_fp64_tile_b(const ladder_plan_s& p, const BlockPair& bp) {
+    // The 4 x 2 tile (two CTAs per SM, half the work per CTA, so the SMs' shares of the tiles
+    // come out more even) unless the 4 x 4 one (one CTA per SM: its accumulators take most of the
+    // registers) fills the SMs' shares better by more than 2 % of the work.
+    const double sms = std::max(1, p.num_sms);
+    const long long t4 = fused_tiles(bp, 4), t2_ = fused_tiles(bp, 2);
+    const double fill4 = t4 / (std::ceil(t4 / sms) * sms), fill2 = t2_ / (std::ceil(t2_ / sms) * sms);
+    return fill4 > fill2 + 0.02 ? 4 : 2;
+}
+
+cudaError_t launch_fp64_fused(const ladder_plan_s& p, const BlockPair& bp, const double* L, const double* t2,
+                              double* R, cudaStream_t s) {
+    LaunchTimer t(p, s, LADDER_KERNEL_FUSED);
+    return fused_fp64_tile_b(p, bp) == 2 ? launch_fused_fbt<2>(p, bp, L, t2, R, s)
+                                         : launch_fused_fbt<4>(p, bp, L, t2, R, s);
+}
 
 cudaError_t launch_fp64_factorised(const ladder_plan_s& p, const double* L, const double* t2, double* R, void* ws,
                                    cudaStream_t s) {

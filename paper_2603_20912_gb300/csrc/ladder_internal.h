@@ -135,7 +135,8 @@ struct ladder_plan_s {
     int lad_bn = ladder::kEmuTileN;  // emulated ladder on one SM: pairs per column tile (16..96)
     int eri_chunk_max = 4;           // emulated ERI: longest exact K chunk, in blocks of 1024 (1..4)
     int pb = 0;                      // emulated: Cholesky vectors per slicing batch (0: all at once)
-    int path = 0;     // 0: rebuild (ac|bd) per block pair; 1: factorised sum_P L_P T_ij L_P^T (FP64)
+    int path = 0;     // 0: rebuild (ac|bd) per block pair; 1: factorised sum_P L_P T_ij L_P^T (FP64);
+                      // 2: fused ERI -> ladder per block pair, no workspace (FP64)
     int fact_pb = 0;  // factorised path: Cholesky vectors per batch
     int shard_rank = 0, shard_world = 1;  // this plan holds shard `shard_rank` of `shard_world`
     std::vector<ladder::BlockPair> bps;
@@ -205,6 +206,11 @@ cudaError_t launch_fp64_block(const ladder_plan_s& p, const BlockPair& bp, const
                               const double* t2, double* R, void* ws, cudaStream_t s);
 cudaError_t launch_fp64_factorised(const ladder_plan_s& p, const double* L, const double* t2, double* R, void* ws,
                                    cudaStream_t s);
+// Fused ERI -> ladder kernel over the pairs of one block pair (no workspace); no^2 at most
+// fused_fp64_max_rows().
+cudaError_t launch_fp64_fused(const ladder_plan_s& p, const BlockPair& bp, const double* L, const double* t2,
+                              double* R, cudaStream_t s);
+int fused_fp64_max_rows();
 // energy.cu
 cudaError_t launch_energy(const ladder_plan_s& p, const double* t2, const double* R, double* E_dev,
                           cudaStream_t s);

@@ -159,19 +159,36 @@ def test_form_model_decisions():
             lad.ladder_form_model(*bad)
 
 
+def test_header_enum_values_match_the_binding():
+    # every LADDER_* enumerator declared in include/ladder.h has the same value in the binding
+    text = open(os.path.join(ROOT, "include", "ladder.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    found = {}
+    for body in re.findall(r"enum\s*\{(.*?)\}", text, flags=re.S):
+        for name, val in re.findall(r"(LADDER_[A-Z0-9_]+)\s*=\s*(\d+)", body):
+            found[name] = int(val)
+    assert {"LADDER_PATH_FUSED", "LADDER_KERNEL_FUSED", "LADDER_KERNEL_CLASSES"} <= set(found)
+    for name, val in found.items():
+        if name == "LADDER_KERNEL_CLASSES":
+            continue
+        assert getattr(lad, name) == val, name
+
+
 def test_path_model_decisions(lib):
     # the factorised order R_ij = sum_P L_P T_ij L_P^T is taken for FP64 plans when it needs
-    # 1.25x fewer flops than rebuilding (ac|bd): 4 X o(o+1)/2 v^3 against 2 X v^2 p + 2 o^2 v^2 p
+    # 1.25x fewer flops than rebuilding (ac|bd): 4 X o(o+1)/2 v^3 against 2 X v^2 p + 2 o^2 v^2 p;
+    # otherwise the rebuild fused on the chip when its accumulators hold no^2 <= 1024 rows
     def rule(no, nv, nchol):
         p = nv * (nv + 1) / 2
         eri = 2.0 * nchol * nv * nv * p + 2.0 * no * no * nv * nv * p
         fact = 4.0 * nchol * no * (no + 1) / 2 * nv ** 3
-        return 1 if 1.25 * fact < eri else 0
-    for name, want in (("c1", 0), ("c2", 0), ("c3", 0)):
+        return 1 if 1.25 * fact < eri else (2 if no * no <= 1024 else 0)
+    for name, want in (("c1", 2), ("c2", 2), ("c3", 2)):
         s = CONFIGS[name]
         assert lad.ladder_path_model(s.no, s.nv, s.nchol, lad.LADDER_FP64) == want
     assert lad.ladder_path_model(12, 64, 8, lad.LADDER_FP64) == 1
-    for no in (1, 3, 10, 30):
+    assert lad.ladder_path_model(33, 400, 1260, lad.LADDER_FP64) == 0
+    for no in (1, 3, 10, 30, 33):
         for nv in (5, 40, 300):
             for nchol in (1, 8, 100, 1000):
                 assert lad.ladder_path_model(no, nv, nchol, lad.LADDER_FP64) == rule(no, nv, nchol)

@@ -91,7 +91,7 @@ def test_switching_orders_and_emulated_rejection():
     s = CONFIGS["c1"]
     L, t2, _, _ = make_inputs(s.no, s.nv, s.nchol, s.seed)
     R0, plan = run(L, t2)
-    assert plan.path() == lad.LADDER_PATH_ERI
+    assert plan.path() == lad.LADDER_PATH_FUSED   # the planner's choice at this shape
     plan.set_path(lad.LADDER_PATH_FACTORISED)
     assert plan.path() == 1
     plan.set_blocks(7, 5)                      # a forced blocking is the rebuild order

@@ -116,9 +116,13 @@ def test_small_budget_forces_split():
 
 
 def test_budget_too_small_is_an_error():
+    # no V block, no factorised batch, and no^2 = 1089 rows are more than the fused kernel holds
     with pytest.raises(lad.LadderError) as e:
-        lad.ladder_plan(3, 37, 45, ws_budget_bytes=512)
+        lad.ladder_plan(33, 37, 45, ws_budget_bytes=512)
     assert e.value.status == lad.LADDER_ERR_BUDGET
+    # with no^2 <= 1024 the fused path needs no workspace and takes the plan
+    plan = lad.ladder_plan(3, 37, 45, ws_budget_bytes=512)
+    assert plan.path() == lad.LADDER_PATH_FUSED and plan.workspace_bytes() <= 512
 
 
 @pytest.mark.parametrize("no,nv,nchol", [(1, 1, 1), (1, 2, 3), (2, 1, 5), (4, 9, 1), (6, 65, 17), (9, 33, 130)])

@@ -1,6 +1,7 @@
 """Whole-R parity at the one-batch workload (no=10, nv=200, nchol=630, seed 1236): every
 element of R from the GPU against the CPU oracle's plain FP64 loops (Eq. vfunction-chol), for
-the native FP64 path and for both forms of the emulated path.
+the native FP64 path (rebuild order through HBM and the fused on-chip kernel) and for both forms
+of the emulated path.
 
 The oracle's R is computed once per module (about 2.3e12 flops: a minute or two on a
 many-core host) and pinned first to its own stored E_L and ||R||_F (tests/golden, written by
@@ -35,9 +36,12 @@ def c2():
     return s, L, t2, ref, E_ref
 
 
-def _run(s, L, t2, precision, form=None):
+def _run(s, L, t2, precision, form=None, path=None):
     torch.cuda.empty_cache()
     plan = lad.ladder_plan(s.no, s.nv, s.nchol, precision)
+    if path is not None:
+        plan.set_path(path)
+        assert plan.path() == path
     if form is not None:
         plan.set_form(form)
         assert plan.form() == form
@@ -54,11 +58,12 @@ def _run(s, L, t2, precision, form=None):
     return out, E
 
 
-@pytest.mark.parametrize("path", ["fp64", "emu_plain", "emu_split"])
+@pytest.mark.parametrize("path", ["fp64", "fp64_fused", "emu_plain", "emu_split"])
 def test_c2_whole_R_against_the_oracle(c2, path):
     s, L, t2, ref, E_ref = c2
-    if path == "fp64":
-        R, E = _run(s, L, t2, lad.LADDER_FP64)
+    if path.startswith("fp64"):
+        R, E = _run(s, L, t2, lad.LADDER_FP64,
+                    path=lad.LADDER_PATH_FUSED if path == "fp64_fused" else lad.LADDER_PATH_ERI)
         tol, diag = 1e-12, None
     else:
         R, E = _run(s, L, t2, lad.LADDER_EMU_BF16, form=0 if path == "emu_plain" else 1)
