@@ -256,6 +256,38 @@ int ladder_apply(ladder_plan_t plan, const double* L, const double* t2, double* 
                  cudaStream_t stream);
 
 /*
+ * ladder_apply_host -- R_host = ladder(L_host, t2_host)   (Eq. vfunction-chol), for operands in
+ * host memory: the inputs are copied to the device, R is formed there from zero (not
+ * accumulated into R_host) and copied back.  The paper's engine stages host arrays to the GPU
+ * and back around every batch (Sec. "An Asymmetric and Dynamic Splitting Protocol"); here the
+ * copies of one call overlap the contraction of the previous one.
+ *
+ *   L_host   host, [nchol][nv][nv] float64;  t2_host host, [no][no][nv][nv] float64 (symmetric
+ *            as for ladder_apply);  R_host host, [no][no][nv][nv] float64, written.
+ *   stage    device buffer of ladder_host_staging_bytes(plan) bytes (256-byte aligned): two
+ *            sets of device copies of L, t2 and R.  Successive calls on a plan alternate between
+ *            the sets.  A call enqueues its host-to-device copies on a copy stream the plan owns,
+ *            behind an event of the call two back (the last one to use the same set), so they
+ *            run while the previous call computes; the contraction waits for them on `stream`,
+ *            then the device-to-host copy of R follows on `stream`.
+ *   ws       the workspace of ladder_apply;  stream  the caller's stream.
+ *
+ * R_host holds the result once `stream` has reached the end of the call (e.g. after
+ * cudaStreamSynchronize(stream)); L_host and t2_host must stay unchanged until then.  Pinned
+ * host memory (cudaHostAlloc / cudaHostRegister) lets the copies run asynchronously; pageable
+ * memory works but the copies then block the host.  Successive calls on one plan must use the
+ * same stream, and the same stage buffer.  The first call creates the plan's copy stream and
+ * four events (freed with the plan), so it cannot be captured into a graph; no call is
+ * capturable, since the copy stream is not part of the caller's capture.  For a shard plan
+ * R_host receives the shard's entries (zero elsewhere).  Returns LADDER_OK, LADDER_ERR_ARG
+ * (NULL pointer, misaligned stage or ws, batched plan), LADDER_ERR_CUDA, or what ladder_apply
+ * returns.  ladder_host_staging_bytes: 0 for NULL or a batched plan.
+ */
+size_t ladder_host_staging_bytes(ladder_plan_t plan);
+int ladder_apply_host(ladder_plan_t plan, const double* L_host, const double* t2_host, double* R_host,
+                      void* stage, void* ws, cudaStream_t stream);
+
+/*
  * ladder_energy -- E_L = sum_{ijab} (2 t2[i,j,a,b] - t2[i,j,b,a]) R[i,j,a,b].
  *
  * The closed-shell energy expression the ladder residual enters (the CC energy

@@ -109,6 +109,10 @@ def _load():
     lib.ladder_plan_describe.restype = ci
     lib.ladder_apply.argtypes = [vp, vp, vp, vp, vp, vp]
     lib.ladder_apply.restype = ci
+    lib.ladder_apply_host.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+    lib.ladder_apply_host.restype = ci
+    lib.ladder_host_staging_bytes.argtypes = [vp]
+    lib.ladder_host_staging_bytes.restype = sz
     lib.ladder_energy.argtypes = [vp, vp, vp, vp, ctypes.POINTER(ctypes.c_double), vp]
     lib.ladder_energy.restype = ci
     lib.ladder_plan_batched.argtypes = [ctypes.POINTER(vp), ci, pint, pint, pint, ci, ci, sz, ci]
@@ -201,6 +205,14 @@ class Plan:
         import torch
         # Round up so the tensor start (torch: 512-byte aligned) stays usable.
         return torch.empty(max(self.workspace_bytes(), 256), dtype=torch.uint8, device=f"cuda:{self.device}")
+
+    def host_staging_bytes(self) -> int:
+        return int(_load().ladder_host_staging_bytes(self._h))
+
+    def host_staging(self):
+        """A device buffer of host_staging_bytes() bytes for ladder_apply_host."""
+        import torch
+        return torch.empty(max(self.host_staging_bytes(), 256), dtype=torch.uint8, device=f"cuda:{self.device}")
 
     def describe(self) -> dict:
         vals = [ctypes.c_int() for _ in range(6)]
@@ -305,6 +317,28 @@ def ladder_apply(plan: Plan, L, t2, R, ws=None, stream=None):
         ws = plan.workspace()
     _check(_load().ladder_apply(plan.handle, _dev_ptr(L, "L"), _dev_ptr(t2, "t2"), _dev_ptr(R, "R"),
                                 ctypes.c_void_p(ws.data_ptr()), _stream_handle(stream)), "ladder_apply")
+    return R
+
+
+def _host_ptr(t, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise TypeError(f"{name} must be a host (CPU) tensor")
+    if t.dtype != torch.float64 or not t.is_contiguous():
+        raise TypeError(f"{name} must be contiguous float64")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def ladder_apply_host(plan: Plan, L, t2, R, stage=None, ws=None, stream=None):
+    """R (host) = ladder(L, t2) from host tensors, through the plan's two device staging sets; the
+    result is in R once the stream has been synchronised.  Returns R."""
+    if stage is None:
+        stage = plan.host_staging()
+    if ws is None:
+        ws = plan.workspace()
+    _check(_load().ladder_apply_host(plan.handle, _host_ptr(L, "L"), _host_ptr(t2, "t2"), _host_ptr(R, "R"),
+                                     ctypes.c_void_p(stage.data_ptr()), ctypes.c_void_p(ws.data_ptr()),
+                                     _stream_handle(stream)), "ladder_apply_host")
     return R
 
 
@@ -467,5 +501,6 @@ EXPORTED_SYMBOLS = [
     "ladder_form_model", "ladder_plan_set_wait_limit", "ladder_plan_get_wait_limit",
     "ladder_plan_shard_dry", "ladder_plan_set_path", "ladder_plan_get_path", "ladder_path_model",
     "ladder_plan_set_ladder_tile", "ladder_plan_get_ladder_tile", "ladder_plan_set_eri_chunk",
-    "ladder_plan_eri_chunk", "ladder_plan_set_pbatch", "ladder_plan_get_pbatch",
+    "ladder_plan_eri_chunk", "ladder_plan_set_pbatch", "ladder_plan_get_pbatch", "ladder_apply_host",
+    "ladder_host_staging_bytes",
 ]

@@ -549,6 +549,11 @@ void destroy_plan(ladder_plan_s* p) {
     cudaGetDevice(&cur);
     if (cur != p->device) cudaSetDevice(p->device);
     free_events(p);
+    if (p->h2d_stream) cudaStreamDestroy(p->h2d_stream);
+    for (int s = 0; s < 2; ++s) {
+        if (p->host_ready[s]) cudaEventDestroy(p->host_ready[s]);
+        if (p->host_free[s]) cudaEventDestroy(p->host_free[s]);
+    }
     if (p->d_tables) cudaFree(p->d_tables);
     if (p->d_status) cudaFree(p->d_status);
     if (p->d_partials) cudaFree(p->d_partials);
@@ -945,6 +950,69 @@ int ladder_apply(ladder_plan_t plan, const double* L, const double* t2, double* 
         }
     }
     return map_cuda(e);
+}
+
+// Staging of ladder_apply_host: two sets, each L [nchol][nv][nv], t2 and R [no][no][nv][nv].
+struct StageLayout {
+    size_t t = 0, R = 0, set = 0;   // offsets of t2 and R in a set, bytes per set (L at 0)
+};
+static StageLayout stage_layout(const ladder_plan_s& p) {
+    using ladder::align_up;
+    using ladder::kAlign;
+    const size_t nv2 = (size_t)p.nv * p.nv;
+    StageLayout s;
+    s.t = align_up(sizeof(double) * (size_t)p.nchol * nv2, kAlign);
+    s.R = s.t + align_up(sizeof(double) * (size_t)p.no * p.no * nv2, kAlign);
+    s.set = s.R + align_up(sizeof(double) * (size_t)p.no * p.no * nv2, kAlign);
+    return s;
+}
+
+size_t ladder_host_staging_bytes(ladder_plan_t plan) {
+    if (!plan || plan->batched) return 0;
+    return 2 * stage_layout(*plan).set;
+}
+
+int ladder_apply_host(ladder_plan_t plan, const double* L_host, const double* t2_host, double* R_host,
+                      void* stage, void* ws, cudaStream_t stream) {
+    if (!plan || plan->batched || !L_host || !t2_host || !R_host || !stage || !ws) return LADDER_ERR_ARG;
+    if (!aligned256(stage) || !aligned256(ws)) return LADDER_ERR_ARG;
+    DeviceGuard guard(plan->device);
+    if (!guard.ok) return LADDER_ERR_CUDA;
+    if (!plan->h2d_stream) {
+        if (cudaStreamCreateWithFlags(&plan->h2d_stream, cudaStreamNonBlocking) != cudaSuccess) {
+            plan->h2d_stream = nullptr;
+            return LADDER_ERR_CUDA;
+        }
+        for (int s = 0; s < 2; ++s)
+            if (cudaEventCreateWithFlags(&plan->host_ready[s], cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&plan->host_free[s], cudaEventDisableTiming) != cudaSuccess)
+                return LADDER_ERR_CUDA;
+    }
+    const StageLayout sl = stage_layout(*plan);
+    const int s = plan->host_parity;
+    char* set = static_cast<char*>(stage) + (size_t)s * sl.set;
+    double* Ld = reinterpret_cast<double*>(set);
+    double* td = reinterpret_cast<double*>(set + sl.t);
+    double* Rd = reinterpret_cast<double*>(set + sl.R);
+    const size_t nv2 = (size_t)plan->nv * plan->nv;
+    const size_t bL = sizeof(double) * (size_t)plan->nchol * nv2, bT = sizeof(double) * (size_t)plan->no * plan->no * nv2;
+    // Inputs into set s on the copy stream, once the call two back (the last one to use set s)
+    // has finished with them: so these copies overlap the previous call's contraction.
+    cudaStream_t h = plan->h2d_stream;
+    if (cudaStreamWaitEvent(h, plan->host_free[s], 0) != cudaSuccess ||
+        cudaMemcpyAsync(Ld, L_host, bL, cudaMemcpyHostToDevice, h) != cudaSuccess ||
+        cudaMemcpyAsync(td, t2_host, bT, cudaMemcpyHostToDevice, h) != cudaSuccess ||
+        cudaEventRecord(plan->host_ready[s], h) != cudaSuccess ||
+        cudaStreamWaitEvent(stream, plan->host_ready[s], 0) != cudaSuccess ||
+        cudaMemsetAsync(Rd, 0, bT, stream) != cudaSuccess)
+        return LADDER_ERR_CUDA;
+    const int rc = ladder_apply(plan, Ld, td, Rd, ws, stream);
+    if (rc != LADDER_OK) return rc;
+    if (cudaEventRecord(plan->host_free[s], stream) != cudaSuccess ||
+        cudaMemcpyAsync(R_host, Rd, bT, cudaMemcpyDeviceToHost, stream) != cudaSuccess)
+        return LADDER_ERR_CUDA;
+    plan->host_parity = s ^ 1;
+    return LADDER_OK;
 }
 
 int ladder_energy(ladder_plan_t plan, const double* t2, const double* R, double* E_dev, double* E_host,

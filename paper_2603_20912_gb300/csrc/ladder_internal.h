@@ -142,6 +142,12 @@ struct ladder_plan_s {
     std::vector<ladder::BlockPair> bps;
     int max_pairs = 0;
     ladder::WsLayout ws;
+    // Host-buffer calls (ladder_apply_host): a copy stream and, per staging set, the events
+    // "inputs copied" and "inputs free again"; created by the first such call.
+    cudaStream_t h2d_stream = nullptr;
+    cudaEvent_t host_ready[2] = {nullptr, nullptr};
+    cudaEvent_t host_free[2] = {nullptr, nullptr};
+    int host_parity = 0;
     // Device-side tables (allocated at plan time).
     void* d_tables = nullptr;          // pair lists (int2) + row_start tables (int)
     size_t tables_bytes = 0;

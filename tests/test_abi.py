@@ -60,6 +60,8 @@ def test_null_arguments_are_rejected_without_a_gpu(lib):
     assert lib.ladder_apply(None, None, None, None, None, None) == lad.LADDER_ERR_ARG
     assert lib.ladder_energy(None, None, None, None, None, None) == lad.LADDER_ERR_ARG
     assert lib.ladder_workspace_bytes(None) == 0
+    assert lib.ladder_apply_host(None, None, None, None, None, None, None) == lad.LADDER_ERR_ARG
+    assert lib.ladder_host_staging_bytes(None) == 0
     lib.ladder_plan_destroy(None)
 
 
