@@ -122,8 +122,9 @@ int ladder_plan_set_form(ladder_plan_t plan, int form);
 /* The form a plan uses: ladder_plan picks 1 on the emulated path when a cost model of the whole
  * call (ERI, tile-padded ladder rows, the extra pass over V) gives it a 5 % lead (the ladder a
  * large share of the call: large no^2 with respect to the 128/256-row MMA tiles and to nchol)
- * and the workspace fits, else 0.  The instances of a batched plan choose the same way (an
- * instance in form 1 runs alone under a grouped schedule).  -1 for NULL. */
+ * and the workspace fits, else 0.  The instances of a batched plan choose the same way.  In
+ * form 1 the X and Y ladder items of a block pair run in one persistent launch when they take
+ * the same CTA shape.  -1 for NULL. */
 int ladder_plan_get_form(ladder_plan_t plan);
 /* The form the cost model above picks for an emulated plan of this shape (nslices 0 = the
  * default), before the workspace check: 0 or 1; -1 for invalid arguments.  Host only. */
@@ -310,13 +311,15 @@ int ladder_energy(ladder_plan_t plan, const double* t2, const double* R, double*
  * sub-plan against the whole budget (one block pair whenever its packed ERI
  * fits).  The plan's workspace (ladder_workspace_bytes) holds as many
  * instances at once as the budget allows.  Two kinds of schedule:
- *   grouped (emulated path, the default): the instances in the plain ladder
- *     form are packed, largest workspace first, into groups that fit the
- *     workspace (an instance in the symmetric/antisymmetric form is a group of
- *     its own); each group runs as
- *     ONE persistent ERI launch over the tiles of all its instances, then ONE
- *     persistent ladder launch per ladder shape (single CTAs for o^2 <= 128,
- *     CTA pairs above) over all their units, with the small per-instance
+ *   grouped (emulated path, the default): the instances are packed, largest
+ *     workspace first, into groups that fit the workspace, of at most 32
+ *     instances and 32 ladder items (one per instance in the plain form, X
+ *     and Y in the symmetric/antisymmetric one; an instance whose Cholesky
+ *     vectors are sliced in batches is a group of its own); each group runs as
+ *     ONE persistent ERI launch over the tiles of all its instances, the
+ *     combine pass of each split-form instance, then ONE persistent ladder
+ *     launch per ladder shape (single CTAs for up to 128 rows, CTA pairs
+ *     above) over all their items' units, with the small per-instance
  *     preparation and finalisation kernels around them;
  *   worker streams (the FP64 path's default): each instance runs as its own
  *     ladder_apply on one of k plan-owned streams (longest first).

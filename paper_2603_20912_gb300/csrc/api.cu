@@ -317,15 +317,16 @@ EriRowTiles eri_row_tiles(const BlockPair& bp, int nv) {
 // (int2 (a, b), a-major) and row_start (first packed row of each a).
 // ERI work entries of one block pair, (rt, qt, 0, 0): a 256-row tile rt (computed by a CTA pair,
 // 128 rows each) and a 96-column tile qt of (b,d), kept when one of its rows stores to one of
-// its b.  Order: a band of row tiles whose operand slices take ~40 MB of L2 stays resident while
-// every column tile of the band streams past it.
+// its b.  Order: a band of row tiles whose operand slices take ~16 MB of L2 stays resident while
+// every column tile of the band streams past it (at no=20 nv=400 nchol=1260 bands of 16, 40 and
+// 120 MB all took the same time; the smallest moved the fewest bytes from DRAM).
 std::vector<int> eri_entries(const BlockPair& bp, int nv, int tile_n, size_t row_bytes) {
     const EriRowTiles rt = eri_row_tiles(bp, nv);
     nv = ladder::emu_vp(nv);  // columns run over the padded (b, d) range
     std::vector<int> out;
     const long long N = (long long)(bp.b1 - bp.b0) * nv;
     const int nrt = (int)rt.key.size(), nqt = (int)((N + tile_n - 1) / tile_n);
-    const int band = (int)std::max<size_t>(4, std::min<size_t>(32, (40u << 20) / std::max<size_t>(1, row_bytes * 256)));
+    const int band = (int)std::max<size_t>(4, std::min<size_t>(32, (16u << 20) / std::max<size_t>(1, row_bytes * 256)));
     for (int r0 = 0; r0 < nrt; r0 += band)
         for (int qt = 0; qt < nqt; ++qt)
             for (int r = r0; r < std::min(nrt, r0 + band); ++r) {
@@ -711,11 +712,19 @@ void schedule_batched(ladder_plan_s& p, int k) {
     }
 }
 
-// An instance can join a group when it runs on the emulated path as a single block pair.
-bool groupable(const ladder_plan_s& s) { return s.precision != LADDER_FP64 && s.form == 0 && s.bps.size() == 1; }
+// An instance can join a group when it runs on the emulated path as a single block pair and slices
+// all its Cholesky vectors at once.
+bool groupable(const ladder_plan_s& s) {
+    return s.precision != LADDER_FP64 && s.bps.size() == 1 && (s.pb <= 0 || s.pb >= s.nchol);
+}
+
+// Ladder items an instance adds to its group's launches: one in the plain form; X, and Y when
+// there are rows i < j and pairs c < d, in the split form.
+int ladder_items_of(const ladder_plan_s& s) { return s.form == 1 && s.no > 1 && s.nv > 1 ? 2 : 1; }
 
 // Grouped schedule: first-fit decreasing of the instances' workspaces into groups of at most
-// `cap` bytes and emu_max_group() instances (an instance that cannot be grouped runs alone),
+// `cap` bytes, emu_max_group() instances and emu_max_group() ladder items (an instance that cannot
+// be grouped runs alone),
 // and the device list of every group's ERI tiles with z = position of the instance in its group.
 int schedule_groups(ladder_plan_s& p, size_t cap) {
     const int n = (int)p.sub.size();
@@ -725,6 +734,7 @@ int schedule_groups(ladder_plan_s& p, size_t cap) {
                      [&](int x, int y) { return p.sub[x]->ws.total > p.sub[y]->ws.total; });
     std::vector<std::vector<int>> groups;
     std::vector<size_t> used;
+    std::vector<int> items;
     p.inst_off.assign(n, 0);
     for (int k : order) {
         const size_t need = ladder::align_up(p.sub[k]->ws.total, ladder::kAlign);
@@ -733,15 +743,18 @@ int schedule_groups(ladder_plan_s& p, size_t cap) {
         if (groupable(*p.sub[k]))
             for (int j = 0; j < (int)groups.size() && g < 0; ++j)
                 if (groupable(*p.sub[groups[j][0]]) && used[j] + need <= cap &&
-                    (int)groups[j].size() < ladder::emu_max_group())
+                    (int)groups[j].size() < ladder::emu_max_group() &&
+                    items[j] + ladder_items_of(*p.sub[k]) <= ladder::emu_max_group())
                     g = j;
         if (g < 0) {
             groups.push_back({});
             used.push_back(0);
+            items.push_back(0);
             g = (int)groups.size() - 1;
         }
         p.inst_off[k] = used[g];
         used[g] += need;
+        items[g] += ladder_items_of(*p.sub[k]);
         groups[g].push_back(k);
     }
     std::vector<int> host;

@@ -874,8 +874,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsEri, 1)
     bool failed = false;
 
     if (warp == 0 && lane == 0) {
-        // ---------------- TMA producer (both CTAs).  The L^T slices are re-read by many tiles:
-        // they are kept in L2 ahead of the V planes, which are written once and streamed.
+        // ---------------- TMA producer (both CTAs).  The row tiles of a band are re-read by every
+        // column tile of the band: they are kept in L2 (evict-last) ahead of the B columns, which
+        // pass through, and of the V planes, which are written once and streamed.
         Ring ring;
         bool ok = true;
         const uint64_t keep = policy_evict_last();
@@ -896,7 +897,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsEri, 1)
 #pragma unroll
                 for (int c = 0; c < CPC; ++c)
                     tma_load_3d_2sm_hint(st + c * ACHUNK, &B.ta[en.z], fb, kb * BK, arow[c], 0, keep);
-                tma_load_3d_2sm_hint(st + ABYTES, &B.tb[en.z], fb, kb * BK, brow, 0, keep);
+                tma_load_3d_2sm(st + ABYTES, &B.tb[en.z], fb, kb * BK, brow, 0);
                 ring.next(STAGES);
             }
         }
@@ -1879,19 +1880,68 @@ bool ladder_item_pm(const ladder_plan_s& p, const BlockPair& bp, void* ws, long 
     return true;
 }
 
+// Split form, shared by single plans and groups: zero the X and Y accumulators of a block pair.
+// Y's accumulator starts at zero whenever there are rows i < j, also when K'' is empty (nv = 1):
+// the finalisation reads it for those rows.
+cudaError_t clear_pm_acc(const ladder_plan_s& p, const BlockPair& bp, void* ws, cudaStream_t s) {
+    const PmDims d = pm_dims(p.no, p.nv);
+    cudaError_t e = cudaMemsetAsync(at<char>(ws, p.ws.rpx), 0, (size_t)bp.npairs * d.np * 8, s);
+    if (e == cudaSuccess && d.nm > 0) e = cudaMemsetAsync(at<char>(ws, p.ws.rpy), 0, (size_t)bp.npairs * d.nm * 8, s);
+    return e;
+}
+
+// Split form: V' and V'' of a block pair from its int64 V.
+template <int S>
+void launch_combine(const ladder_plan_s& p, const BlockPair& bp, void* ws, cudaStream_t s) {
+    const PmDims d = pm_dims(p.no, p.nv);
+    const int vp = padded_vp(p.nv);
+    CombineArgs ca{p.nv, vp, bp.npairs, (p.nv + 31) / 32, (size_t)p.max_pairs * d.kp_pad,
+                   (size_t)p.max_pairs * d.km_pad, (long long)p.nv * vp, d.kp_pad, d.km_pad,
+                   at<long long>(ws, p.ws.v_blk), at<__nv_bfloat16>(ws, p.ws.vp_blk),
+                   at<__nv_bfloat16>(ws, p.ws.vm_blk), p.d_status};
+    const long long units = (long long)bp.npairs * ca.ntile * (ca.ntile + 1) / 2;
+    vpm_combine_kernel<S><<<(unsigned)units, kCombineThreads, 0, s>>>(ca);
+}
+
+// Split form: the X item (and the Y item, when there are rows i < j and K'' is not empty) of a
+// block pair, each appended to the batch of its CTA shape (lb[0]: single CTAs, lb[1]: CTA pairs)
+// after the units and tiles already there.  False when a batch is full.
+template <int S>
+bool add_pm_items(const ladder_plan_s& p, const BlockPair& bp, void* ws, LadBatch* lb) {
+    const PmDims d = pm_dims(p.no, p.nv);
+    const bool has_y = d.nm > 0 && d.km > 0;
+    for (int part = 0; part < (has_y ? 2 : 1); ++part) {
+        LadBatch& b = lb[(part == 0 ? d.np : d.nm) > kEmuTile ? 1 : 0];
+        if (b.nitems >= kMaxItems) return false;
+        LadItem* it = &b.item[b.nitems];
+        if (!ladder_item_pm<S>(p, bp, ws, b.units, part == 0, it, &b.ta[b.nitems], &b.tb[b.nitems], b.tiles))
+            return false;
+        b.units += it->units;
+        b.tiles += it->ntiles;
+        ++b.nitems;
+    }
+    return true;
+}
+
+// Split form: R from the X and Y accumulators of a block pair.
+void launch_finalize_pm(const ladder_plan_s& p, const BlockPair& bp, void* ws, double* R, cudaStream_t s) {
+    const PmDims d = pm_dims(p.no, p.nv);
+    const unsigned gx = (unsigned)std::min<long long>((bp.npairs + 255) / 256, 1024);
+    const unsigned gy = (unsigned)std::min(d.np, 65535);
+    finalize_pm_kernel<<<dim3(gx, gy), 256, 0, s>>>(
+        at<unsigned long long>(ws, p.ws.rpx), at<unsigned long long>(ws, p.ws.rpy), bp.npairs, p.no, p.nv, d.np, d.nm,
+        reinterpret_cast<const int2*>(p.d_tables) + bp.pairs_off, at<int>(ws, p.ws.v_exp), at<int>(ws, p.ws.tp_exp),
+        at<int>(ws, p.ws.tm_exp), R, p.d_status);
+}
+
 // One block pair in the symmetric/antisymmetric form: ERI and self-product entries as in the
-// plain form, V -> V', V'', the X and Y ladders, and the four-way finalisation.
+// plain form, V -> V', V'', the X and Y ladders (one persistent launch for both when they run on
+// the same CTA shape), and the four-way finalisation.
 template <int S>
 cudaError_t block_pm_impl(const ladder_plan_s& p, const BlockPair& bp, const double* L, double* R, void* ws,
                           cudaStream_t s) {
-    const PmDims d = pm_dims(p.no, p.nv);
-    const bool has_y = d.nm > 0 && d.km > 0;
     cudaError_t e;
-    if ((e = cudaMemsetAsync(at<char>(ws, p.ws.rpx), 0, (size_t)bp.npairs * d.np * 8, s)) != cudaSuccess) return e;
-    // Y's accumulator starts at zero whenever there are rows i < j, also when K'' is empty
-    // (nv = 1): the finalisation reads it for those rows.
-    if (d.nm > 0 && (e = cudaMemsetAsync(at<char>(ws, p.ws.rpy), 0, (size_t)bp.npairs * d.nm * 8, s)) != cudaSuccess)
-        return e;
+    if ((e = clear_pm_acc(p, bp, ws, s)) != cudaSuccess) return e;
     const int2* table = reinterpret_cast<const int2*>(p.d_tables);
     EriBatch eb{};
     eb.nitems = 1;
@@ -1899,7 +1949,6 @@ cudaError_t block_pm_impl(const ladder_plan_s& p, const BlockPair& bp, const dou
     eb.entries = reinterpret_cast<const int4*>(table + bp.tiles_off);
     eb.status = p.d_status;
     eb.wait_ns = p.wait_ns;
-    const int vp = padded_vp(p.nv);
     const int pb = lt_batch(p);
     if (pb >= p.nchol) {
         if (!eri_item<S>(p, bp, ws, &eb.item[0], &eb.ta[0], &eb.tb[0])) return cudaErrorInvalidValue;
@@ -1926,37 +1975,27 @@ cudaError_t block_pm_impl(const ladder_plan_s& p, const BlockPair& bp, const dou
     }
     {
         LaunchTimer tm(p, s, LADDER_KERNEL_COMBINE);
-        CombineArgs ca{p.nv, vp, bp.npairs, (p.nv + 31) / 32, (size_t)p.max_pairs * d.kp_pad,
-                       (size_t)p.max_pairs * d.km_pad, (long long)p.nv * vp, d.kp_pad, d.km_pad,
-                       at<long long>(ws, p.ws.v_blk), at<__nv_bfloat16>(ws, p.ws.vp_blk),
-                       at<__nv_bfloat16>(ws, p.ws.vm_blk), p.d_status};
-        const long long units = (long long)bp.npairs * ca.ntile * (ca.ntile + 1) / 2;
-        vpm_combine_kernel<S><<<(unsigned)units, kCombineThreads, 0, s>>>(ca);
+        launch_combine<S>(p, bp, ws, s);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int fit = p.pair_clusters > 0 ? p.pair_clusters : p.num_sms / 2;
-    for (int part = 0; part < (has_y ? 2 : 1); ++part) {
-        LadBatch lb{};
-        lb.nitems = 1;
+    static thread_local LadBatch lbs[2];   // ~17 KB: kept off the stack
+    lbs[0] = LadBatch{};
+    lbs[1] = LadBatch{};
+    if (!add_pm_items<S>(p, bp, ws, lbs)) return cudaErrorInvalidValue;
+    for (int shape = 0; shape < 2; ++shape) {   // 0: single CTAs, 1: CTA pairs
+        LadBatch& lb = lbs[shape];
+        if (lb.nitems == 0) continue;
         lb.status = p.d_status;
         lb.wait_ns = p.wait_ns;
-        if (!ladder_item_pm<S>(p, bp, ws, 0, part == 0, &lb.item[0], &lb.ta[0], &lb.tb[0]))
-            return cudaErrorInvalidValue;
-        lb.BN = ladder_bn(p, lb.item[0].M > kEmuTile);
-        lb.units = lb.item[0].units;
-        lb.tiles = lb.item[0].ntiles;
+        lb.BN = ladder_bn(p, shape == 1);
         LaunchTimer tm(p, s, LADDER_KERNEL_LADDER);
-        launch_ladder_batch<S>(lb, lb.item[0].M > kEmuTile, fit, p.num_sms, s);
+        launch_ladder_batch<S>(lb, shape == 1, fit, p.num_sms, s);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     {
         LaunchTimer tm(p, s, LADDER_KERNEL_FINISH);
-        const unsigned gx = (unsigned)std::min<long long>((bp.npairs + 255) / 256, 1024);
-        const unsigned gy = (unsigned)std::min(d.np, 65535);
-        finalize_pm_kernel<<<dim3(gx, gy), 256, 0, s>>>(
-            at<unsigned long long>(ws, p.ws.rpx), at<unsigned long long>(ws, p.ws.rpy), bp.npairs, p.no, p.nv, d.np,
-            d.nm, table + bp.pairs_off, at<int>(ws, p.ws.v_exp), at<int>(ws, p.ws.tp_exp), at<int>(ws, p.ws.tm_exp),
-            R, p.d_status);
+        launch_finalize_pm(p, bp, ws, R, s);
     }
     return cudaGetLastError();
 }
@@ -2026,11 +2065,11 @@ cudaError_t group_impl(const ladder_plan_s& parent, const ladder_plan_s* const* 
     cudaError_t e;
     for (int k = 0; k < n; ++k) {
         const ladder_plan_s& p = *subs[k];
-        if (p.bps.size() != 1) return cudaErrorInvalidValue;
+        if (p.bps.size() != 1 || (p.form == 1 && lt_batch(p) < p.nchol)) return cudaErrorInvalidValue;
         if ((e = prep_impl<S>(p, L[k], t2[k], ws[k], s)) != cudaSuccess) return e;
-        if ((e = cudaMemsetAsync(at<char>(ws[k], p.ws.rp_int), 0, (size_t)p.bps[0].npairs * p.no * p.no * 8, s)) !=
-            cudaSuccess)
-            return e;
+        e = p.form == 1 ? clear_pm_acc(p, p.bps[0], ws[k], s)
+                        : cudaMemsetAsync(at<char>(ws[k], p.ws.rp_int), 0, (size_t)p.bps[0].npairs * p.no * p.no * 8, s);
+        if (e != cudaSuccess) return e;
     }
     static thread_local EriBatch eb;   // ~10 KB: kept off the stack
     eb = EriBatch{};
@@ -2050,26 +2089,40 @@ cudaError_t group_impl(const ladder_plan_s& parent, const ladder_plan_s* const* 
         for (int k = 0; k < n; ++k) launch_self<S>(*subs[k], subs[k]->bps[0], ws[k], s);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    int n_pm = 0;
+    for (int k = 0; k < n; ++k) n_pm += subs[k]->form == 1;
+    if (n_pm > 0) {   // instances in the split form: V', V'' from their int64 V
+        LaunchTimer tm(parent, s, LADDER_KERNEL_COMBINE, n_pm);
+        for (int k = 0; k < n; ++k)
+            if (subs[k]->form == 1) launch_combine<S>(*subs[k], subs[k]->bps[0], ws[k], s);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // One persistent ladder launch per CTA shape over the items of every instance of the group
+    // (one item per plain instance, X and Y per split-form instance).
+    static thread_local LadBatch lbs[2];
+    lbs[0] = LadBatch{};
+    lbs[1] = LadBatch{};
+    for (int k = 0; k < n; ++k) {
+        const ladder_plan_s& p = *subs[k];
+        if (p.form == 1) {
+            if (!add_pm_items<S>(p, p.bps[0], ws[k], lbs)) return cudaErrorInvalidValue;
+            continue;
+        }
+        LadBatch& lb = lbs[ladder_on_pairs(p) ? 1 : 0];
+        if (lb.nitems >= kMaxItems) return cudaErrorInvalidValue;
+        LadItem* it = &lb.item[lb.nitems];
+        if (!ladder_item<S>(p, p.bps[0], ws[k], lb.units, it, &lb.ta[lb.nitems], &lb.tb[lb.nitems], lb.tiles))
+            return cudaErrorInvalidValue;
+        lb.units += it->units;
+        lb.tiles += it->ntiles;
+        ++lb.nitems;
+    }
     for (int shape = 0; shape < 2; ++shape) {   // 0: single CTAs, 1: CTA pairs
-        static thread_local LadBatch lb;
-        lb = LadBatch{};
+        LadBatch& lb = lbs[shape];
+        if (lb.nitems == 0) continue;
         lb.BN = shape == 1 ? kEmuTileN : parent.lad_bn;   // every single-CTA item of the group uses it
         lb.status = parent.d_status;
         lb.wait_ns = parent.wait_ns;
-        long long units = 0, tiles = 0;
-        for (int k = 0; k < n; ++k) {
-            if ((int)ladder_on_pairs(*subs[k]) != shape) continue;
-            LadItem* it = &lb.item[lb.nitems];
-            if (!ladder_item<S>(*subs[k], subs[k]->bps[0], ws[k], units, it, &lb.ta[lb.nitems], &lb.tb[lb.nitems],
-                                tiles))
-                return cudaErrorInvalidValue;
-            units += it->units;
-            tiles += it->ntiles;
-            ++lb.nitems;
-        }
-        if (lb.nitems == 0) continue;
-        lb.units = units;
-        lb.tiles = tiles;
         LaunchTimer tm(parent, s, LADDER_KERNEL_LADDER);
         launch_ladder_batch<S>(lb, shape == 1, pair_fit, subs[0]->num_sms, s);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -2079,6 +2132,10 @@ cudaError_t group_impl(const ladder_plan_s& parent, const ladder_plan_s* const* 
         for (int k = 0; k < n; ++k) {
             const ladder_plan_s& p = *subs[k];
             const BlockPair& bp = p.bps[0];
+            if (p.form == 1) {
+                launch_finalize_pm(p, bp, ws[k], R[k], s);
+                continue;
+            }
             const long long cnt = (long long)bp.npairs * p.no * p.no;
             finalize_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(
                 at<unsigned long long>(ws[k], p.ws.rp_int), bp.npairs, p.no, p.nv,

@@ -190,3 +190,28 @@ def test_tuned_choice_is_bit_identical_to_single_plans():
         lad.ladder_apply(single, L, t, R1)
         torch.cuda.synchronize()
         assert torch.equal(R, R1)
+
+
+def test_split_form_instances_share_a_group_bit_for_bit():
+    # instances that take the symmetric/antisymmetric form (no = 20, 24 at these sizes) join the
+    # group: one ERI launch, their combine passes, one ladder launch with their X and Y items
+    # beside the plain instances' items; exact integer sums, so the bits of single plans
+    pm = [(20, 12, 8), (20, 16, 12), (24, 28, 40)]
+    for o, v, x in pm:
+        assert lad.ladder_form_model(o, v, x, 0) == 1
+    shapes = SMALL + pm
+    host, Ls, ts = _make(shapes, seed0=1300)
+    plan = lad.ladder_plan_batched([s[0] for s in shapes], [s[1] for s in shapes], [s[2] for s in shapes], EMU)
+    ws = plan.workspace()
+    assert lad.ladder_batched_schedule(plan, -1) == -1   # one group of all nine instances
+    Rs = [torch.zeros_like(t) for t in ts]
+    lad.ladder_apply_batched(plan, Ls, ts, Rs, ws)
+    torch.cuda.synchronize()
+    assert plan.last_status() == lad.LADDER_OK
+    for (o, v, x), (L, t), Ld, td, R in zip(shapes, host, Ls, ts, Rs):
+        single = lad.ladder_plan(o, v, x, EMU)
+        R1 = torch.zeros_like(td)
+        lad.ladder_apply(single, Ld, td, R1)
+        torch.cuda.synchronize()
+        assert torch.equal(R, R1)
+        assert rel_fro(R.cpu().numpy(), oracle.ladder(L, t)) <= 1e-10

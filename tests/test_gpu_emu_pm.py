@@ -40,8 +40,11 @@ def pm_ladder(L, t2, blocks=None, budget=0):
     return R.cpu().numpy(), plan
 
 
+# X and Y on CTA pairs in one ladder launch (no = 18, 20), both on single CTAs (no = 12), and
+# X on CTA pairs with Y on single CTAs in two launches (no = 16: 136 and 120 rows).
 @pytest.mark.parametrize("no,nv,nchol", [(5, 19, 72), (1, 7, 9), (2, 1, 5), (3, 32, 50), (4, 45, 60),
-                                         (18, 30, 40), (12, 47, 33), (3, 23, 1500)])
+                                         (18, 30, 40), (12, 47, 33), (3, 23, 1500), (16, 29, 35),
+                                         (20, 33, 21)])
 def test_parity_with_the_oracle(no, nv, nchol):
     L, t2, _, _ = make_inputs(no, nv, nchol, seed=no * 1000 + nv)
     R, plan = pm_ladder(L, t2)
