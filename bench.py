@@ -62,7 +62,7 @@ TRAFFIC_CAPTURES = {
     ("fp64", "c2"): ("efd514e3bd5bd3a9", 49657817856 + 6438093312, "profiles/dram_traffic_no10_nv200_nchol630.md",
                      (200, 200)),
     # mean of the call's two ERI launches (20100 and 60100 pair rows)
-    ("emu", "c3"): ("6413435cd2b07522", (113352329728 + 31373112832 + 379428436224 + 89989395456) // 2,
+    ("emu", "c3"): ("e87887827be608ef", (100091149824 + 31024744448 + 290397778944 + 89547002368) // 2,
                     "profiles/dram_traffic_no20_nv400_nchol1260_emu.md", (400, 200)),
 }
 KERNEL_SOURCE_DIR = os.path.join(ROOT, "paper_2603_20912_gb300", "csrc")
