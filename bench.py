@@ -370,6 +370,14 @@ def batched_record(args, lad, local, world, device_inputs, steps, warmup, fp64_s
     assert plan.last_status() == lad.LADDER_OK
     ms_total = max_over_ranks(ev0.elapsed_time(ev1), world)
     value = world * flops * steps / (ms_total * 1e-3) / 1e12
+    # Where a call's time goes: one more call, outside the graph and after the timed region, with
+    # the library's event pairs around each kernel class (the events add a little time).
+    plan.set_timing(True)
+    lad.ladder_apply_batched(plan, Ls, ts, Rs, ws)
+    torch.cuda.synchronize()
+    kms, kcounts = kernel_times(lad, plan, 1)
+    plan.set_timing(False)
+    split = {k: v for k, v in kms.items() if v > 0}
     fp64 = None
     if fp64_sequential:
         torch.cuda.synchronize()
@@ -408,6 +416,7 @@ def batched_record(args, lad, local, world, device_inputs, steps, warmup, fp64_s
            "tuned": tuned,
            "split_form_instances": sum(1 for f in forms if f == "pm"),
            "graph": "one CUDA graph replay per step",
+           "kernel_ms_one_call": split, "launches_one_call": sum(kcounts.values()),
            "inputs": "drawn on the GPU (timing)" if device_inputs else "ladder_inputs host generators",
            "roofline": roof, "clocks": clocks, "fp64_sequential": fp64}
     del ws, Ls, ts, Rs
@@ -436,6 +445,7 @@ def run_batched(args):
             "config": {"workload": rec["workload"], "instances": rec["instances"], "total_flops": rec["total_flops"],
                        "schedule": rec["schedule"], "tuned": rec["tuned"], "graph": rec["graph"]},
             "roofline": rec["roofline"], "clocks": rec["clocks"], "fp64_sequential": rec["fp64_sequential"],
+            "kernel_ms_one_call": rec["kernel_ms_one_call"], "gpu_launches": rec["launches_one_call"] * args.steps,
         }
         print(json.dumps(line), flush=True)
 

@@ -53,7 +53,7 @@ using namespace tc;
 constexpr int kG = kExpGroupRows;  // rows per exponent group
 constexpr int kEpiWarps = 8;       // ladder epilogue warps (2 per TMEM lane quadrant)
 constexpr int kThreadsTC = 32 * (2 + kEpiWarps);
-constexpr int kEriEpiWarps = 8;    // ERI epilogue warps (4 per TMEM lane quadrant)
+constexpr int kEriEpiWarps = 12;   // ERI epilogue warps (3 per TMEM lane quadrant)
 constexpr int kThreadsEri = 32 * (2 + kEriEpiWarps);
 constexpr int kEriRuns = kEmuTileN / (kEriEpiWarps / 4) / 8;  // runs of 8 columns per epilogue warp
 static_assert(kEriRuns % 2 == 0, "runs are stored in sector pairs");
