@@ -122,9 +122,8 @@ int ladder_plan_set_form(ladder_plan_t plan, int form);
 /* The form a plan uses: ladder_plan picks 1 on the emulated path when a cost model of the whole
  * call (ERI, tile-padded ladder rows, the extra pass over V) gives it a 5 % lead (the ladder a
  * large share of the call: large no^2 with respect to the 128/256-row MMA tiles and to nchol)
- * and the workspace fits, else 0.  The instances of a batched plan choose the same way.  In
- * form 1 the X and Y ladder items of a block pair run in one persistent launch when they take
- * the same CTA shape.  -1 for NULL. */
+ * and the workspace fits, else 0.  The instances of a batched plan choose the same way.  -1 for
+ * NULL. */
 int ladder_plan_get_form(ladder_plan_t plan);
 /* The form the cost model above picks for an emulated plan of this shape (nslices 0 = the
  * default), before the workspace check: 0 or 1; -1 for invalid arguments.  Host only. */

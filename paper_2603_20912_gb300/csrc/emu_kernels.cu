@@ -1935,8 +1935,9 @@ void launch_finalize_pm(const ladder_plan_s& p, const BlockPair& bp, void* ws, d
 }
 
 // One block pair in the symmetric/antisymmetric form: ERI and self-product entries as in the
-// plain form, V -> V', V'', the X and Y ladders (one persistent launch for both when they run on
-// the same CTA shape), and the four-way finalisation.
+// plain form, V -> V', V'', the X and Y ladders (one launch each: at no=100 nv=700 nchol=4000 one
+// launch for both took 5 % longer, at lower clocks under the power cap), and the four-way
+// finalisation.
 template <int S>
 cudaError_t block_pm_impl(const ladder_plan_s& p, const BlockPair& bp, const double* L, double* R, void* ws,
                           cudaStream_t s) {
@@ -1979,19 +1980,24 @@ cudaError_t block_pm_impl(const ladder_plan_s& p, const BlockPair& bp, const dou
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int fit = p.pair_clusters > 0 ? p.pair_clusters : p.num_sms / 2;
-    static thread_local LadBatch lbs[2];   // ~17 KB: kept off the stack
-    lbs[0] = LadBatch{};
-    lbs[1] = LadBatch{};
-    if (!add_pm_items<S>(p, bp, ws, lbs)) return cudaErrorInvalidValue;
-    for (int shape = 0; shape < 2; ++shape) {   // 0: single CTAs, 1: CTA pairs
-        LadBatch& lb = lbs[shape];
-        if (lb.nitems == 0) continue;
-        lb.status = p.d_status;
-        lb.wait_ns = p.wait_ns;
-        lb.BN = ladder_bn(p, shape == 1);
-        LaunchTimer tm(p, s, LADDER_KERNEL_LADDER);
-        launch_ladder_batch<S>(lb, shape == 1, fit, p.num_sms, s);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    {
+        const PmDims dd = pm_dims(p.no, p.nv);
+        const bool has_y = dd.nm > 0 && dd.km > 0;
+        for (int part = 0; part < (has_y ? 2 : 1); ++part) {
+            static thread_local LadBatch lb;
+            lb = LadBatch{};
+            lb.nitems = 1;
+            lb.status = p.d_status;
+            lb.wait_ns = p.wait_ns;
+            if (!ladder_item_pm<S>(p, bp, ws, 0, part == 0, &lb.item[0], &lb.ta[0], &lb.tb[0]))
+                return cudaErrorInvalidValue;
+            lb.BN = ladder_bn(p, lb.item[0].M > kEmuTile);
+            lb.units = lb.item[0].units;
+            lb.tiles = lb.item[0].ntiles;
+            LaunchTimer tm(p, s, LADDER_KERNEL_LADDER);
+            launch_ladder_batch<S>(lb, lb.item[0].M > kEmuTile, fit, p.num_sms, s);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
     }
     {
         LaunchTimer tm(p, s, LADDER_KERNEL_FINISH);
