@@ -991,15 +991,22 @@ int ladder_apply_host(ladder_plan_t plan, const double* L_host, const double* t2
     if (!aligned256(stage) || !aligned256(ws)) return LADDER_ERR_ARG;
     DeviceGuard guard(plan->device);
     if (!guard.ok) return LADDER_ERR_CUDA;
-    if (!plan->h2d_stream) {
-        if (cudaStreamCreateWithFlags(&plan->h2d_stream, cudaStreamNonBlocking) != cudaSuccess) {
-            plan->h2d_stream = nullptr;
+    if (!plan->h2d_stream) {   // first call: the copy stream and its events, all or nothing
+        cudaStream_t hs = nullptr;
+        cudaEvent_t ev[4] = {};
+        bool ok = cudaStreamCreateWithFlags(&hs, cudaStreamNonBlocking) == cudaSuccess;
+        for (int i = 0; i < 4 && ok; ++i) ok = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) {
+            for (auto e : ev)
+                if (e) cudaEventDestroy(e);
+            if (hs) cudaStreamDestroy(hs);
             return LADDER_ERR_CUDA;
         }
-        for (int s = 0; s < 2; ++s)
-            if (cudaEventCreateWithFlags(&plan->host_ready[s], cudaEventDisableTiming) != cudaSuccess ||
-                cudaEventCreateWithFlags(&plan->host_free[s], cudaEventDisableTiming) != cudaSuccess)
-                return LADDER_ERR_CUDA;
+        plan->host_ready[0] = ev[0];
+        plan->host_ready[1] = ev[1];
+        plan->host_free[0] = ev[2];
+        plan->host_free[1] = ev[3];
+        plan->h2d_stream = hs;
     }
     const StageLayout sl = stage_layout(*plan);
     const int s = plan->host_parity;
