@@ -51,7 +51,9 @@ namespace {
 using namespace tc;
 
 constexpr int kG = kExpGroupRows;  // rows per exponent group
-constexpr int kEpiWarps = 8;       // ladder epilogue warps (2 per TMEM lane quadrant)
+constexpr int kEpiWarps = 12;      // ladder epilogue warps (3 per TMEM lane quadrant)
+constexpr int kEpiPerQuad = kEpiWarps / 4;
+constexpr int kLadRuns = 6 / kEpiPerQuad;   // 16-column chunks per epilogue warp
 constexpr int kThreadsTC = 32 * (2 + kEpiWarps);
 constexpr int kEriEpiWarps = 12;   // ERI epilogue warps (3 per TMEM lane quadrant)
 constexpr int kThreadsEri = 32 * (2 + kEriEpiWarps);
@@ -1357,9 +1359,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1) ladder_emu_kernel(const __grid_
         // Each warp: TMEM lane quadrant q, column chunks ci = h, h+2, h+4 (16 columns each).
         const int q = warp & 3, h = (warp - 2) >> 2;
         const int nchunks = B.BN / 16;
-        long long run[3][16];
+        long long run[kLadRuns][16];
 #pragma unroll
-        for (int i = 0; i < 3; ++i)
+        for (int i = 0; i < kLadRuns; ++i)
 #pragma unroll
             for (int k = 0; k < 16; ++k) run[i][k] = 0;
         int it = 0;
@@ -1372,8 +1374,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1) ladder_emu_kernel(const __grid_
             if (!mbar_wait(&acc_full, (uint32_t)(it & 1), B.status, kStatusTimeout, B.wait_ns)) break;
             tc_fence_after();
 #pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                const int ci = h + 2 * i;
+            for (int i = 0; i < kLadRuns; ++i) {
+                const int ci = h + kEpiPerQuad * i;
                 if (ci < nchunks) {
                     const uint32_t base = tmem + ((uint32_t)(32 * q) << 16) + 16 * ci;
                     uint32_t v[3][16];
@@ -1406,8 +1408,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1) ladder_emu_kernel(const __grid_
                 tile_coords(p, tile, mt, nt);
                 const int m = mt * kEmuTile + 32 * q + lane;
 #pragma unroll
-                for (int i = 0; i < 3; ++i) {
-                    const int ci = h + 2 * i;
+                for (int i = 0; i < kLadRuns; ++i) {
+                    const int ci = h + kEpiPerQuad * i;
                     if (ci < nchunks) {
 #pragma unroll
                         for (int k = 0; k < 16; ++k) {
@@ -1534,9 +1536,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
     } else if (warp >= 2) {
         const int q = warp & 3, h = (warp - 2) >> 2;
         const uint32_t acc_empty_leader = mapa_rank(smem_u32(&acc_empty), 0);
-        long long run[3][16];
+        long long run[kLadRuns][16];
 #pragma unroll
-        for (int i = 0; i < 3; ++i)
+        for (int i = 0; i < kLadRuns; ++i)
 #pragma unroll
             for (int k = 0; k < 16; ++k) run[i][k] = 0;
         int it = 0;
@@ -1550,8 +1552,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
             if (!(ok = mbar_wait(&acc_full, (uint32_t)(it & 1), B.status, kStatusTimeout, B.wait_ns))) break;
             tc_fence_after();
 #pragma unroll
-            for (int cc = 0; cc < 3; ++cc) {
-                const uint32_t base = tmem + ((uint32_t)(32 * q) << 16) + 48 * h + 16 * cc;
+            for (int cc = 0; cc < kLadRuns; ++cc) {
+                const uint32_t base = tmem + ((uint32_t)(32 * q) << 16) + 16 * (h + kEpiPerQuad * cc);
                 uint32_t v[3][16];
                 tmem_ld16(base, v[0]);
                 tmem_ld16(base + kAccStride, v[1]);
@@ -1580,10 +1582,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreadsTC, 1)
                 tile_coords(p, tile, mt, nt);
                 const int m = mt * 2 * kEmuTile + kEmuTile * (int)rank + 32 * q + lane;  // (i,j)
 #pragma unroll
-                for (int cc = 0; cc < 3; ++cc)
+                for (int cc = 0; cc < kLadRuns; ++cc)
 #pragma unroll
                     for (int k = 0; k < 16; ++k) {
-                        const int n = nt * kEmuTileN + 48 * h + 16 * cc + k;                  // pair
+                        const int n = nt * kEmuTileN + 16 * (h + kEpiPerQuad * cc) + k;       // pair
                         if (m < p.M && n < p.N && run[cc][k] != 0 &&
                             LADDER_IN_BOUNDS((size_t)n * p.no2 + m < (size_t)p.N * p.no2, B.status))
                             atomicAdd(p.rp + (size_t)n * p.no2 + m, (unsigned long long)run[cc][k]);
