@@ -62,7 +62,7 @@ TRAFFIC_CAPTURES = {
     ("fp64", "c2"): ("efd514e3bd5bd3a9", 49657817856 + 6438093312, "profiles/dram_traffic_no10_nv200_nchol630.md",
                      (200, 200)),
     # mean of the call's two ERI launches (20100 and 60100 pair rows)
-    ("emu", "c3"): ("2af8c81092d6475b", (95538071296 + 32362756352 + 282143539968 + 93019627008) // 2,
+    ("emu", "c3"): ("97af10a6ecc01af8", (118275270912 + 32870906112 + 308907295488 + 93364802304) // 2,
                     "profiles/dram_traffic_no20_nv400_nchol1260_emu.md", (400, 200)),
 }
 KERNEL_SOURCE_DIR = os.path.join(ROOT, "paper_2603_20912_gb300", "csrc")
