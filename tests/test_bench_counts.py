@@ -73,3 +73,34 @@ def test_ladder_products_brute_force(no, nv):
         pm += sum(1 for i in range(no) for j in range(no) if i <= j) * sum(1 for c in range(nv) for d in range(nv) if c <= d)
         pm += sum(1 for i in range(no) for j in range(no) if i < j) * sum(1 for c in range(nv) for d in range(nv) if c < d)
     assert ladder_products(no, nv, "pm") == pm
+
+
+def test_fp64_roofline_counts_the_kernel_that_carries_the_flops():
+    # the fused kernel carries the whole call's packed flops; the rebuild order's ERI kernel its
+    # 2 X v^2 p share (timed separately from the ladder)
+    import types
+    import bench
+    import paper_2603_20912_gb300 as lad
+    from paper_2603_20912_gb300 import build
+    build.build()
+    cfg = types.SimpleNamespace(no=20, nv=400, nchol=1260)
+    kms = {"fused": 2000.0, "eri": 1500.0}
+    p = 400 * 401 // 2
+    for path, flops, ms in [(lad.LADDER_PATH_FUSED, lad.ladder_flops(20, 400, 1260), 2000.0),
+                            (lad.LADDER_PATH_ERI, 2.0 * 1260 * 400 * 400 * p, 1500.0)]:
+        plan = types.SimpleNamespace(path=lambda path=path: path)
+        r = bench.fp64_roofline(lad, plan, cfg, kms, 2, 1.1)
+        assert r["achieved"] == pytest.approx(flops * 2 / (ms * 1e-3) / 1e12)
+        assert r["frac"] == pytest.approx(r["achieved"] / 1.1)
+    assert "fused" in bench.fp64_roofline(lad, types.SimpleNamespace(path=lambda: 2), cfg, kms, 1, 1.1)["kernel"]
+
+
+def test_traffic_is_reported_only_for_the_captured_sources_and_blocking(monkeypatch):
+    import bench
+    sha, nbytes, src, blocking = bench.TRAFFIC_CAPTURES[("emu", "c3")]
+    monkeypatch.setattr(bench, "kernel_sources_sha", lambda: sha)
+    assert bench.captured_traffic("emu", "c3", blocking) == (nbytes, src)
+    assert bench.captured_traffic("emu", "c3", (blocking[0], blocking[1] + 1)) == (None, None)
+    monkeypatch.setattr(bench, "kernel_sources_sha", lambda: "0" * 16)
+    assert bench.captured_traffic("emu", "c3", blocking) == (None, None)
+    assert bench.captured_traffic("emu", "c9", blocking) == (None, None)
